@@ -1,0 +1,301 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test is chosen so that a plausible mistake in the oracle (a dropped
+term, a wrong sign or index, a transposed operand, a wrong rank rule)
+fails at least one of them.  None of them compares the oracle with itself.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as w
+from oracle import apply, hss, qrcp, tree
+from oracle.hss import Options, compress
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- generator
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = w.philox4x32_10(np.array(v[:4], dtype=np.uint32), np.array(v[4:6], dtype=np.uint32))
+        assert [int(x) for x in out] == v[6:]
+
+
+def test_gaussian_moments():
+    R = w.gaussian_matrix(7, 4096, 0, 64)
+    z = R.ravel()
+    assert abs(z.mean()) < 4 / math.sqrt(z.size)
+    assert abs(z.var() - 1) < 4 * math.sqrt(2 / z.size)
+    # columns drawn separately equal the corresponding block of a wide draw
+    assert np.array_equal(w.gaussian_matrix(7, 4096, 10, 5), R[:, 10:15])
+
+
+# --------------------------------------------------------------------- tree
+def test_halving_tree_partition():
+    for n, leaf in [(1024, 64), (1000, 64), (2048 + 77, 128), (64, 64), (65, 64)]:
+        nodes = tree.halving_tree(n, leaf)
+        assert nodes[0].lo == 0 and nodes[0].size == n
+        for t in nodes:
+            if t.children:
+                a, b = (nodes[c] for c in t.children)
+                assert a.lo == t.lo and a.size == t.size // 2
+                assert b.lo == a.lo + a.size and a.size + b.size == t.size
+                assert a.level == b.level == t.level + 1
+            else:
+                assert t.size <= leaf
+        # level order numbering
+        assert [t.level for t in nodes] == sorted(t.level for t in nodes)
+    assert len(tree.halving_tree(1024, 64)) == 31
+
+
+def test_rcb_properties():
+    rng = np.random.default_rng(3)
+    P = rng.random((1000, 3)) * np.array([1.0, 4.0, 2.0])
+    perm = tree.rcb_order(P, 64)
+    assert sorted(perm) == list(range(1000))
+    Q = P[perm]
+    for t in tree.halving_tree(1000, 64):
+        if not t.children:
+            continue
+        blk = Q[t.lo:t.lo + t.size]
+        c = int(np.argmax(blk.max(0) - blk.min(0)))
+        h = t.size // 2
+        assert blk[:h, c].max() <= blk[h:, c].min()
+    # 1-D points: RCB is a sort
+    x = rng.random((300, 1))
+    assert np.array_equal(tree.rcb_order(x, 8), np.argsort(x[:, 0], kind="stable"))
+
+
+# --------------------------------------------------------------------- QRCP
+def _graded(d, m, seed):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((d, m))
+    return G * (10.0 ** -np.linspace(0, 6, m))[rng.permutation(m)]
+
+
+def test_qrcp_matches_lapack_pivoting():
+    W = _graded(80, 50, 0)
+    piv, R, k, stopped = qrcp.qrcp(W, lambda j, r, r1: False)
+    Q2, R2, P2 = sla.qr(W, pivoting=True, mode="economic")
+    assert not stopped and k == 50
+    assert np.array_equal(piv, P2)
+    np.testing.assert_allclose(np.abs(np.diag(R)), np.abs(np.diag(R2)), rtol=1e-12)
+    # W Pi = Q R with Q orthonormal: R^T R = (W Pi)^T (W Pi)
+    WP = W[:, piv]
+    np.testing.assert_allclose(R.T @ R, WP.T @ WP, rtol=1e-10, atol=1e-12)
+
+
+def test_plain_rule_rank_and_id_exact():
+    rng = np.random.default_rng(1)
+    m, d, k = 60, 40, 13
+    S = rng.standard_normal((m, k)) @ rng.standard_normal((k, d))   # m x d, rank k
+    piv, R, kk, stopped = qrcp.qrcp(S.T, qrcp.plain_rule(1e-10, 1e-14))
+    assert stopped and kk == k
+    J, X, U = qrcp.interpolative(piv, R, kk)
+    np.testing.assert_array_equal(U[J], np.eye(k))
+    np.testing.assert_allclose(U @ S[J], S, rtol=0, atol=1e-11 * np.abs(S).max())
+
+
+def test_id_matches_scipy_interpolative():
+    import scipy.linalg.interpolative as sli
+    S = _graded(30, 45, 4).T            # 45 x 30 sample; ID of its rows
+    k = 12
+    idx, proj = sli.interp_decomp(np.asfortranarray(S.T), k, rand=False)
+    piv, R, kk, _ = qrcp.qrcp(S.T, lambda j, r, r1: j >= k)
+    J, X, U = qrcp.interpolative(piv, R, kk)
+    assert np.array_equal(J, idx[:k])
+    np.testing.assert_allclose(X, proj, rtol=1e-9, atol=1e-12)
+
+
+def test_hmt_rule_is_more_conservative():
+    rng = np.random.default_rng(2)
+    m, d = 80, 64
+    sv = 10.0 ** -np.linspace(0, 12, m)
+    U, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    S = (U * sv) @ rng.standard_normal((m, d))
+    _, _, k_plain, _ = qrcp.qrcp(S.T, qrcp.plain_rule(1e-6, 1e-30))
+    _, _, k_hmt, st = qrcp.qrcp(S.T, qrcp.hmt_rule(1e-6, 1e-30, d, m, 1000))
+    assert st and k_hmt > k_plain
+    # the factor grows without bound as the oversampling d-k-1 vanishes
+    assert qrcp.hmt_factor(d - 2, d, m, 1000) > qrcp.hmt_factor(10, d, m, 1000) > 1
+    assert qrcp.hmt_factor(d - 1, d, m, 1000) == math.inf
+
+
+# ------------------------------------------------------ Incrementing block test
+def test_incrementing_block_cases():
+    rng = np.random.default_rng(5)
+    m = 50
+    Q, _ = np.linalg.qr(rng.standard_normal((m, 10)))
+    # a block inside span(Q): the projected block vanishes -> sufficient
+    st = dict(Q=Q.copy(), rho=1.0)
+    assert hss.incrementing_block_test(Q @ rng.standard_normal((10, 8)), st, 1e-8, 1e-30)
+    # a full-rank block: not sufficient, Q grows by the block width, stays orthonormal
+    st = dict(Q=Q.copy(), rho=None)
+    assert not hss.incrementing_block_test(rng.standard_normal((m, 8)), st, 1e-8, 1e-30)
+    assert st["Q"].shape == (m, 18)
+    np.testing.assert_allclose(st["Q"].T @ st["Q"], np.eye(18), atol=1e-13)
+    # a rank-deficient block outside span(Q): min |diag R| is tiny -> sufficient
+    st = dict(Q=Q.copy(), rho=None)
+    blk = rng.standard_normal((m, 3)) @ rng.standard_normal((3, 8))
+    assert hss.incrementing_block_test(blk, st, 1e-8, 1e-30)
+
+
+def test_incrementing_residual_estimator():
+    """E ||(I-QQ^T) F R||_F^2 / b = ||(I-QQ^T) F||_F^2 (section 2.5): the
+    projected block norm estimates the residual of the Hankel block."""
+    rng = np.random.default_rng(6)
+    m, ncol, b = 40, 200, 16
+    F = rng.standard_normal((m, 5)) @ rng.standard_normal((5, ncol)) + 1e-3 * rng.standard_normal((m, ncol))
+    Q, _ = np.linalg.qr(F @ rng.standard_normal((ncol, 5)))
+    truth = np.linalg.norm(F - Q @ (Q.T @ F)) ** 2
+    est = []
+    for s in range(300):
+        Rk = w.gaussian_matrix(100 + s, ncol, 0, b)
+        Sk = F @ Rk
+        Sh = Sk - Q @ (Q.T @ Sk)
+        Sh = Sh - Q @ (Q.T @ Sh)
+        est.append(np.linalg.norm(Sh) ** 2 / b)
+    est = np.array(est)
+    assert abs(est.mean() - truth) < 4 * est.std() / math.sqrt(est.size)
+
+
+def test_norm_estimator_theorem1():
+    """E ||A R||_F^2 / d = ||A||_F^2 (Theorem 1 and the estimate after it)."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((30, 60)) * (0.7 ** np.arange(60))
+    vals = np.array([np.linalg.norm(A @ w.gaussian_matrix(s, 60, 0, 8)) ** 2 / 8 for s in range(500)])
+    assert abs(vals.mean() - np.linalg.norm(A) ** 2) < 4 * vals.std() / math.sqrt(vals.size)
+
+
+# ------------------------------------------------------------ compression
+@pytest.mark.parametrize("strategy", ["incrementing", "doubling"])
+@pytest.mark.parametrize("d0,dd", [(32, 16), (8, 8)])
+def test_synthetic_hss_exact_ranks(strategy, d0, dd):
+    n, leaf = 1024, 64
+    ranks = {4: 8, 3: 12, 2: 16, 1: 20}
+    A = w.synthetic_hss(n, leaf, ranks, seed=3)
+    R = w.gaussian_matrix(5, n, 0, 512)
+    res = compress(w.dense_source(A), R, Options(leaf=leaf, rtol=1e-10, atol=1e-14, d0=d0,
+                                                 dd=dd, d_max=512, strategy=strategy))
+    assert res.converged
+    for t in res.nodes[1:]:
+        assert len(t.Jr) == len(t.Jc) == ranks[t.level], (t.idx, t.level)
+    assert apply.rel_error(res, A) < 1e-12
+    if d0 == 8:
+        assert res.n_adapt >= 1
+
+
+def _hankel(A, t):
+    I = t.I
+    mask = np.ones(A.shape[0], bool)
+    mask[I] = False
+    return A[np.ix_(I, np.flatnonzero(mask))], A[np.ix_(np.flatnonzero(mask), I)]
+
+
+@pytest.mark.parametrize("strategy", ["incrementing", "doubling"])
+def test_bruteforce_svd_small(strategy):
+    """n = 512: every node's ID rank against the singular values of its
+    Hankel blocks, the interpolation error of the leaf Hankel blocks, and
+    the final error bound rtol."""
+    n, leaf = 512, 32
+    A = w.toeplitz_inverse_distance(n).to_dense()
+    R = w.gaussian_matrix(11, n, 0, 512)
+    rtol = 1e-6
+    opts = Options(leaf=leaf, rtol=rtol, atol=1e-14, d0=32, dd=16, d_max=512, strategy=strategy)
+    res = compress(w.toeplitz_inverse_distance(n), R, opts)
+    assert res.converged
+    L = max(t.level for t in res.nodes)
+    for t in res.nodes[1:]:
+        eps = rtol / t.level
+        Fr, Fc = _hankel(A, t)
+        for F, k in ((Fr, len(t.Jr)), (Fc.T, len(t.Jc))):
+            s = np.linalg.svd(F, compute_uv=False)
+            lo = int(np.sum(s > eps * s[0] * 30.0))
+            hi = int(np.sum(s > eps * s[0] / 30.0))
+            assert lo <= k <= hi + 16, (t.idx, k, lo, hi)
+        if t.is_leaf:
+            # rows J interpolate the true Hankel row block
+            err = np.linalg.norm(Fr - t.U @ Fr[t.Jr]) / np.linalg.norm(Fr)
+            assert err < 100 * eps, (t.idx, err)
+            err = np.linalg.norm(Fc.T - t.V @ Fc.T[t.Jc]) / np.linalg.norm(Fc)
+            assert err < 100 * eps, (t.idx, err)
+    assert apply.rel_error(res, A) <= rtol
+
+
+def test_structural_invariants():
+    n = 1024
+    src = w.toeplitz_inverse_distance(n)
+    A = src.to_dense()
+    res = compress(src, w.gaussian_matrix(0, n, 0, 1024), Options())
+    Ubig, Vbig = {}, {}
+    for t in reversed(res.nodes[1:]):
+        np.testing.assert_array_equal(t.U[t.Jr], np.eye(len(t.Jr)))
+        np.testing.assert_array_equal(t.V[t.Jc], np.eye(len(t.Jc)))
+        if t.is_leaf:
+            Ubig[t.idx], Vbig[t.idx] = t.U, t.V
+        else:
+            a, b = (res.nodes[c] for c in t.children)
+            # B blocks are exact sub-blocks of A at the skeleton indices
+            assert np.array_equal(t.B12, A[np.ix_(a.Ir, b.Ic)])
+            assert np.array_equal(t.B21, A[np.ix_(b.Ir, a.Ic)])
+            ka = Ubig[a.idx].shape[1]
+            Ubig[t.idx] = np.vstack([Ubig[a.idx] @ t.U[:ka], Ubig[b.idx] @ t.U[ka:]])
+            kc = Vbig[a.idx].shape[1]
+            Vbig[t.idx] = np.vstack([Vbig[a.idx] @ t.V[:kc], Vbig[b.idx] @ t.V[kc:]])
+        # nested skeleton: the big basis is the identity on the global rows I^r
+        np.testing.assert_allclose(Ubig[t.idx][t.Ir - t.lo], np.eye(len(t.Ir)), atol=1e-12)
+        np.testing.assert_allclose(Vbig[t.idx][t.Ic - t.lo], np.eye(len(t.Ic)), atol=1e-12)
+    x = np.random.default_rng(0).standard_normal((n, 3))
+    np.testing.assert_allclose(apply.matvec(res, x), A @ x, rtol=0, atol=5e-6 * np.abs(A @ x).max())
+
+
+def test_toeplitz_1024_error_bound():
+    wl = w.workload_toeplitz_1024()
+    A = wl.source.to_dense()
+    res = compress(wl.source, w.gaussian_matrix(0, 1024, 0, 1024),
+                   Options(leaf=64, rtol=1e-6, atol=1e-12, d0=64, dd=32, d_max=1024))
+    assert res.converged
+    assert apply.rel_error(res, A) <= 1e-6
+
+
+def test_not_converged_when_dmax_too_small():
+    n = 512
+    A = w.udv_matrix(n, 80, seed=2)
+    res = compress(w.dense_source(A), w.gaussian_matrix(0, n, 0, 24),
+                   Options(leaf=64, rtol=1e-12, atol=1e-16, d0=16, dd=8, d_max=24))
+    assert not res.converged and res.d_final == 24 and res.n_adapt == 1
+
+
+def test_block_diagonal_rank_zero():
+    """Zero off-diagonal blocks: every node has rank 0 and H = A exactly."""
+    n, leaf = 256, 32
+    A = np.zeros((n, n))
+    for lo in range(0, n, leaf):
+        A[lo:lo + leaf, lo:lo + leaf] = np.random.default_rng(lo).standard_normal((leaf, leaf))
+    for strat in ("incrementing", "doubling"):
+        res = compress(w.dense_source(A), w.gaussian_matrix(0, n, 0, 64),
+                       Options(leaf=leaf, d0=16, dd=16, d_max=64, strategy=strat))
+        assert res.converged and res.max_rank() == 0
+        np.testing.assert_array_equal(apply.to_dense(res), A)
+
+
+def test_table3_rank_band():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table3_udv_ranks.txt"))
+            if l.strip() and not l.startswith("#")]
+    n, r = 2048, 200
+    A = w.udv_matrix(n, r, seed=1)
+    R = w.gaussian_matrix(1, n, 0, 1024)
+    for rtol, atol, _err, rank in rows:
+        rtol, atol, rank = float(rtol), float(atol), int(rank)
+        res = compress(w.dense_source(A), R, Options(leaf=128, rtol=rtol, atol=atol, d0=128,
+                                                     dd=64, d_max=1024))
+        assert res.converged
+        assert 0.7 * rank <= res.max_rank() <= 1.3 * rank, (rtol, res.max_rank(), rank)
+        assert apply.rel_error(res, A) <= rtol
