@@ -1,0 +1,187 @@
+/*
+ * hss.h -- C ABI of the GB300 library for adaptive randomized HSS
+ * compression (Gorman, Chavez, Ghysels, Mary, Rouet, Li, "Matrix-free
+ * construction of HSS representation using adaptive randomized sampling",
+ * arXiv:1810.04125).
+ *
+ * Conventions for every entry point:
+ *  - All functions return hss_status (0 = HSS_OK).  None aborts or exits;
+ *    the last failure's message is available from hss_last_error().
+ *  - "device" pointers are CUDA global-memory pointers of the current
+ *    device, owned by the caller and only read (or written, for outputs)
+ *    during the call.  "host" pointers are ordinary CPU memory.
+ *  - Matrices are FP64.  "col-major" means element (i, j) at p[i + j*ld];
+ *    "row-major" means element (i, j) at p[i*ld + j].
+ *  - Work is issued on the caller's CUDA stream (NULL = legacy default
+ *    stream).  Calls return after their last stream synchronisation,
+ *    except hss_matvec, hss_random_normal and hss_sample_offdiag, which
+ *    are asynchronous on that stream.
+ */
+#ifndef HSS_H
+#define HSS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HSS_OK = 0,
+  HSS_ERR_ARG = 1,            /* invalid argument; nothing was launched        */
+  HSS_ERR_NOMEM = 2,          /* device or host allocation failed              */
+  HSS_ERR_CUDA = 3,           /* a CUDA call failed (message in last_error)    */
+  HSS_ERR_NOT_CONVERGED = 4,  /* d reached d_max with the root not COMPRESSED;
+                                 the handle is returned with per-node states,
+                                 but holds no usable generators                */
+  HSS_ERR_NONFINITE = 5,      /* NaN or Inf found in the random samples        */
+  HSS_ERR_TIMEOUT = 6,        /* a bounded device wait expired                 */
+  HSS_ERR_UNSUPPORTED = 7     /* option combination not implemented            */
+} hss_status;
+
+/* Sample growth strategy (paper section 2.4): Doubling = Algorithm 4 with
+ * the HMT-scaled RRQR stop of eq. RRQRHMTstop; Incrementing = Algorithm 5
+ * with the four tests of eq. stopping_criteria. */
+enum { HSS_DOUBLING = 0, HSS_INCREMENTING = 1 };
+
+/* Arithmetic of the sampling product S = A R (the only step that is not
+ * FP64 in the mixed forms; the QR, ID, tests and merges are always FP64).
+ *  FP64   : plain FP64 products.
+ *  TF32X2 : A split as A0 + A1 (two TF32 terms), R rounded once to TF32,
+ *           two tensor-core products with FP32 accumulation.
+ *  BF16X3 : A split as A0 + A1 + A2 (three BF16 terms), R rounded once to
+ *           BF16, three tensor-core products with FP32 accumulation. */
+enum { HSS_PREC_FP64 = 0, HSS_PREC_TF32X2 = 1, HSS_PREC_BF16X3 = 2 };
+
+/* Where the entries of A come from (paper section 3.1, "Partially
+ * Matrix-Free Interface": sampling plus element extraction A(I, J)). */
+enum {
+  HSS_SRC_DENSE = 0,     /* a: device col-major n x n, leading dimension ld  */
+  HSS_SRC_TOEPLITZ = 1,  /* a: device first column c[0..n-1], A_ij = c[i-j]
+                            for i >= j; b: device first row r[0..n-1],
+                            A_ij = r[j-i] for j > i (b may equal a)          */
+  HSS_SRC_GAUSS = 2,     /* a: device points, col-major n x dim (ld);
+                            A_ij = exp(-|x_i - x_j|^2 / (2 p0^2)) + p1 [i==j] */
+  HSS_SRC_LAPLACE = 3    /* a: device points, col-major n x 3 (ld);
+                            A_ij = 1 / (4 pi |x_i - x_j|), A_ii = p0          */
+};
+
+typedef struct hss_source {
+  int kind;              /* HSS_SRC_*                                        */
+  int n;                 /* matrix order                                     */
+  int dim;               /* point dimension (GAUSS, LAPLACE)                 */
+  int reserved;
+  const double* a;       /* device, see HSS_SRC_*                            */
+  const double* b;       /* device, TOEPLITZ first row; NULL otherwise       */
+  long long ld;          /* leading dimension of a (DENSE, points)           */
+  double p0, p1;         /* kernel parameters, see HSS_SRC_*                 */
+} hss_source;
+
+/* Node states of Algorithm 3. */
+enum { HSS_UNTOUCHED = 0, HSS_PARTIALLY_COMPRESSED = 1, HSS_COMPRESSED = 2 };
+
+typedef struct hss_opts {
+  int leaf;              /* leaf size of the halving cluster tree (>= 1)     */
+  int strategy;          /* HSS_DOUBLING or HSS_INCREMENTING                  */
+  int precision;         /* HSS_PREC_*                                       */
+  int level_tol_scaling; /* 1: node tolerances eps/level(tau) (Algorithm 3);
+                            0: plain eps                                      */
+  double rtol, atol;     /* eps_r, eps_a (> = 0)                              */
+  int d0;                /* initial number of random vectors                 */
+  int dd;                /* Incrementing step Delta d (ignored by Doubling)  */
+  int d_max;             /* cap on the number of random vectors (<= n)       */
+  int oversample_p;      /* Doubling oversampling p (paper default 10)       */
+  unsigned long long seed; /* Philox key when R == NULL                      */
+  const double* R;       /* optional device col-major n x d_max random
+                            matrix (ld = n); NULL = generated on the device
+                            with Philox4x32-10 (hss_random_normal)            */
+} hss_opts;
+
+typedef struct hss_stats {
+  int n, n_nodes, levels, d_final, n_adapt, converged;
+  int max_rank_r, max_rank_c;
+  double ms_total;       /* wall time of hss_compress on the stream (events) */
+  double ms_sample;      /* random generation + sampling kernels              */
+  double ms_id;          /* QRCP / ID kernels                                 */
+  double ms_test;        /* Incrementing projection + QR kernels              */
+  double ms_merge;       /* extraction, merge and reduction kernels           */
+  double flop_sample;    /* algorithmic sampling flops, sum of 4 n^2 Delta d */
+  double bytes_sample;   /* algorithmic sampling bytes (A read + S, R)        */
+  long long launches;    /* kernels launched by the call                      */
+} hss_stats;
+
+typedef struct hss_node_info {
+  int lo, size, level, parent, child0, child1; /* tree (level-order index)   */
+  int state;             /* HSS_UNTOUCHED / _PARTIALLY_COMPRESSED / _COMPRESSED */
+  int mr, mc;            /* rows of the local samples tau.S^r, tau.S^c        */
+  int kr, kc;            /* ranks: #J^r (columns of U), #J^c (columns of V)   */
+} hss_node_info;
+
+typedef struct hss_matrix_s* hss_matrix;   /* opaque; owns device memory    */
+
+/* Adaptive randomized HSS compression, Algorithm 3 (HSSCompressAdaptive and
+ * CompressNodeAdaptive) with Algorithm 2 (ComputeLocalSamples,
+ * ReduceLocalSamples), the ID of eq. ID and the strategy of opts->strategy.
+ * A: source of the entries of A (device data).  out: receives a handle,
+ * also on HSS_ERR_NOT_CONVERGED (then the states are valid but the
+ * generators are not); on any other error *out is NULL.  The handle owns
+ * all generator memory until hss_free. */
+hss_status hss_compress(const hss_source* A, const hss_opts* opts, void* stream,
+                        hss_matrix* out);
+
+/* Y = H X for a compressed handle: the O(r n) product of section 2.1
+ * (up-sweep x^_tau = V_tau^T [...], sibling coupling with B12/B21, down-sweep
+ * with U_tau, leaves D_tau).  X, Y: device col-major n x nrhs (ldx, ldy >= n);
+ * Y is overwritten.  Asynchronous on the stream. */
+hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx,
+                      double* Y, long long ldy, void* stream);
+
+hss_status hss_get_stats(hss_matrix H, hss_stats* s);                 /* host */
+hss_status hss_get_node(hss_matrix H, int node, hss_node_info* info); /* host */
+
+/* Host copies of one node's generators (any pointer may be NULL):
+ * Jr[kr], Jc[kc]  skeleton rows of tau.S^r / tau.S^c, local to the sample
+ *                 (pivot order; U(Jr, :) = I);
+ * Pr[mr], Pc[mc]  full pivot order (first kr / kc entries are Jr / Jc);
+ * Xr (kr x (mr-kr)), Xc (kc x (mc-kc))  col-major R1^{-1} R2, so that
+ *                 U = Pi [I; Xr^T] (eq. ID);
+ * Ir[kr], Ic[kc]  global skeleton indices tau.I^r, tau.I^c;
+ * D (size x size, leaves), B12 (kr(nu1) x kc(nu2)), B21 (kr(nu2) x kc(nu1))
+ *                 col-major, non-leaves. */
+hss_status hss_export_node(hss_matrix H, int node, int* Jr, int* Jc, int* Pr, int* Pc,
+                           double* Xr, double* Xc, int* Ir, int* Ic, double* D,
+                           double* B12, double* B21);
+
+void hss_free(hss_matrix H);
+const char* hss_status_str(hss_status s);
+const char* hss_last_error(void);
+
+/* Recursive coordinate bisection of a host point set (col-major n x dim,
+ * ld >= n): at each node of size m > leaf, sort by the coordinate of largest
+ * extent, ties by original index, and split into floor(m/2) + ceil(m/2).
+ * perm (host, n): perm[new] = old.  The halving tree of the permuted points
+ * is the cluster tree (paper section 3: binary, possibly imbalanced). */
+hss_status hss_rcb_order(const double* points, int n, int dim, long long ld, int leaf,
+                         int* perm);
+
+/* Gaussian random matrix R(:, col0:col0+ncols) (Table "helper functions",
+ * randn): Philox4x32-10 keyed by seed, counter (i >> 1, column, 0, 0), two
+ * 53-bit uniforms, Box-Muller; row i takes the cosine (even i) or sine (odd
+ * i) branch.  round_mode 0: FP64; 1: rounded to an 11-bit significand
+ * (TF32); 2: rounded to an 8-bit significand (BF16).  R: device col-major,
+ * column col0 at R (ld >= n).  Asynchronous. */
+hss_status hss_random_normal(unsigned long long seed, int n, int col0, int ncols,
+                             double* R, long long ldr, int round_mode, void* stream);
+
+/* The sampling step with the leaf diagonal blocks removed, eq.
+ * sample_off_diag at the leaf level:  Sr = (A - D^(L)) R,
+ * Sc = (A - D^(L))^T R, where D^(L) = blockdiag of the leaves of the halving
+ * tree with the given leaf size.  R: device col-major n x ncols (ldr);
+ * Sr, Sc: device row-major n x ncols (row stride lds >= ncols); either may
+ * be NULL to skip it.  precision: HSS_PREC_*.  Asynchronous. */
+hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int ncols,
+                              const double* R, long long ldr, double* Sr, double* Sc,
+                              long long lds, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSS_H */

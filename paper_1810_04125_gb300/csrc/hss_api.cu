@@ -1,0 +1,1131 @@
+// Host driver and C ABI of the HSS library (include/hss.h).
+//
+// hss_compress runs Algorithm 3 (HSSCompressAdaptive): sample, then sweep
+// the cluster tree bottom-up one level at a time, and grow the sample until
+// the root is COMPRESSED.  Every step of a level is one batched launch over
+// all nodes of that level (extraction, upward merge, strategy test, ID,
+// reduction); the host reads back the ranks and test flags once per level
+// (twice for Incrementing) to update the node states of Algorithm 3 and to
+// size the next level's buffers.  All arithmetic runs in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hss_internal.h"
+
+using namespace hss;
+
+namespace {
+
+thread_local std::string g_err;
+
+hss_status fail(hss_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(x)                                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (x);                                                                       \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(HSS_ERR_CUDA, "%s failed: %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                    \
+  } while (0)
+#define CKS(x)                      \
+  do {                              \
+    hss_status s_ = (x);            \
+    if (s_ != HSS_OK) return s_;    \
+  } while (0)
+
+// Chunked bump allocator for memory that lives as long as the handle.
+struct Arena {
+  std::vector<void*> chunks;
+  char* cur = nullptr;
+  size_t left = 0;
+  size_t chunk = size_t(256) << 20;
+  void* alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    if (bytes > left) {
+      size_t sz = std::max(chunk, bytes);
+      void* p = nullptr;
+      if (cudaMalloc(&p, sz) != cudaSuccess) return nullptr;
+      chunks.push_back(p);
+      cur = (char*)p;
+      left = sz;
+    }
+    void* r = cur;
+    cur += bytes;
+    left -= bytes;
+    return r;
+  }
+  void release() {
+    for (void* p : chunks) cudaFree(p);
+    chunks.clear();
+    cur = nullptr;
+    left = 0;
+  }
+};
+
+// Growable per-phase scratch (reset before each phase; growing waits for
+// the stream, which is idle at these points anyway).
+struct Scratch {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  std::vector<size_t> plan;
+  void reset() { used = 0; }
+  static size_t rnd(size_t b) { return (b + 255) & ~size_t(255); }
+  cudaError_t ensure(size_t bytes, cudaStream_t st) {
+    if (bytes <= cap) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+    size_t sz = std::max(bytes + bytes / 4, size_t(1) << 20);
+    e = cudaMalloc(&base, sz);
+    if (e != cudaSuccess) return e;
+    cap = sz;
+    return cudaSuccess;
+  }
+  void* take(size_t bytes) {
+    void* r = base + used;
+    used += rnd(bytes);
+    return r;
+  }
+  void release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = used = 0;
+  }
+};
+
+struct Side {
+  double* S = nullptr;   // local sample, m x dmax row-major
+  int m = 0, k = 0;
+  int* piv = nullptr;    // m
+  double* X = nullptr;   // k x (m-k) col-major, ld max(k,1)
+  int* I = nullptr;      // k global skeleton indices
+  double* Q = nullptr;   // Incrementing basis, m x dmax row-major
+  int q = 0, tested = 0;
+  double rho = -1.0;
+  bool done = false;
+  // per-level staging
+  int qr_k = 0, qr_acc = 0;
+};
+
+struct Node {
+  int lo, size, level, parent, ch[2];
+  bool leaf;
+  int state = HSS_UNTOUCHED;
+  Side r, c;
+  double* Rr = nullptr;  // tau.R^r = V^T R(I_tau): c.k x dmax row-major
+  double* Rc = nullptr;  // tau.R^c = U^T R(I_tau): r.k x dmax row-major
+  double* D = nullptr;   // leaf: size x size col-major
+  double* B12 = nullptr; // kr(nu1) x kc(nu2) col-major, ld max(kr(nu1),1)
+  double* B21 = nullptr; // kr(nu2) x kc(nu1) col-major, ld max(kr(nu2),1)
+};
+
+struct PhaseTimer {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ph;
+  cudaError_t mark(int phase, cudaStream_t st) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+    ph.push_back(phase);
+    return cudaEventRecord(e, st);
+  }
+  void sum(double out[6]) {
+    for (int i = 0; i < 6; ++i) out[i] = 0.0;
+    for (size_t i = 0; i + 1 < ev.size(); ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) {
+        out[ph[i]] += ms;
+        out[5] += ms;
+      }
+    }
+  }
+  void clear() {
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+    ph.clear();
+  }
+};
+enum { PH_SAMPLE = 0, PH_ID = 1, PH_TEST = 2, PH_MERGE = 3, PH_OTHER = 4 };
+
+}  // namespace
+
+struct hss_matrix_s {
+  int n = 0, dmax = 0, device = 0;
+  hss_opts o{};
+  hss_source src{};
+  std::vector<Node> nodes;
+  std::vector<std::vector<int>> by_level;
+  int max_level = 0;
+  Arena arena;
+  Scratch scratch;
+  double* R = nullptr;     // n x dmax col-major (ld n)
+  double* Sg_r = nullptr;  // n x dmax row-major: leaf samples
+  double* Sg_c = nullptr;
+  int* leaf_id = nullptr;
+  int* iota = nullptr;
+  int* d_flag = nullptr;   // device int scratch
+  int* h_pinned = nullptr; // host pinned readback buffer
+  size_t h_pinned_cap = 0;
+  int d_final = 0, n_adapt = 0, converged = 0;
+  bool usable = false;
+  hss_stats st{};
+  long long launches = 0;
+  PhaseTimer timer;
+  ~hss_matrix_s() {
+    timer.clear();
+    scratch.release();
+    arena.release();
+    if (h_pinned) cudaFreeHost(h_pinned);
+  }
+};
+
+namespace {
+
+SrcDev make_src(const hss_source& s, const int* leaf_id) {
+  SrcDev d;
+  d.kind = s.kind;
+  d.n = s.n;
+  d.dim = s.dim;
+  d.pad = 0;
+  d.a = s.a;
+  d.b = s.b ? s.b : s.a;
+  d.ld = s.ld;
+  d.p0 = s.p0;
+  d.p1 = s.p1;
+  d.leaf_id = leaf_id;
+  return d;
+}
+
+hss_status check_source(const hss_source* A) {
+  if (!A) return fail(HSS_ERR_ARG, "source is NULL");
+  if (A->n <= 0) return fail(HSS_ERR_ARG, "n must be positive (got %d)", A->n);
+  if (!A->a) return fail(HSS_ERR_ARG, "source data pointer is NULL");
+  switch (A->kind) {
+    case HSS_SRC_DENSE:
+      if (A->ld < A->n) return fail(HSS_ERR_ARG, "dense ld %lld < n %d", A->ld, A->n);
+      break;
+    case HSS_SRC_TOEPLITZ:
+      break;
+    case HSS_SRC_GAUSS:
+      if (A->dim <= 0 || A->ld < A->n) return fail(HSS_ERR_ARG, "points need dim > 0 and ld >= n");
+      if (!(A->p0 > 0.0)) return fail(HSS_ERR_ARG, "Gaussian bandwidth p0 must be > 0");
+      break;
+    case HSS_SRC_LAPLACE:
+      if (A->dim != 3 || A->ld < A->n) return fail(HSS_ERR_ARG, "Laplace points need dim == 3, ld >= n");
+      break;
+    default:
+      return fail(HSS_ERR_ARG, "unknown source kind %d", A->kind);
+  }
+  return HSS_OK;
+}
+
+// Halving tree in level order (node 0 = root).
+void build_tree(int n, int leaf, std::vector<Node>& nodes) {
+  nodes.clear();
+  Node root{};
+  root.lo = 0; root.size = n; root.level = 0; root.parent = -1; root.ch[0] = root.ch[1] = -1;
+  nodes.push_back(root);
+  for (size_t i = 0; i < nodes.size(); ++i) {
+    if (nodes[i].size > leaf) {
+      int h = nodes[i].size / 2;
+      Node a{}, b{};
+      a.lo = nodes[i].lo; a.size = h;
+      b.lo = nodes[i].lo + h; b.size = nodes[i].size - h;
+      a.level = b.level = nodes[i].level + 1;
+      a.parent = b.parent = (int)i;
+      a.ch[0] = a.ch[1] = b.ch[0] = b.ch[1] = -1;
+      nodes[i].ch[0] = (int)nodes.size();
+      nodes.push_back(a);
+      nodes[i].ch[1] = (int)nodes.size();
+      nodes.push_back(b);
+    }
+  }
+  for (auto& t : nodes) t.leaf = t.ch[0] < 0;
+}
+
+hss_status upload(hss_matrix_s* H, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return HSS_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+  return HSS_OK;
+}
+
+hss_status readback(hss_matrix_s* H, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes > H->h_pinned_cap) {
+    if (H->h_pinned) cudaFreeHost(H->h_pinned);
+    H->h_pinned = nullptr;
+    H->h_pinned_cap = 0;
+    size_t sz = std::max(bytes, size_t(1) << 16);
+    CK(cudaMallocHost((void**)&H->h_pinned, sz));
+    H->h_pinned_cap = sz;
+  }
+  if (bytes) CK(cudaMemcpyAsync(H->h_pinned, src, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return HSS_OK;
+}
+
+Opnd opnd(const double* p, long long rs, long long cs, const int* rows = nullptr,
+          const double* p2 = nullptr, int split = 0x7fffffff) {
+  Opnd o;
+  o.p = p; o.p2 = p2 ? p2 : p; o.rs = rs; o.cs = cs; o.rows = rows; o.split = split;
+  return o;
+}
+
+GemmJob gemm_job() {
+  GemmJob j;
+  memset(&j, 0, sizeof j);
+  j.A = opnd(nullptr, 0, 0);
+  j.B = opnd(nullptr, 0, 0);
+  j.C0 = opnd(nullptr, 0, 0);
+  j.c_split = 0x7fffffff;
+  j.alpha = 1.0;
+  return j;
+}
+
+// Runs a list of tile-product jobs (one launch).
+hss_status run_gemms(hss_matrix_s* H, const std::vector<GemmJob>& jobs, cudaStream_t st) {
+  std::vector<GemmTile> tiles;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    const GemmJob& j = jobs[i];
+    if (j.M <= 0 || j.N <= 0) continue;
+    for (int ti = 0; ti < (j.M + 63) / 64; ++ti)
+      for (int tj = 0; tj < (j.N + 63) / 64; ++tj) tiles.push_back({(int)i, ti, tj});
+  }
+  if (tiles.empty()) return HSS_OK;
+  size_t bj = jobs.size() * sizeof(GemmJob), bt = tiles.size() * sizeof(GemmTile);
+  void* dj = nullptr;
+  CK(cudaMallocAsync(&dj, Scratch::rnd(bj) + bt, st));
+  GemmTile* dt = (GemmTile*)((char*)dj + Scratch::rnd(bj));
+  CKS(upload(H, dj, jobs.data(), bj, st));
+  CKS(upload(H, dt, tiles.data(), bt, st));
+  CK(launch_gemm((const GemmJob*)dj, dt, (int)tiles.size(), st));
+  H->launches++;
+  CK(cudaFreeAsync(dj, st));
+  return HSS_OK;
+}
+
+template <class T>
+hss_status upload_jobs(hss_matrix_s* H, const std::vector<T>& jobs, T** dev, cudaStream_t st) {
+  *dev = nullptr;
+  if (jobs.empty()) return HSS_OK;
+  CK(cudaMallocAsync((void**)dev, jobs.size() * sizeof(T), st));
+  return upload(H, *dev, jobs.data(), jobs.size() * sizeof(T), st);
+}
+
+double tol_scale(const hss_matrix_s* H, int level) {
+  return H->o.level_tol_scaling ? 1.0 / (double)level : 1.0;
+}
+
+// ---------------------------------------------------------------- sampling
+hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool own_R) {
+  const int n = H->n, w = c1 - c0;
+  if (w <= 0) return HSS_OK;
+  CK(H->timer.mark(PH_SAMPLE, st));
+  if (own_R) {
+    int rm = H->o.precision == HSS_PREC_TF32X2 ? 1 : (H->o.precision == HSS_PREC_BF16X3 ? 2 : 0);
+    CK(launch_random_normal(H->o.seed, n, c0, w, H->R + (long long)c0 * n, n, rm, st));
+    H->launches++;
+  }
+  SrcDev s = make_src(H->src, H->leaf_id);
+  const double* Rc = H->R + (long long)c0 * n;
+  if (H->o.precision == HSS_PREC_FP64) {
+    CK(launch_sample_fp64(s, w, Rc, n, H->Sg_r + c0, H->Sg_c + c0, H->dmax, st));
+    H->launches += 2;
+  } else {
+    return fail(HSS_ERR_UNSUPPORTED, "mixed-precision sampling is not built in this library");
+  }
+  H->st.flop_sample += 4.0 * (double)n * (double)n * (double)w;
+  CK(cudaMemsetAsync(H->d_flag, 0, sizeof(int), st));
+  CK(launch_nonfinite(H->Sg_r, H->dmax, n, c0, c1, H->d_flag, st));
+  CK(launch_nonfinite(H->Sg_c, H->dmax, n, c0, c1, H->d_flag, st));
+  H->launches += 2;
+  CKS(readback(H, H->d_flag, sizeof(int), st));
+  if (H->h_pinned[0]) return fail(HSS_ERR_NONFINITE, "NaN or Inf in the random samples (columns %d..%d)", c0, c1);
+  return HSS_OK;
+}
+
+// ------------------------------------------------------ one pass of Alg. 3
+struct LevelWork {
+  std::vector<int> cand, upd;   // nodes to test / to update
+};
+
+hss_status alloc_side(hss_matrix_s* H, Side& s, bool leaf, double* Sleaf, int m) {
+  s.m = m;
+  s.S = leaf ? Sleaf : (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(m, 1) * H->dmax);
+  s.piv = (int*)H->arena.alloc(sizeof(int) * (size_t)std::max(m, 1));
+  if (!s.S || !s.piv) return fail(HSS_ERR_NOMEM, "device arena allocation failed (side, m=%d)", m);
+  if (H->o.strategy == HSS_INCREMENTING) {
+    s.Q = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(m, 1) * H->dmax);
+    if (!s.Q) return fail(HSS_ERR_NOMEM, "device arena allocation failed (basis Q)");
+  }
+  return HSS_OK;
+}
+
+// Merge jobs (Algorithm 2, non-leaf ComputeLocalSamples) for columns [cs, d).
+void merge_jobs(hss_matrix_s* H, Node& t, int cs, int d, std::vector<GemmJob>& jobs) {
+  Node& a = H->nodes[t.ch[0]];
+  Node& b = H->nodes[t.ch[1]];
+  const long long dm = H->dmax;
+  const int N = d - cs;
+  auto blk = [&](double* dst, const Side& child, const double* Bm, long long brs, long long bcs,
+                 const double* Rred, int K) {
+    GemmJob j = gemm_job();
+    j.M = child.k; j.N = N; j.K = K;
+    j.C0 = opnd(child.S + cs, dm, 1, child.piv);
+    j.beta = 1.0;
+    j.A = opnd(Bm, brs, bcs);
+    j.B = opnd(Rred + cs, dm, 1);
+    j.alpha = -1.0;
+    j.C = dst + cs; j.c_rs = dm; j.c_cs = 1;
+    jobs.push_back(j);
+  };
+  const int k1r = a.r.k, k2r = b.r.k, k1c = a.c.k, k2c = b.c.k;
+  // tau.S^r = [nu1.S^r(J) - B12 nu2.R^r ; nu2.S^r(J) - B21 nu1.R^r]
+  blk(t.r.S, a.r, t.B12, 1, std::max(k1r, 1), b.Rr, k2c);
+  blk(t.r.S + (long long)k1r * dm, b.r, t.B21, 1, std::max(k2r, 1), a.Rr, k1c);
+  // tau.S^c = [nu1.S^c(J) - B21^T nu2.R^c ; nu2.S^c(J) - B12^T nu1.R^c]
+  blk(t.c.S, a.c, t.B21, std::max(k2r, 1), 1, b.Rc, k2r);
+  blk(t.c.S + (long long)k1c * dm, b.c, t.B12, std::max(k1r, 1), 1, a.Rc, k1r);
+}
+
+// ReduceLocalSamples (Algorithm 2) for columns [cs, d): Rr = V^T x, Rc = U^T x.
+void reduce_jobs(hss_matrix_s* H, Node& t, int cs, int d, std::vector<GemmJob>& jobs) {
+  const long long dm = H->dmax;
+  const int N = d - cs;
+  auto one = [&](double* out, const Side& s, Opnd x_rows_gather_base) {
+    if (s.k <= 0 || N <= 0) return;
+    GemmJob j = gemm_job();
+    j.M = s.k; j.N = N; j.K = s.m - s.k;
+    Opnd c0 = x_rows_gather_base;
+    c0.rows = s.piv;
+    j.C0 = c0;
+    j.beta = 1.0;
+    j.A = opnd(s.X, 1, std::max(s.k, 1));
+    Opnd bb = x_rows_gather_base;
+    bb.rows = s.piv + s.k;
+    j.B = bb;
+    j.C = out + cs; j.c_rs = dm; j.c_cs = 1;
+    jobs.push_back(j);
+  };
+  if (t.leaf) {
+    Opnd x = opnd(H->R + t.lo + (long long)cs * H->n, 1, H->n);
+    one(t.Rr, t.c, x);
+    one(t.Rc, t.r, x);
+  } else {
+    Node& a = H->nodes[t.ch[0]];
+    Node& b = H->nodes[t.ch[1]];
+    one(t.Rr, t.c, opnd(a.Rr + cs, dm, 1, nullptr, b.Rr + cs, a.c.k));
+    one(t.Rc, t.r, opnd(a.Rc + cs, dm, 1, nullptr, b.Rc + cs, a.r.k));
+  }
+}
+
+// QRCP/ID over all columns [0, d) of the listed node sides.
+struct QrcpReq { int node; int side; int rule; };
+
+hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cudaStream_t st,
+                    std::vector<double*>& wbuf) {
+  H->scratch.reset();
+  size_t need = 0;
+  for (auto& q : reqs) {
+    Side& s = q.side ? H->nodes[q.node].c : H->nodes[q.node].r;
+    need += Scratch::rnd(sizeof(double) * (size_t)d * std::max(s.m, 1)) +
+            Scratch::rnd(sizeof(double) * 2 * std::max(s.m, 1)) + Scratch::rnd(3 * sizeof(int));
+  }
+  CK(H->scratch.ensure(need, st));
+  std::vector<QrcpJob> jobs;
+  wbuf.clear();
+  int* outs = nullptr;
+  for (size_t i = 0; i < reqs.size(); ++i) {
+    const QrcpReq& q = reqs[i];
+    Node& t = H->nodes[q.node];
+    Side& s = q.side ? t.c : t.r;
+    QrcpJob j;
+    memset(&j, 0, sizeof j);
+    j.S = s.S; j.lds = H->dmax; j.m = s.m; j.d = d;
+    j.W = (double*)H->scratch.take(sizeof(double) * (size_t)d * std::max(s.m, 1));
+    j.ldw = d;
+    j.nrm = (double*)H->scratch.take(sizeof(double) * 2 * std::max(s.m, 1));
+    j.piv = s.piv;
+    j.rule = q.rule;
+    j.mh = t.size; j.nh = H->n - t.size; j.p = H->o.oversample_p;
+    j.do_id = 1;
+    double sc = tol_scale(H, t.level);
+    j.er = H->o.rtol * sc; j.ea = H->o.atol * sc;
+    wbuf.push_back(j.W);
+    jobs.push_back(j);
+  }
+  outs = (int*)H->scratch.take(sizeof(int) * 3 * std::max<size_t>(reqs.size(), 1));
+  for (size_t i = 0; i < jobs.size(); ++i) jobs[i].out = outs + 3 * i;
+  if (jobs.empty()) return HSS_OK;
+  CK(H->timer.mark(PH_ID, st));
+  QrcpJob* dj;
+  CKS(upload_jobs(H, jobs, &dj, st));
+  CK(launch_qrcp(dj, (int)jobs.size(), st));
+  H->launches++;
+  CK(cudaFreeAsync(dj, st));
+  CKS(readback(H, outs, sizeof(int) * 3 * jobs.size(), st));
+  for (size_t i = 0; i < reqs.size(); ++i) {
+    Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
+    s.qr_k = H->h_pinned[3 * i];
+    s.qr_acc = H->h_pinned[3 * i + 2];
+  }
+  return HSS_OK;
+}
+
+// After an accepted QRCP: permanent X (compacted out of the workspace) and
+// the global skeleton indices tau.I = base(J).
+hss_status finalize_id(hss_matrix_s* H, int node, int side, const double* W, int d,
+                       std::vector<GemmJob>& copies, cudaStream_t st) {
+  Node& t = H->nodes[node];
+  Side& s = side ? t.c : t.r;
+  s.k = s.qr_k;
+  const int k = s.k, m = s.m;
+  s.X = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(k, 1) * std::max(m - k, 1));
+  s.I = (int*)H->arena.alloc(sizeof(int) * (size_t)std::max(k, 1));
+  if (!s.X || !s.I) return fail(HSS_ERR_NOMEM, "device arena allocation failed (ID)");
+  if (k > 0 && m > k) {
+    GemmJob j = gemm_job();
+    j.M = k; j.N = m - k; j.K = 0;
+    j.C0 = opnd(W + (long long)k * d, 1, d);
+    j.beta = 1.0;
+    j.C = s.X; j.c_rs = 1; j.c_cs = k;
+    copies.push_back(j);
+  }
+  if (k > 0) {
+    if (t.leaf) {
+      CK(launch_gather_int(H->iota + t.lo, s.piv, s.I, k, nullptr, 0x7fffffff, st));
+    } else {
+      Side& a = side ? H->nodes[t.ch[0]].c : H->nodes[t.ch[0]].r;
+      Side& b = side ? H->nodes[t.ch[1]].c : H->nodes[t.ch[1]].r;
+      CK(launch_gather_int(a.I, s.piv, s.I, k, b.I, a.k, st));
+    }
+    H->launches++;
+  }
+  return HSS_OK;
+}
+
+hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
+  const bool dbl = H->o.strategy == HSS_DOUBLING;
+  SrcDev src = make_src(H->src, H->leaf_id);
+  for (int lev = H->max_level; lev >= 1; --lev) {
+    LevelWork lw;
+    for (int id : H->by_level[lev]) {
+      Node& t = H->nodes[id];
+      if (!t.leaf && (H->nodes[t.ch[0]].state != HSS_COMPRESSED ||
+                      H->nodes[t.ch[1]].state != HSS_COMPRESSED))
+        continue;
+      (t.state == HSS_COMPRESSED ? lw.upd : lw.cand).push_back(id);
+    }
+    if (lw.cand.empty() && lw.upd.empty()) continue;
+    CK(H->timer.mark(PH_MERGE, st));
+    // --- extraction of D (new leaves) and B12/B21 (new non-leaves)
+    std::vector<ExtractJob> ex;
+    int max_tiles = 1;
+    auto add_ex = [&](const int* I, int i0, int mi, const int* J, int j0, int nj, double* out, long long ldo) {
+      if (mi <= 0 || nj <= 0) return;
+      ExtractJob e{I, i0, mi, J, j0, nj, out, ldo};
+      ex.push_back(e);
+      max_tiles = std::max(max_tiles, ((mi + 31) / 32) * ((nj + 31) / 32));
+    };
+    for (int id : lw.cand) {
+      Node& t = H->nodes[id];
+      if (t.state != HSS_UNTOUCHED) continue;
+      if (t.leaf) {
+        t.D = (double*)H->arena.alloc(sizeof(double) * (size_t)t.size * t.size);
+        if (!t.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
+        add_ex(nullptr, t.lo, t.size, nullptr, t.lo, t.size, t.D, t.size);
+        CKS(alloc_side(H, t.r, true, H->Sg_r + (long long)t.lo * H->dmax, t.size));
+        CKS(alloc_side(H, t.c, true, H->Sg_c + (long long)t.lo * H->dmax, t.size));
+      } else {
+        Node& a = H->nodes[t.ch[0]];
+        Node& b = H->nodes[t.ch[1]];
+        t.B12 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(a.r.k, 1) * std::max(b.c.k, 1));
+        t.B21 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(b.r.k, 1) * std::max(a.c.k, 1));
+        if (!t.B12 || !t.B21) return fail(HSS_ERR_NOMEM, "device arena allocation failed (B)");
+        add_ex(a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, t.B12, std::max(a.r.k, 1));
+        add_ex(b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, t.B21, std::max(b.r.k, 1));
+        CKS(alloc_side(H, t.r, false, nullptr, a.r.k + b.r.k));
+        CKS(alloc_side(H, t.c, false, nullptr, a.c.k + b.c.k));
+      }
+    }
+    if (!ex.empty()) {
+      ExtractJob* dj;
+      CKS(upload_jobs(H, ex, &dj, st));
+      CK(launch_extract(src, dj, (int)ex.size(), max_tiles, st));
+      H->launches++;
+      CK(cudaFreeAsync(dj, st));
+    }
+    // --- local samples of non-leaf nodes (upward merge)
+    std::vector<GemmJob> mj;
+    for (int id : lw.cand) {
+      Node& t = H->nodes[id];
+      if (!t.leaf) merge_jobs(H, t, t.state == HSS_UNTOUCHED ? 0 : d_prev, d, mj);
+    }
+    for (int id : lw.upd) {
+      Node& t = H->nodes[id];
+      if (!t.leaf) merge_jobs(H, t, d_prev, d, mj);
+    }
+    CKS(run_gemms(H, mj, st));
+
+    // --- strategy test on the candidates
+    std::vector<int> accepted;
+    std::vector<QrcpReq> reqs;
+    if (dbl) {
+      for (int id : lw.cand) {
+        reqs.push_back({id, 0, 1});
+        reqs.push_back({id, 1, 1});
+      }
+    } else {
+      // Incrementing: project the untested columns and run the block test
+      struct Sd { int node, side; };
+      std::vector<Sd> sides;
+      for (int id : lw.cand) {
+        Node& t = H->nodes[id];
+        for (int sd = 0; sd < 2; ++sd) {
+          Side& s = sd ? t.c : t.r;
+          if (s.done) s.tested = d;
+          else if (d > s.tested) sides.push_back({id, sd});
+        }
+      }
+      if (!sides.empty()) {
+        CK(H->timer.mark(PH_TEST, st));
+        H->scratch.reset();
+        size_t need = 0;
+        for (auto& x : sides) {
+          Side& s = x.side ? H->nodes[x.node].c : H->nodes[x.node].r;
+          size_t b = d - s.tested, m = std::max(s.m, 1);
+          need += Scratch::rnd(8 * m * b) + Scratch::rnd(8 * std::max<size_t>(std::max(s.q, s.m), 1) * b) +
+                  Scratch::rnd(8 * b) + Scratch::rnd(8 * 4) + Scratch::rnd(8);
+        }
+        CK(H->scratch.ensure(need, st));
+        std::vector<IncJob> ij;
+        std::vector<GemmJob> g1, g2, g3;
+        double* res0 = nullptr;
+        int* flag0 = nullptr;
+        for (auto& x : sides) {
+          Node& t = H->nodes[x.node];
+          Side& s = x.side ? t.c : t.r;
+          IncJob j;
+          memset(&j, 0, sizeof j);
+          const int b = d - s.tested, m = s.m;
+          j.S = s.S; j.lds = H->dmax; j.m = m; j.c0 = s.tested; j.b = b;
+          j.Q = s.Q; j.q = s.q;
+          j.Sh = (double*)H->scratch.take(8 * (size_t)std::max(m, 1) * b);
+          j.T = (double*)H->scratch.take(8 * (size_t)std::max(std::max(s.q, m), 1) * b);
+          j.tau = (double*)H->scratch.take(8 * (size_t)b);
+          double sc = tol_scale(H, t.level);
+          j.er = H->o.rtol * sc; j.ea = H->o.atol * sc;
+          j.rho = s.rho;
+          ij.push_back(j);
+          // Sh = S(:, tested:d)
+          GemmJob c = gemm_job();
+          c.M = m; c.N = b; c.K = 0;
+          c.C0 = opnd(s.S + s.tested, H->dmax, 1);
+          c.beta = 1.0;
+          c.C = j.Sh; c.c_rs = 1; c.c_cs = m;
+          g1.push_back(c);
+          if (s.q > 0) {
+            GemmJob t1 = gemm_job();   // T = Q^T Sh
+            t1.M = s.q; t1.N = b; t1.K = m;
+            t1.A = opnd(s.Q, 1, H->dmax);
+            t1.B = opnd(j.Sh, 1, m);
+            t1.C = j.T; t1.c_rs = 1; t1.c_cs = s.q;
+            g2.push_back(t1);
+            GemmJob t2 = gemm_job();   // Sh -= Q T
+            t2.M = m; t2.N = b; t2.K = s.q;
+            t2.A = opnd(s.Q, H->dmax, 1);
+            t2.B = opnd(j.T, 1, s.q);
+            t2.alpha = -1.0; t2.gamma = 1.0;
+            t2.C = j.Sh; t2.c_rs = 1; t2.c_cs = m;
+            g3.push_back(t2);
+          }
+        }
+        res0 = (double*)H->scratch.take(sizeof(double) * 4 * ij.size());
+        flag0 = (int*)H->scratch.take(sizeof(int) * 2 * ij.size());
+        for (size_t i = 0; i < ij.size(); ++i) { ij[i].res = res0 + 4 * i; ij[i].flag = flag0 + 2 * i; }
+        CKS(run_gemms(H, g1, st));
+        for (int rep = 0; rep < 2; ++rep) {   // (I - Q Q^T)^2
+          CKS(run_gemms(H, g2, st));
+          CKS(run_gemms(H, g3, st));
+        }
+        IncJob* dj;
+        CKS(upload_jobs(H, ij, &dj, st));
+        CK(launch_inc_qr(dj, (int)ij.size(), st));
+        H->launches++;
+        CK(cudaFreeAsync(dj, st));
+        // read flags and res together: copy both into the pinned buffer
+        std::vector<int> flags(2 * ij.size());
+        std::vector<double> res(4 * ij.size());
+        CK(cudaMemcpyAsync(flags.data(), flag0, sizeof(int) * flags.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(res.data(), res0, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < sides.size(); ++i) {
+          Side& s = sides[i].side ? H->nodes[sides[i].node].c : H->nodes[sides[i].node].r;
+          s.tested = d;
+          s.q = flags[2 * i + 1];
+          if (s.rho < 0.0 && res[4 * i + 3] >= 0.0) s.rho = res[4 * i + 3];
+          s.done = flags[2 * i] != 0;
+        }
+      }
+      for (int id : lw.cand) {
+        Node& t = H->nodes[id];
+        if (t.r.done && t.c.done) {
+          reqs.push_back({id, 0, 0});
+          reqs.push_back({id, 1, 0});
+        } else {
+          t.state = HSS_PARTIALLY_COMPRESSED;
+        }
+      }
+    }
+    std::vector<double*> wbuf;
+    CKS(run_qrcp(H, reqs, d, st, wbuf));
+    CK(H->timer.mark(PH_MERGE, st));
+    std::vector<GemmJob> copies, rj;
+    for (size_t i = 0; i + 1 < reqs.size(); i += 2) {
+      Node& t = H->nodes[reqs[i].node];
+      if (t.r.qr_acc && t.c.qr_acc) {
+        CKS(finalize_id(H, reqs[i].node, 0, wbuf[i], d, copies, st));
+        CKS(finalize_id(H, reqs[i].node, 1, wbuf[i + 1], d, copies, st));
+        t.state = HSS_COMPRESSED;
+        t.Rr = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(t.c.k, 1) * H->dmax);
+        t.Rc = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(t.r.k, 1) * H->dmax);
+        if (!t.Rr || !t.Rc) return fail(HSS_ERR_NOMEM, "device arena allocation failed (reduced R)");
+        accepted.push_back(reqs[i].node);
+      } else {
+        t.state = HSS_PARTIALLY_COMPRESSED;
+      }
+    }
+    CKS(run_gemms(H, copies, st));
+    for (int id : accepted) reduce_jobs(H, H->nodes[id], 0, d, rj);
+    for (int id : lw.upd) reduce_jobs(H, H->nodes[id], d_prev, d, rj);
+    CKS(run_gemms(H, rj, st));
+  }
+  Node& root = H->nodes[0];
+  if (root.leaf || (H->nodes[root.ch[0]].state == HSS_COMPRESSED &&
+                    H->nodes[root.ch[1]].state == HSS_COMPRESSED)) {
+    if (root.leaf && root.state == HSS_UNTOUCHED) {
+      root.D = (double*)H->arena.alloc(sizeof(double) * (size_t)root.size * root.size);
+      if (!root.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
+      std::vector<ExtractJob> ex{{nullptr, 0, root.size, nullptr, 0, root.size, root.D, root.size}};
+      ExtractJob* dj;
+      CKS(upload_jobs(H, ex, &dj, st));
+      CK(launch_extract(src, dj, 1, ((root.size + 31) / 32) * ((root.size + 31) / 32), st));
+      H->launches++;
+      CK(cudaFreeAsync(dj, st));
+    }
+    if (!root.leaf && root.state == HSS_UNTOUCHED) {
+      // the root keeps B12 = A(nu1.I^r, nu2.I^c) and B21 = A(nu2.I^r, nu1.I^c)
+      Node& a = H->nodes[root.ch[0]];
+      Node& b = H->nodes[root.ch[1]];
+      root.B12 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(a.r.k, 1) * std::max(b.c.k, 1));
+      root.B21 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(b.r.k, 1) * std::max(a.c.k, 1));
+      if (!root.B12 || !root.B21) return fail(HSS_ERR_NOMEM, "device arena allocation failed (B)");
+      std::vector<ExtractJob> ex;
+      int tiles = 1;
+      if (a.r.k > 0 && b.c.k > 0) {
+        ex.push_back({a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, root.B12, std::max(a.r.k, 1)});
+        tiles = std::max(tiles, ((a.r.k + 31) / 32) * ((b.c.k + 31) / 32));
+      }
+      if (b.r.k > 0 && a.c.k > 0) {
+        ex.push_back({b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, root.B21, std::max(b.r.k, 1)});
+        tiles = std::max(tiles, ((b.r.k + 31) / 32) * ((a.c.k + 31) / 32));
+      }
+      if (!ex.empty()) {
+        ExtractJob* dj;
+        CKS(upload_jobs(H, ex, &dj, st));
+        CK(launch_extract(src, dj, (int)ex.size(), tiles, st));
+        H->launches++;
+        CK(cudaFreeAsync(dj, st));
+      }
+    }
+    root.state = HSS_COMPRESSED;
+  }
+  return HSS_OK;
+}
+
+hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st, hss_matrix_s* H) {
+  const int n = A->n;
+  H->n = n;
+  H->o = *o;
+  H->src = *A;
+  H->dmax = std::min(o->d_max, n);
+  CK(cudaGetDevice(&H->device));
+  build_tree(n, o->leaf, H->nodes);
+  H->max_level = 0;
+  for (auto& t : H->nodes) H->max_level = std::max(H->max_level, t.level);
+  H->by_level.assign(H->max_level + 1, {});
+  for (size_t i = 0; i < H->nodes.size(); ++i) H->by_level[H->nodes[i].level].push_back((int)i);
+  // leaf id per index, iota
+  std::vector<int> lid(n), io(n);
+  {
+    int cnt = 0;
+    for (auto& t : H->nodes)
+      if (t.leaf) {
+        for (int i = t.lo; i < t.lo + t.size; ++i) lid[i] = cnt;
+        ++cnt;
+      }
+    for (int i = 0; i < n; ++i) io[i] = i;
+  }
+  const size_t nd = (size_t)n * H->dmax;
+  H->leaf_id = (int*)H->arena.alloc(sizeof(int) * n);
+  H->iota = (int*)H->arena.alloc(sizeof(int) * n);
+  H->d_flag = (int*)H->arena.alloc(256);
+  H->Sg_r = (double*)H->arena.alloc(sizeof(double) * nd);
+  H->Sg_c = (double*)H->arena.alloc(sizeof(double) * nd);
+  const bool mixed = o->precision != HSS_PREC_FP64;
+  const bool own_R = (o->R == nullptr) || mixed;
+  if (own_R) H->R = (double*)H->arena.alloc(sizeof(double) * nd);
+  else H->R = const_cast<double*>(o->R);
+  if (!H->leaf_id || !H->iota || !H->d_flag || !H->Sg_r || !H->Sg_c || !H->R)
+    return fail(HSS_ERR_NOMEM, "device allocation of %zu bytes for samples failed", 3 * nd * 8);
+  CKS(upload(H, H->leaf_id, lid.data(), sizeof(int) * n, st));
+  CKS(upload(H, H->iota, io.data(), sizeof(int) * n, st));
+  if (mixed && o->R) return fail(HSS_ERR_UNSUPPORTED, "caller R with mixed precision is not supported");
+
+  CK(H->timer.mark(PH_OTHER, st));
+  int d = std::min(o->d0, H->dmax), d_prev = 0;
+  CKS(sample_columns(H, 0, d, st, own_R));
+  for (;;) {
+    CKS(run_pass(H, d_prev, d, st));
+    if (H->nodes[0].state == HSS_COMPRESSED) { H->converged = 1; break; }
+    if (d >= H->dmax) break;
+    int dd = (o->strategy == HSS_DOUBLING) ? d : o->dd;
+    dd = std::min(dd, H->dmax - d);
+    CKS(sample_columns(H, d, d + dd, st, own_R));
+    d_prev = d;
+    d += dd;
+    H->n_adapt++;
+  }
+  CK(H->timer.mark(PH_OTHER, st));
+  CK(cudaStreamSynchronize(st));
+  H->d_final = d;
+  H->usable = H->converged != 0;
+  double ph[6];
+  H->timer.sum(ph);
+  H->st.ms_sample = ph[PH_SAMPLE];
+  H->st.ms_id = ph[PH_ID];
+  H->st.ms_test = ph[PH_TEST];
+  H->st.ms_merge = ph[PH_MERGE] + ph[PH_OTHER];
+  H->st.ms_total = ph[5];
+  H->timer.clear();
+  H->scratch.release();
+  return HSS_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+const char* hss_status_str(hss_status s) {
+  switch (s) {
+    case HSS_OK: return "HSS_OK";
+    case HSS_ERR_ARG: return "HSS_ERR_ARG";
+    case HSS_ERR_NOMEM: return "HSS_ERR_NOMEM";
+    case HSS_ERR_CUDA: return "HSS_ERR_CUDA";
+    case HSS_ERR_NOT_CONVERGED: return "HSS_ERR_NOT_CONVERGED";
+    case HSS_ERR_NONFINITE: return "HSS_ERR_NONFINITE";
+    case HSS_ERR_TIMEOUT: return "HSS_ERR_TIMEOUT";
+    case HSS_ERR_UNSUPPORTED: return "HSS_ERR_UNSUPPORTED";
+  }
+  return "HSS_ERR_UNKNOWN";
+}
+
+const char* hss_last_error(void) { return g_err.c_str(); }
+
+hss_status hss_compress(const hss_source* A, const hss_opts* o, void* stream, hss_matrix* out) {
+  if (!out) return fail(HSS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  CKS(check_source(A));
+  if (!o) return fail(HSS_ERR_ARG, "opts is NULL");
+  if (o->leaf < 1) return fail(HSS_ERR_ARG, "leaf must be >= 1 (got %d)", o->leaf);
+  if (o->d0 < 1 || o->d_max < 1) return fail(HSS_ERR_ARG, "d0 and d_max must be >= 1");
+  if (o->strategy != HSS_DOUBLING && o->strategy != HSS_INCREMENTING)
+    return fail(HSS_ERR_ARG, "unknown strategy %d", o->strategy);
+  if (o->strategy == HSS_INCREMENTING && o->dd < 1) return fail(HSS_ERR_ARG, "dd must be >= 1");
+  if (o->precision < HSS_PREC_FP64 || o->precision > HSS_PREC_BF16X3)
+    return fail(HSS_ERR_ARG, "unknown precision %d", o->precision);
+  if (!(o->rtol >= 0.0) || !(o->atol >= 0.0)) return fail(HSS_ERR_ARG, "tolerances must be >= 0");
+  if (o->oversample_p < 0) return fail(HSS_ERR_ARG, "oversample_p must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  hss_matrix_s* H = new (std::nothrow) hss_matrix_s();
+  if (!H) return fail(HSS_ERR_NOMEM, "host allocation failed");
+  hss_status s = compress_impl(A, o, st, H);
+  if (s != HSS_OK) {
+    cudaStreamSynchronize(st);
+    delete H;
+    return s;
+  }
+  H->st.n = H->n;
+  H->st.n_nodes = (int)H->nodes.size();
+  H->st.levels = H->max_level + 1;
+  H->st.d_final = H->d_final;
+  H->st.n_adapt = H->n_adapt;
+  H->st.converged = H->converged;
+  H->st.launches = H->launches;
+  for (size_t i = 1; i < H->nodes.size(); ++i) {
+    H->st.max_rank_r = std::max(H->st.max_rank_r, H->nodes[i].r.k);
+    H->st.max_rank_c = std::max(H->st.max_rank_c, H->nodes[i].c.k);
+  }
+  *out = H;
+  if (!H->converged)
+    return fail(HSS_ERR_NOT_CONVERGED, "root not compressed at d = d_max = %d", H->d_final);
+  return HSS_OK;
+}
+
+void hss_free(hss_matrix H) { delete H; }
+
+hss_status hss_get_stats(hss_matrix H, hss_stats* s) {
+  if (!H || !s) return fail(HSS_ERR_ARG, "NULL argument");
+  *s = H->st;
+  return HSS_OK;
+}
+
+hss_status hss_get_node(hss_matrix H, int node, hss_node_info* info) {
+  if (!H || !info) return fail(HSS_ERR_ARG, "NULL argument");
+  if (node < 0 || node >= (int)H->nodes.size()) return fail(HSS_ERR_ARG, "node %d out of range", node);
+  const Node& t = H->nodes[node];
+  info->lo = t.lo; info->size = t.size; info->level = t.level; info->parent = t.parent;
+  info->child0 = t.ch[0]; info->child1 = t.ch[1]; info->state = t.state;
+  info->mr = t.r.m; info->mc = t.c.m; info->kr = t.r.k; info->kc = t.c.k;
+  return HSS_OK;
+}
+
+hss_status hss_export_node(hss_matrix H, int node, int* Jr, int* Jc, int* Pr, int* Pc, double* Xr,
+                           double* Xc, int* Ir, int* Ic, double* D, double* B12, double* B21) {
+  if (!H) return fail(HSS_ERR_ARG, "NULL handle");
+  if (node < 0 || node >= (int)H->nodes.size()) return fail(HSS_ERR_ARG, "node %d out of range", node);
+  const Node& t = H->nodes[node];
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> hss_status {
+    if (!dst || !bytes) return HSS_OK;
+    if (!src) return fail(HSS_ERR_ARG, "node %d has no such generator", node);
+    CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    return HSS_OK;
+  };
+  if (t.state == HSS_COMPRESSED && node != 0) {
+    CKS(cp(Jr, t.r.piv, sizeof(int) * t.r.k));
+    CKS(cp(Jc, t.c.piv, sizeof(int) * t.c.k));
+    CKS(cp(Pr, t.r.piv, sizeof(int) * t.r.m));
+    CKS(cp(Pc, t.c.piv, sizeof(int) * t.c.m));
+    CKS(cp(Xr, t.r.X, sizeof(double) * (size_t)t.r.k * (t.r.m - t.r.k)));
+    CKS(cp(Xc, t.c.X, sizeof(double) * (size_t)t.c.k * (t.c.m - t.c.k)));
+    CKS(cp(Ir, t.r.I, sizeof(int) * t.r.k));
+    CKS(cp(Ic, t.c.I, sizeof(int) * t.c.k));
+  }
+  if (t.leaf) CKS(cp(D, t.D, sizeof(double) * (size_t)t.size * t.size));
+  if (!t.leaf && t.state == HSS_COMPRESSED) {
+    const Node& a = H->nodes[t.ch[0]];
+    const Node& b = H->nodes[t.ch[1]];
+    CKS(cp(B12, t.B12, sizeof(double) * (size_t)a.r.k * b.c.k));
+    CKS(cp(B21, t.B21, sizeof(double) * (size_t)b.r.k * a.c.k));
+  }
+  return HSS_OK;
+}
+
+hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, double* Y,
+                      long long ldy, void* stream) {
+  if (!H || !X || !Y) return fail(HSS_ERR_ARG, "NULL argument");
+  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators (not converged)");
+  if (nrhs < 0 || ldx < H->n || ldy < H->n) return fail(HSS_ERR_ARG, "bad nrhs / leading dimension");
+  if (nrhs == 0) return HSS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nn = (int)H->nodes.size();
+  // per-node x^ (kc x nrhs) and y^ (kr x nrhs), row-major (row stride nrhs)
+  std::vector<size_t> offx(nn), offy(nn);
+  size_t tot = 0;
+  for (int i = 1; i < nn; ++i) {
+    offx[i] = tot; tot += (size_t)H->nodes[i].c.k * nrhs;
+    offy[i] = tot; tot += (size_t)H->nodes[i].r.k * nrhs;
+  }
+  double* buf = nullptr;
+  CK(cudaMallocAsync((void**)&buf, sizeof(double) * std::max<size_t>(tot, 1), st));
+  auto xh = [&](int i) { return buf + offx[i]; };
+  auto yh = [&](int i) { return buf + offy[i]; };
+  const long long R_ = nrhs;
+  // up-sweep: x^_tau = V_tau^T [x(I_tau) | x^_nu1; x^_nu2]
+  for (int lev = H->max_level; lev >= 1; --lev) {
+    std::vector<GemmJob> jobs;
+    for (int id : H->by_level[lev]) {
+      Node& t = H->nodes[id];
+      const Side& s = t.c;
+      if (s.k <= 0) continue;
+      Opnd x = t.leaf ? opnd(X + t.lo, 1, ldx)
+                      : opnd(xh(t.ch[0]), R_, 1, nullptr, xh(t.ch[1]), H->nodes[t.ch[0]].c.k);
+      GemmJob j = gemm_job();
+      j.M = s.k; j.N = nrhs; j.K = s.m - s.k;
+      j.C0 = x; j.C0.rows = s.piv; j.beta = 1.0;
+      j.A = opnd(s.X, 1, std::max(s.k, 1));
+      j.B = x; j.B.rows = s.piv + s.k;
+      j.C = xh(id); j.c_rs = R_; j.c_cs = 1;
+      jobs.push_back(j);
+    }
+    hss_status e = run_gemms(H, jobs, st);
+    if (e != HSS_OK) { cudaFreeAsync(buf, st); return e; }
+  }
+  // down-sweep
+  for (int lev = 0; lev < H->max_level; ++lev) {
+    std::vector<GemmJob> p0, p1;
+    for (int id : H->by_level[lev]) {
+      Node& t = H->nodes[id];
+      if (t.leaf) continue;
+      const int a = t.ch[0], b = t.ch[1];
+      const Node& na = H->nodes[a];
+      const Node& nb = H->nodes[b];
+      const bool root = (id == 0);
+      if (!root && t.r.k > 0) {
+        // [y^_nu1; y^_nu2] = U_tau y^_tau, U = Pi [I; Xr^T]
+        GemmJob c = gemm_job();
+        c.M = t.r.k; c.N = nrhs; c.K = 0;
+        c.C0 = opnd(yh(id), R_, 1); c.beta = 1.0;
+        c.C = yh(a); c.C2 = yh(b); c.c_split = na.r.k; c.c_rows = t.r.piv;
+        c.c_rs = R_; c.c_cs = 1;
+        p0.push_back(c);
+        if (t.r.m > t.r.k) {
+          GemmJob g = gemm_job();
+          g.M = t.r.m - t.r.k; g.N = nrhs; g.K = t.r.k;
+          g.A = opnd(t.r.X, std::max(t.r.k, 1), 1);
+          g.B = opnd(yh(id), R_, 1);
+          g.C = yh(a); g.C2 = yh(b); g.c_split = na.r.k; g.c_rows = t.r.piv + t.r.k;
+          g.c_rs = R_; g.c_cs = 1;
+          p0.push_back(g);
+        }
+      }
+      const double gam = (root || t.r.k == 0) ? 0.0 : 1.0;
+      // y^_nu1 (+)= B12 x^_nu2 ; y^_nu2 (+)= B21 x^_nu1
+      GemmJob g1 = gemm_job();
+      g1.M = na.r.k; g1.N = nrhs; g1.K = nb.c.k;
+      g1.A = opnd(t.B12, 1, std::max(na.r.k, 1));
+      g1.B = opnd(xh(b), R_, 1);
+      g1.gamma = gam;
+      g1.C = yh(a); g1.c_rs = R_; g1.c_cs = 1;
+      p1.push_back(g1);
+      GemmJob g2 = gemm_job();
+      g2.M = nb.r.k; g2.N = nrhs; g2.K = na.c.k;
+      g2.A = opnd(t.B21, 1, std::max(nb.r.k, 1));
+      g2.B = opnd(xh(a), R_, 1);
+      g2.gamma = gam;
+      g2.C = yh(b); g2.c_rs = R_; g2.c_cs = 1;
+      p1.push_back(g2);
+    }
+    hss_status e = run_gemms(H, p0, st);
+    if (e == HSS_OK) e = run_gemms(H, p1, st);
+    if (e != HSS_OK) { cudaFreeAsync(buf, st); return e; }
+  }
+  // leaves: Y(I) = D X(I) + U y^
+  std::vector<GemmJob> l0, l1;
+  for (int id = 0; id < nn; ++id) {
+    Node& t = H->nodes[id];
+    if (!t.leaf) continue;
+    GemmJob g = gemm_job();
+    g.M = t.size; g.N = nrhs; g.K = t.size;
+    g.A = opnd(t.D, 1, t.size);
+    g.B = opnd(X + t.lo, 1, ldx);
+    g.C = Y + t.lo; g.c_rs = 1; g.c_cs = ldy;
+    l0.push_back(g);
+    if (id == 0 || t.r.k <= 0) continue;
+    GemmJob c = gemm_job();
+    c.M = t.r.k; c.N = nrhs; c.K = 0;
+    c.C0 = opnd(yh(id), R_, 1); c.beta = 1.0; c.gamma = 1.0;
+    c.C = Y + t.lo; c.c_rows = t.r.piv; c.c_rs = 1; c.c_cs = ldy;
+    l1.push_back(c);
+    if (t.r.m > t.r.k) {
+      GemmJob e2 = gemm_job();
+      e2.M = t.r.m - t.r.k; e2.N = nrhs; e2.K = t.r.k;
+      e2.A = opnd(t.r.X, std::max(t.r.k, 1), 1);
+      e2.B = opnd(yh(id), R_, 1);
+      e2.gamma = 1.0;
+      e2.C = Y + t.lo; e2.c_rows = t.r.piv + t.r.k; e2.c_rs = 1; e2.c_cs = ldy;
+      l1.push_back(e2);
+    }
+  }
+  hss_status e = run_gemms(H, l0, st);
+  if (e == HSS_OK) e = run_gemms(H, l1, st);
+  cudaFreeAsync(buf, st);
+  return e;
+}
+
+hss_status hss_rcb_order(const double* points, int n, int dim, long long ld, int leaf, int* perm) {
+  if (!points || !perm || n <= 0 || dim <= 0 || ld < n || leaf < 1)
+    return fail(HSS_ERR_ARG, "bad arguments to hss_rcb_order");
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  std::vector<std::pair<int, int>> stack{{0, n}};
+  std::vector<int> tmp;
+  while (!stack.empty()) {
+    auto [lo, m] = stack.back();
+    stack.pop_back();
+    if (m <= leaf) continue;
+    int best = 0;
+    double bext = -1.0;
+    for (int c = 0; c < dim; ++c) {
+      double mn = points[perm[lo] + c * ld], mx = mn;
+      for (int i = lo + 1; i < lo + m; ++i) {
+        double v = points[perm[i] + c * ld];
+        mn = std::min(mn, v);
+        mx = std::max(mx, v);
+      }
+      if (mx - mn > bext) { bext = mx - mn; best = c; }
+    }
+    const double* col = points + best * ld;
+    std::sort(perm + lo, perm + lo + m, [&](int x, int y) {
+      double a = col[x], b = col[y];
+      return a < b || (a == b && x < y);
+    });
+    int h = m / 2;
+    stack.push_back({lo + h, m - h});
+    stack.push_back({lo, h});
+  }
+  return HSS_OK;
+}
+
+hss_status hss_random_normal(unsigned long long seed, int n, int col0, int ncols, double* R,
+                             long long ldr, int round_mode, void* stream) {
+  if (!R || n <= 0 || ncols < 0 || col0 < 0 || ldr < n || round_mode < 0 || round_mode > 2)
+    return fail(HSS_ERR_ARG, "bad arguments to hss_random_normal");
+  CK(launch_random_normal(seed, n, col0, ncols, R, ldr, round_mode, (cudaStream_t)stream));
+  return HSS_OK;
+}
+
+hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int ncols, const double* R,
+                              long long ldr, double* Sr, double* Sc, long long lds, void* stream) {
+  CKS(check_source(A));
+  const int n = A->n;
+  if (leaf < 1 || ncols < 0 || !R || ldr < n || lds < ncols)
+    return fail(HSS_ERR_ARG, "bad arguments to hss_sample_offdiag");
+  if (precision != HSS_PREC_FP64)
+    return fail(HSS_ERR_UNSUPPORTED, "mixed-precision sampling is not built in this library");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<Node> nodes;
+  build_tree(n, leaf, nodes);
+  std::vector<int> lid(n);
+  int cnt = 0;
+  for (auto& t : nodes)
+    if (t.leaf) {
+      for (int i = t.lo; i < t.lo + t.size; ++i) lid[i] = cnt;
+      ++cnt;
+    }
+  int* d_lid = nullptr;
+  CK(cudaMallocAsync((void**)&d_lid, sizeof(int) * n, st));
+  CK(cudaMemcpyAsync(d_lid, lid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  SrcDev s = make_src(*A, d_lid);
+  CK(launch_sample_fp64(s, ncols, R, ldr, Sr, Sc, lds, st));
+  CK(cudaFreeAsync(d_lid, st));
+  return HSS_OK;
+}
+
+}  // extern "C"

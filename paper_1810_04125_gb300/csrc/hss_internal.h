@@ -1,0 +1,136 @@
+// Internal declarations shared by the host driver and the kernels of the
+// HSS library.  Nothing here is part of the C ABI (include/hss.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hss.h"
+
+namespace hss {
+
+// Device view of an hss_source plus the leaf id of every index (entries of
+// A inside one leaf's diagonal block are "on the diagonal" and are removed
+// from the sampled matrix, eq. sample_off_diag at the leaf level).
+struct SrcDev {
+  int kind, n, dim, pad;
+  const double* a;
+  const double* b;
+  long long ld;
+  double p0, p1;
+  const int* leaf_id;   // n entries, nondecreasing
+};
+
+// Entry A(i, j) in FP64 (the definitions of HSS_SRC_*).
+__device__ __forceinline__ double entry(const SrcDev& s, int i, int j) {
+  switch (s.kind) {
+    case HSS_SRC_DENSE:
+      return s.a[(long long)i + (long long)j * s.ld];
+    case HSS_SRC_TOEPLITZ:
+      return i >= j ? s.a[i - j] : s.b[j - i];
+    case HSS_SRC_GAUSS: {
+      double r2 = 0.0;
+      for (int c = 0; c < s.dim; ++c) {
+        double t = s.a[i + c * s.ld] - s.a[j + c * s.ld];
+        r2 = __fma_rn(t, t, r2);
+      }
+      return exp(-r2 / (2.0 * s.p0 * s.p0)) + (i == j ? s.p1 : 0.0);
+    }
+    default: {  // HSS_SRC_LAPLACE
+      if (i == j) return s.p0;
+      double r2 = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double t = s.a[i + c * s.ld] - s.a[j + c * s.ld];
+        r2 = __fma_rn(t, t, r2);
+      }
+      return 1.0 / (4.0 * 3.141592653589793 * sqrt(r2));
+    }
+  }
+}
+
+// A strided operand view: logical element (i, l) is
+//   base[r * rs + l * cs]  with r = rows ? rows[i] : i, and base = p, or p2
+//   with r -= split when r >= split (two stacked blocks).
+struct Opnd {
+  const double* p;
+  const double* p2;
+  long long rs, cs;
+  const int* rows;
+  int split;
+};
+
+// Generic batched FP64 tile product, one 64 x 64 output tile per CTA:
+//   C(rows_c[i], j) = alpha * sum_l A(i, l) B(l, j) + beta * C0(i, j)
+//                     + gamma * C(rows_c[i], j)
+struct GemmJob {
+  Opnd A, B, C0;
+  double* C;
+  long long c_rs, c_cs;
+  const int* c_rows;
+  double* C2;           // second output block for rows >= c_split
+  int c_split;
+  int M, N, K;
+  double alpha, beta, gamma;
+};
+struct GemmTile { int job, ti, tj; };
+
+// QR with column pivoting of W = S^T (S: m x d rows, row-major ld lds),
+// truncated by the plain rule (rule 0) or the HMT-scaled rule (rule 1),
+// followed by X = R1^{-1} R2 in place when accepted and do_id.
+struct QrcpJob {
+  const double* S;
+  long long lds;
+  int m, d;
+  double* W;            // workspace, col-major d x m, ld = ldw
+  long long ldw;
+  double* nrm;          // workspace 2*m
+  int* piv;             // out: m entries
+  int rule;             // 0 plain, 1 HMT
+  int mh, nh, p;        // Hankel block sizes and oversampling (HMT)
+  int do_id;
+  double er, ea;
+  int* out;             // out[0] = k, out[1] = stopped, out[2] = accepted
+};
+
+// One Incrementing block test on one side of a node (Algorithm 5):
+// Sh = (I - Q Q^T)^2 S(:, c0:c0+b), norms, Householder QR of Sh, the four
+// tests of eq. stopping_criteria, and on failure Q <- [Q Q_k].
+struct IncJob {
+  const double* S;      // m x lds row-major local sample
+  long long lds;
+  int m, c0, b;
+  double* Q;            // m x lds row-major, q columns in use
+  int q;
+  double* Sh;           // workspace m x b col-major (ld m)
+  double* T;            // workspace q x b col-major (ld q)
+  double* tau;          // workspace b
+  double er, ea;
+  double rho;           // |(R_1)_11| of the first block, < 0 if none yet
+  double* res;          // out: [0]=|S_k|_F, [1]=|Sh|_F, [2]=min|diag|, [3]=|R_11|
+  int* flag;            // out: [0]=sufficient, [1]=new q
+};
+
+// Gather of sub-blocks of A: out(i, j) = A(I[i], J[j]) (col-major, ld ldo);
+// I or J may be NULL meaning i0 + i / j0 + j.
+struct ExtractJob {
+  const int* I; int i0, mi;
+  const int* J; int j0, nj;
+  double* out; long long ldo;
+};
+
+// Launch wrappers (return cudaError_t of the launch).
+cudaError_t launch_random_normal(unsigned long long seed, int n, int col0, int ncols,
+                                 double* R, long long ldr, int round_mode, cudaStream_t st);
+cudaError_t launch_sample_fp64(const SrcDev& src, int ncols, const double* R, long long ldr,
+                               double* Sr, double* Sc, long long lds, cudaStream_t st);
+cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int njobs,
+                           int max_tiles, cudaStream_t st);
+cudaError_t launch_gemm(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles,
+                        cudaStream_t st);
+cudaError_t launch_qrcp(const QrcpJob* jobs_dev, int njobs, cudaStream_t st);
+cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
+cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int c1,
+                             int* flag, cudaStream_t st);
+cudaError_t launch_gather_int(const int* src, const int* idx, int* dst, int cnt,
+                              const int* src2, int split, cudaStream_t st);
+
+}  // namespace hss

@@ -1,0 +1,77 @@
+// Element extraction A(I, J) for the generators D_tau = A(I_tau, I_tau) and
+// B12 = A(nu1.I^r, nu2.I^c), B21 = A(nu2.I^r, nu1.I^c) (Algorithm 3,
+// section 3.1), all blocks of one tree level in one launch; plus small
+// helpers (finiteness check of the samples, index gathers for
+// tau.I^r = [nu1.I^r nu2.I^r](tau.J^r) of Algorithm 2).
+#include "hss_internal.h"
+
+namespace hss {
+namespace {
+
+// grid: (tile, job); each CTA fills 32 x 32 tiles of its job, striding
+// over the job's tiles.
+__global__ void k_extract(SrcDev src, const ExtractJob* __restrict__ jobs) {
+  const ExtractJob jb = jobs[blockIdx.y];
+  const int tiles_i = (jb.mi + 31) / 32, tiles_j = (jb.nj + 31) / 32;
+  const int ntiles = tiles_i * tiles_j;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int ti = t % tiles_i, tj = t / tiles_i;
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      int il = e % 32, jl = e / 32;
+      int i = ti * 32 + il, j = tj * 32 + jl;
+      if (i >= jb.mi || j >= jb.nj) continue;
+      int gi = jb.I ? jb.I[i] : jb.i0 + i;
+      int gj = jb.J ? jb.J[j] : jb.j0 + j;
+      jb.out[(long long)i + (long long)j * jb.ldo] = entry(src, gi, gj);
+    }
+  }
+}
+
+__global__ void k_nonfinite(const double* __restrict__ S, long long lds, int n, int c0, int c1,
+                            int* flag) {
+  int w = c1 - c0;
+  long long total = (long long)n * w;
+  int bad = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long i = t / w;
+    int c = c0 + (int)(t % w);
+    double v = S[i * lds + c];
+    if (!isfinite(v)) bad = 1;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+__global__ void k_gather_int(const int* __restrict__ src, const int* __restrict__ idx, int* dst,
+                             int cnt, const int* __restrict__ src2, int split) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  int r = idx[t];
+  dst[t] = (r < split) ? src[r] : src2[r - split];
+}
+
+}  // namespace
+
+cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int njobs, int max_tiles,
+                           cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  int gx = max_tiles < 1 ? 1 : (max_tiles > 64 ? 64 : max_tiles);
+  k_extract<<<dim3(gx, njobs), 256, 0, st>>>(src, jobs_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int c1, int* flag,
+                             cudaStream_t st) {
+  if (n <= 0 || c1 <= c0) return cudaSuccess;
+  k_nonfinite<<<152 * 4, 256, 0, st>>>(S, lds, n, c0, c1, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_int(const int* src, const int* idx, int* dst, int cnt, const int* src2,
+                              int split, cudaStream_t st) {
+  if (cnt <= 0) return cudaSuccess;
+  k_gather_int<<<(cnt + 127) / 128, 128, 0, st>>>(src, idx, dst, cnt, src2, split);
+  return cudaGetLastError();
+}
+
+}  // namespace hss

@@ -1,0 +1,131 @@
+"""Helpers shared by the GPU tests: marshalling of the seeded inputs to the
+C ABI and comparison of a GPU result with the oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+import workloads as w
+from oracle import apply, qrcp
+from oracle.tree import halving_tree
+
+
+def dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+def col_major(A: np.ndarray):
+    """Device tensor with A's entries stored column-major (stride(0) == 1)."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.float64).T)).to(dev()).t()
+
+
+def device_source(src: w.Source):
+    from paper_1810_04125_gb300 import hss
+    if src.kind == w.SRC_DENSE:
+        return hss.dense_source(col_major(src.dense))
+    if src.kind == w.SRC_TOEPLITZ:
+        import torch
+        return hss.toeplitz_source(torch.from_numpy(src.col).to(dev()),
+                                   torch.from_numpy(src.row).to(dev()))
+    return hss.points_source(src.kind, col_major(src.points), src.p0, src.p1)
+
+
+STRAT = {"incrementing": 1, "doubling": 0}
+PREC = {"fp64": 0, "tf32x2": 1, "bf16x3": 2}
+
+
+def gpu_compress(src, R, o, precision="fp64", pass_R=True, seed=0, allow_not_converged=False):
+    from paper_1810_04125_gb300 import hss
+    s = device_source(src)
+    Rd = col_major(R) if pass_R else None
+    opts = hss.make_opts(o.leaf, o.rtol, o.atol, o.d0, o.dd, o.d_max, STRAT[o.strategy],
+                         PREC[precision], o.p, seed, Rd, int(o.level_tol_scaling))
+    return hss.hss_compress(s, opts, allow_not_converged=allow_not_converged)
+
+
+def gpu_dense(H, n):
+    import torch
+    from paper_1810_04125_gb300 import hss
+    X = torch.eye(n, dtype=torch.float64, device=dev()).t()
+    Y = torch.empty((n, n), dtype=torch.float64, device=dev()).t()
+    hss.hss_matvec(H, X, Y)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy()
+
+
+class _Res:
+    def __init__(self, n, nodes):
+        self.n, self.nodes = n, nodes
+
+
+def expand_exported(H, n, leaf):
+    """The GPU generators put into the oracle's node objects, so that the
+    oracle's plain expansion (eq. nestedUV) can be applied to them."""
+    nodes = halving_tree(n, leaf)
+    for t in nodes:
+        e = H.export_node(t.idx)
+        if t.is_leaf:
+            t.D = e["D"]
+        if t.idx == 0:
+            if not t.is_leaf:
+                t.B12, t.B21 = e["B12"], e["B21"]
+            continue
+        for side in ("r", "c"):
+            piv, X = e["P" + side], e["X" + side]
+            k = X.shape[0]
+            m = piv.size
+            U = np.zeros((m, k))
+            U[piv[:k], np.arange(k)] = 1.0
+            U[piv[k:], :] = X.T
+            setattr(t, "U" if side == "r" else "V", U)
+            setattr(t, "J" + side, piv[:k])
+            setattr(t, "I" + side, e["I" + side])
+        if not t.is_leaf:
+            t.B12, t.B21 = e["B12"], e["B21"]
+    return _Res(n, nodes)
+
+
+def _thresholds(diag, er, ea, rule, d, mh, nh):
+    out = []
+    for j in range(diag.size):
+        f = 1.0
+        if rule == "hmt":
+            f = qrcp.hmt_factor(j + 1, d, mh, nh)
+        out.append(max(ea / f, er * diag[0] / f))
+    return np.array(out)
+
+
+def rank_mismatch_allowed(t, side, o, d, k_lo, k_hi, n, band=0.1):
+    """A rank difference is allowed where a pivot of the oracle's node sample
+    lies within +-10% of the threshold between the two ranks."""
+    S = (t.Sr if side == "r" else t.Sc)[:, :d]
+    _, Rf, _, _ = qrcp.qrcp(S.T, lambda j, r, r1: False)
+    diag = np.abs(np.diag(Rf))
+    scale = 1.0 / t.level if o.level_tol_scaling else 1.0
+    er, ea = o.rtol * scale, o.atol * scale
+    rule = "hmt" if o.strategy == "doubling" else "plain"
+    thr = _thresholds(diag, er, ea, rule, d, t.size, n - t.size)
+    for j in range(max(0, k_lo - 1), min(diag.size, k_hi + 1)):
+        if abs(diag[j] - thr[j]) <= band * thr[j]:
+            return True
+    return False
+
+
+def compare_with_oracle(H, ref, o, n):
+    """Ranks node by node; returns the list of unexplained mismatches."""
+    bad = []
+    gr = H.ranks()
+    for t in ref.nodes[1:]:
+        if t.Jr is None:
+            continue
+        kg = gr[t.idx]
+        ko = (len(t.Jr), len(t.Jc))
+        for s, a, b in (("r", kg[0], ko[0]), ("c", kg[1], ko[1])):
+            if a != b and not rank_mismatch_allowed(t, s, o, ref.d_final, min(a, b), max(a, b), n):
+                bad.append((t.idx, s, a, b))
+    return bad
+
+
+def rel_err(A, H_dense):
+    return float(np.linalg.norm(A - H_dense) / np.linalg.norm(A))
