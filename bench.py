@@ -1,0 +1,353 @@
+"""Benchmark: adaptive randomized HSS compression on one GB300 per rank.
+
+Workload (one step = one full hss_compress, all adaptation passes): the
+Gaussian kernel K_ij = exp(-|x_i - x_j|^2 / 2) + delta_ij on n = 16384
+points uniform in [0,1]^8 (seed 0), ordered by recursive coordinate
+bisection, leaf 128, rtol 1e-4, atol 1e-8, Doubling from d0 = 128 with
+p = 10, d_max = 4096; A is a dense FP64 matrix resident in HBM before the
+timed region (2.1 GB, larger than L2, so no flush is needed).
+
+metric: sampled TFLOP/s = sum over passes of 4 n^2 Delta d, divided by the
+compression time; the JSON line also carries the compression seconds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32x2]
+  python bench.py --impl reference     # the CPU oracle on a bounded sample
+
+Multi-GPU (torchrun): every rank compresses its own replica of the matrix
+(the path does not shard in this build), value = all ranks' flops / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HSS compression s and sampled TFLOP/s at rtol; mixed vs FP64 plain on 1 GB300"
+WORKLOAD = dict(workload="gauss8_rcb_n16384_dense_doubling", n=16384, dim=8, leaf=128, rtol=1e-4,
+                atol=1e-8, strategy="doubling", d0=128, p=10, d_max=4096, seed=0)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 FMA pipe: 2 FMA / clock / SM (the nominal 1.25 TFLOP/s over 152 SMs at
+# 2070 MHz); the plain sampling kernel is bound by it.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def traffic_from_profiles(kernel: str):
+    """Per-launch DRAM bytes of `kernel` on this workload, recorded from an
+    ncu capture in profiles/ (line 'traffic_bytes_per_launch: <int>')."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            v = line.split(":", 1)[1].strip()
+            return None if v in ("null", "") else float(v)
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def build_inputs(device, n, dim, seed, leaf):
+    """Points (RCB-ordered by the library's host routine) and the dense
+    Gaussian-kernel matrix, built on the device in column blocks."""
+    import torch
+
+    import workloads as w
+    from paper_1810_04125_gb300 import hss
+    P = w.uniform_points(n, dim, seed=seed)
+    P = P[hss.hss_rcb_order(P, leaf)]
+    X = torch.from_numpy(P).to(device)
+    A = torch.empty((n, n), dtype=torch.float64, device=device)      # A^T row-major = A col-major
+    blk = 1024
+    for j0 in range(0, n, blk):
+        Xj = X[j0:j0 + blk]
+        r2 = torch.zeros((Xj.shape[0], n), dtype=torch.float64, device=device)
+        for c in range(dim):
+            r2 += (Xj[:, c:c + 1] - X[:, c][None, :]) ** 2
+        A[j0:j0 + blk] = torch.exp(-r2 / 2.0)
+    A.diagonal().add_(1.0)
+    return P, A.t()     # column-major view: element (i, j) at i + j*n
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1810_04125_gb300 import build as B
+    B.build()
+    from paper_1810_04125_gb300 import hss
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = dict(WORKLOAD)
+    if args.n:
+        cfg["n"] = args.n
+        cfg["workload"] = WORKLOAD["workload"].replace("16384", str(args.n))
+    n = cfg["n"]
+    P, A = build_inputs(dev, n, cfg["dim"], cfg["seed"], cfg["leaf"])
+    prec = {"fp64": hss.HSS_PREC_FP64, "tf32x2": hss.HSS_PREC_TF32X2, "bf16x3": hss.HSS_PREC_BF16X3}[args.precision]
+    src = hss.dense_source(A)
+    opts = hss.make_opts(cfg["leaf"], cfg["rtol"], cfg["atol"], cfg["d0"], cfg["d0"], cfg["d_max"],
+                         hss.HSS_DOUBLING, prec, cfg["p"], seed=cfg["seed"])
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        with torch.cuda.stream(stream):
+            H = hss.hss_compress(src, opts, stream=stream)
+        return H
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    stats = []
+    clocks = Clocks(local)
+    with clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            H = step()
+            stats.append(H.stats())
+            del H
+        ev1.record(stream)
+        barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    flops = sum(s.flop_sample for s in stats)
+    tmax = t_ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+        f = torch.tensor([flops], device=dev, dtype=torch.float64)
+        dist.all_reduce(f)
+        flops_all = float(f.item())
+    else:
+        flops_all = flops
+    value = flops_all / (tmax / 1e3) / 1e12
+    s0 = stats[-1]
+
+    # --- end to end through the C ABI: A from pinned host memory, stats back
+    A_host = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+    A_host.copy_(A.t().cpu())
+    A_dev2 = torch.empty((n, n), dtype=torch.float64, device=dev)
+    src2 = hss.dense_source(A_dev2.t())
+    e2e_steps = max(1, min(args.steps, 2))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_flops, h2d, d2h = 0.0, 0, 0
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            A_dev2.copy_(A_host, non_blocking=True)
+            H = hss.hss_compress(src2, opts, stream=stream)
+        st = H.stats()
+        ranks = H.ranks()          # host-side per-node ranks (the result read back)
+        e2e_flops += st.flop_sample
+        h2d += A_host.numel() * 8 + st.bytes_h2d
+        d2h += st.bytes_d2h
+        del H
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": e2e_flops / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps)}
+
+    # --- roofline of the dominant kernel: the sampling kernels
+    pk, pk_kind = peaks()
+    if args.precision == "fp64":
+        ach = s0.flop_sample / s0.sample_launches / (s0.ms_sample / s0.sample_launches / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "kernel": "k_sample_fp64",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz",
+                "traffic": traffic_from_profiles("k_sample_fp64_gauss8_n16384")}
+    else:
+        ach = s0.bytes_sample / (s0.ms_sample / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "kernel": "k_sample_tc",
+                "peak_source": f"{pk_kind} hbm_gbs",
+                "traffic": traffic_from_profiles("k_sample_tc_gauss8_n16384")}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_n)
+    out = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
+        "data": "synthetic", "gpu_launches": int(sum(s.launches for s in stats)),
+        "config": {**cfg, "precision": args.precision, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (A is 2.1 GB); no flush"},
+        "compress_s": tmax / args.steps / 1e3,
+        "result": {"d_final": s0.d_final, "n_adapt": s0.n_adapt, "max_rank": max(s0.max_rank_r, s0.max_rank_c),
+                   "converged": s0.converged},
+        "phases_ms": {"sample": s0.ms_sample, "rng_check": s0.ms_rng, "id": s0.ms_id,
+                      "test": s0.ms_test, "merge_reduce": s0.ms_merge, "total": s0.ms_total},
+        "roofline": roof, "e2e": e2e, "clocks": clocks.summary(),
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def oracle_sample(n):
+    """The CPU oracle on the same family and settings at order n."""
+    import workloads as w
+    from oracle import tree
+    from oracle.hss import Options, compress
+    P = w.uniform_points(n, WORKLOAD["dim"], seed=WORKLOAD["seed"])
+    P = P[tree.rcb_order(P, WORKLOAD["leaf"])]
+    src = w.gaussian_kernel(P, 1.0, 1.0)
+    d_max = min(n, WORKLOAD["d_max"])
+    R = w.gaussian_matrix(WORKLOAD["seed"], n, 0, d_max)
+    o = Options(leaf=WORKLOAD["leaf"], rtol=WORKLOAD["rtol"], atol=WORKLOAD["atol"], d0=WORKLOAD["d0"],
+                dd=WORKLOAD["d0"], d_max=d_max, strategy="doubling", p=WORKLOAD["p"])
+    t = time.perf_counter()
+    res = compress(src, R, o)
+    dt = time.perf_counter() - t
+    fl = sum(4.0 * n * n * dd for dd in _deltas(res))
+    return fl, dt, res
+
+
+def _deltas(res):
+    ds = [p["d"] for p in res.passes]
+    return [ds[0]] + [b - a for a, b in zip(ds, ds[1:])]
+
+
+def cpu_cores():
+    try:
+        import numpy.__config__  # noqa: F401
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_baseline(n):
+    fl, dt, res = oracle_sample(n)
+    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"same kernel family and settings at n={n} (RCB points, leaf 128, Doubling, "
+                      f"rtol 1e-4): {dt:.1f} s, d_final {res.d_final}, max rank {res.max_rank()}"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(args.ref_n)
+    tot_fl, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        fl, dt, res = oracle_sample(args.ref_n)
+        tot_fl += fl
+        tot_t += dt
+    v = tot_fl / tot_t / 1e12
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {**WORKLOAD, "precision": "fp64", "sample_n": args.ref_n},
+           "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+                            "sample": f"oracle at n={args.ref_n} per step, same family and settings"},
+           "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32x2", "bf16x3"])
+    ap.add_argument("--cpu-n", type=int, default=2048)
+    ap.add_argument("--ref-n", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="diagnostic override of the matrix order")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

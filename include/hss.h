@@ -98,14 +98,19 @@ typedef struct hss_opts {
 typedef struct hss_stats {
   int n, n_nodes, levels, d_final, n_adapt, converged;
   int max_rank_r, max_rank_c;
-  double ms_total;       /* wall time of hss_compress on the stream (events) */
-  double ms_sample;      /* random generation + sampling kernels              */
+  double ms_total;       /* time of hss_compress on the stream (CUDA events)  */
+  double ms_sample;      /* sampling kernels only (events around them)        */
+  double ms_rng;         /* random generation and sample checks               */
   double ms_id;          /* QRCP / ID kernels                                 */
   double ms_test;        /* Incrementing projection + QR kernels              */
-  double ms_merge;       /* extraction, merge and reduction kernels           */
+  double ms_merge;       /* extraction, merge, reduction and bookkeeping      */
   double flop_sample;    /* algorithmic sampling flops, sum of 4 n^2 Delta d */
-  double bytes_sample;   /* algorithmic sampling bytes (A read + S, R)        */
+  double bytes_sample;   /* algorithmic sampling bytes: one read of A (dense
+                            source) + R read + S^r, S^c written, summed      */
   long long launches;    /* kernels launched by the call                      */
+  long long sample_launches; /* of which sampling kernels                     */
+  long long bytes_h2d;   /* host-to-device bytes copied by the call           */
+  long long bytes_d2h;   /* device-to-host bytes copied by the call           */
 } hss_stats;
 
 typedef struct hss_node_info {

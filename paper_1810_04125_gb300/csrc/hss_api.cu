@@ -146,13 +146,14 @@ struct PhaseTimer {
     ph.push_back(phase);
     return cudaEventRecord(e, st);
   }
-  void sum(double out[6]) {
-    for (int i = 0; i < 6; ++i) out[i] = 0.0;
+  // out[phase] = summed time of the phase; out[PH_N - 1] = total
+  void sum(double* out, int nph) {
+    for (int i = 0; i < nph; ++i) out[i] = 0.0;
     for (size_t i = 0; i + 1 < ev.size(); ++i) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) {
         out[ph[i]] += ms;
-        out[5] += ms;
+        out[nph - 1] += ms;
       }
     }
   }
@@ -162,7 +163,7 @@ struct PhaseTimer {
     ph.clear();
   }
 };
-enum { PH_SAMPLE = 0, PH_ID = 1, PH_TEST = 2, PH_MERGE = 3, PH_OTHER = 4 };
+enum { PH_SAMPLE = 0, PH_ID = 1, PH_TEST = 2, PH_MERGE = 3, PH_OTHER = 4, PH_RNG = 5, PH_N = 7 };
 
 }  // namespace
 
@@ -263,6 +264,7 @@ void build_tree(int n, int leaf, std::vector<Node>& nodes) {
 hss_status upload(hss_matrix_s* H, void* dst, const void* src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return HSS_OK;
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+  H->st.bytes_h2d += (long long)bytes;
   return HSS_OK;
 }
 
@@ -276,6 +278,7 @@ hss_status readback(hss_matrix_s* H, const void* src, size_t bytes, cudaStream_t
     H->h_pinned_cap = sz;
   }
   if (bytes) CK(cudaMemcpyAsync(H->h_pinned, src, bytes, cudaMemcpyDeviceToHost, st));
+  H->st.bytes_d2h += (long long)bytes;
   CK(cudaStreamSynchronize(st));
   return HSS_OK;
 }
@@ -336,7 +339,7 @@ double tol_scale(const hss_matrix_s* H, int level) {
 hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool own_R) {
   const int n = H->n, w = c1 - c0;
   if (w <= 0) return HSS_OK;
-  CK(H->timer.mark(PH_SAMPLE, st));
+  CK(H->timer.mark(PH_RNG, st));
   if (own_R) {
     int rm = H->o.precision == HSS_PREC_TF32X2 ? 1 : (H->o.precision == HSS_PREC_BF16X3 ? 2 : 0);
     CK(launch_random_normal(H->o.seed, n, c0, w, H->R + (long long)c0 * n, n, rm, st));
@@ -344,13 +347,18 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
   }
   SrcDev s = make_src(H->src, H->leaf_id);
   const double* Rc = H->R + (long long)c0 * n;
+  CK(H->timer.mark(PH_SAMPLE, st));
   if (H->o.precision == HSS_PREC_FP64) {
     CK(launch_sample_fp64(s, w, Rc, n, H->Sg_r + c0, H->Sg_c + c0, H->dmax, st));
     H->launches += 2;
+    H->st.sample_launches += 2;
   } else {
     return fail(HSS_ERR_UNSUPPORTED, "mixed-precision sampling is not built in this library");
   }
+  CK(H->timer.mark(PH_RNG, st));
   H->st.flop_sample += 4.0 * (double)n * (double)n * (double)w;
+  H->st.bytes_sample += (H->src.kind == HSS_SRC_DENSE ? 8.0 * n * (double)n : 0.0) +
+                        3.0 * 8.0 * n * (double)w;
   CK(cudaMemsetAsync(H->d_flag, 0, sizeof(int), st));
   CK(launch_nonfinite(H->Sg_r, H->dmax, n, c0, c1, H->d_flag, st));
   CK(launch_nonfinite(H->Sg_c, H->dmax, n, c0, c1, H->d_flag, st));
@@ -675,6 +683,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         CK(cudaMemcpyAsync(flags.data(), flag0, sizeof(int) * flags.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(res.data(), res0, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        H->st.bytes_d2h += (long long)(sizeof(int) * flags.size() + sizeof(double) * res.size());
         for (size_t i = 0; i < sides.size(); ++i) {
           Side& s = sides[i].side ? H->nodes[sides[i].node].c : H->nodes[sides[i].node].r;
           s.tested = d;
@@ -816,13 +825,14 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
   CK(cudaStreamSynchronize(st));
   H->d_final = d;
   H->usable = H->converged != 0;
-  double ph[6];
-  H->timer.sum(ph);
+  double ph[PH_N];
+  H->timer.sum(ph, PH_N);
   H->st.ms_sample = ph[PH_SAMPLE];
+  H->st.ms_rng = ph[PH_RNG];
   H->st.ms_id = ph[PH_ID];
   H->st.ms_test = ph[PH_TEST];
   H->st.ms_merge = ph[PH_MERGE] + ph[PH_OTHER];
-  H->st.ms_total = ph[5];
+  H->st.ms_total = ph[PH_N - 1];
   H->timer.clear();
   H->scratch.release();
   return HSS_OK;

@@ -44,9 +44,11 @@ class hss_stats(C.Structure):
     _fields_ = [("n", C.c_int), ("n_nodes", C.c_int), ("levels", C.c_int), ("d_final", C.c_int),
                 ("n_adapt", C.c_int), ("converged", C.c_int), ("max_rank_r", C.c_int),
                 ("max_rank_c", C.c_int), ("ms_total", C.c_double), ("ms_sample", C.c_double),
-                ("ms_id", C.c_double), ("ms_test", C.c_double), ("ms_merge", C.c_double),
-                ("flop_sample", C.c_double), ("bytes_sample", C.c_double),
-                ("launches", C.c_longlong)]
+                ("ms_rng", C.c_double), ("ms_id", C.c_double), ("ms_test", C.c_double),
+                ("ms_merge", C.c_double), ("flop_sample", C.c_double),
+                ("bytes_sample", C.c_double), ("launches", C.c_longlong),
+                ("sample_launches", C.c_longlong), ("bytes_h2d", C.c_longlong),
+                ("bytes_d2h", C.c_longlong)]
 
 
 class hss_node_info(C.Structure):
