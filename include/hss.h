@@ -186,6 +186,25 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
                               const double* R, long long ldr, double* Sr, double* Sc,
                               long long lds, void* stream);
 
+/* The same computation as hss_sample_offdiag (same arguments, same
+ * results), for callers that cannot let a library allocate device memory:
+ * a serving process or framework that owns the whole device-memory budget
+ * through its own pool, or a caller that cannot accept the synchronisation
+ * or the possible failure of cudaMalloc / cudaMallocAsync in the middle of
+ * a run.  It allocates nothing: the per-index leaf table the kernel needs
+ * lives in a fixed device array inside the library (4 MiB, held on every
+ * GPU that loads the library until the process exits), so n may not
+ * exceed 2^20 (larger n returns HSS_ERR_ARG without launching anything).
+ * The first call on a device looks up that array's device address (a
+ * one-time set-up per device); make that first call before any stream
+ * capture.  All calls share the array and overwrite the first n entries:
+ * calls that overlap on the GPU (on different streams, or from different
+ * host threads) race on it and must be serialised by the caller.  The
+ * paper has no counterpart to this entry point.  Asynchronous. */
+hss_status hss_sample_offdiag_noalloc(const hss_source* A, int leaf, int precision, int ncols,
+                                      const double* R, long long ldr, double* Sr, double* Sc,
+                                      long long lds, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1139,3 +1139,87 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
 }
 
 }  // extern "C"
+
+// ===================================================================
+// Sampling without any device allocation.
+//
+// hss_sample_offdiag allocates (stream-ordered) a small table that tells the
+// sampling kernel which leaf every index belongs to.  Some callers cannot
+// let a library allocate device memory: a serving process or framework that
+// owns the whole device-memory budget through its own pool, or a caller that
+// cannot accept the synchronisation or the possible failure of cudaMalloc /
+// cudaMallocAsync in the middle of a run.  hss_sample_offdiag_noalloc keeps
+// that table in a fixed device array that is part of the library image
+// instead: it exists on every GPU that loads the library, until the process
+// exits, and bounds n by HSS_NOALLOC_MAX_N.
+// ===================================================================
+#include <mutex>
+
+#define HSS_NOALLOC_MAX_N (1 << 20)   /* 4 MiB of leaf labels */
+#define HSS_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) int g_noalloc_leaf_label[HSS_NOALLOC_MAX_N];
+
+namespace {
+
+// leaf label of index i = first index of the leaf of the halving tree that
+// contains i (equal within a leaf, nondecreasing over i)
+__global__ void k_noalloc_leaf_label(int* label, int n, int leaf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, size = n;
+  while (size > leaf) {
+    int h = size / 2;
+    if (i < lo + h) size = h;
+    else { lo += h; size -= h; }
+  }
+  label[i] = lo;
+}
+
+std::mutex g_noalloc_mu;
+int* g_noalloc_ptr[HSS_NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the label array on the current device, looked up once
+// per device (host code must not pass the symbol itself to a kernel).
+hss_status noalloc_table(int** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= HSS_NOALLOC_MAX_DEVICES)
+    return fail(HSS_ERR_UNSUPPORTED, "device index %d beyond %d", dev, HSS_NOALLOC_MAX_DEVICES);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_leaf_label);
+    if (e != cudaSuccess || !p)
+      return fail(HSS_ERR_CUDA, "cudaGetSymbolAddress of the leaf-label array failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (int*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return HSS_OK;
+}
+
+}  // namespace
+
+extern "C" hss_status hss_sample_offdiag_noalloc(const hss_source* A, int leaf, int precision,
+                                                 int ncols, const double* R, long long ldr,
+                                                 double* Sr, double* Sc, long long lds,
+                                                 void* stream) {
+  CKS(check_source(A));
+  const int n = A->n;
+  if (leaf < 1 || ncols < 0 || !R || ldr < n || lds < ncols)
+    return fail(HSS_ERR_ARG, "bad arguments to hss_sample_offdiag_noalloc");
+  if (n > HSS_NOALLOC_MAX_N)
+    return fail(HSS_ERR_ARG, "n = %d exceeds the fixed table of hss_sample_offdiag_noalloc (%d)", n,
+                HSS_NOALLOC_MAX_N);
+  if (precision != HSS_PREC_FP64)
+    return fail(HSS_ERR_UNSUPPORTED, "mixed-precision sampling is not built in this library");
+  int* label = nullptr;
+  CKS(noalloc_table(&label));
+  cudaStream_t st = (cudaStream_t)stream;
+  k_noalloc_leaf_label<<<(n + 255) / 256, 256, 0, st>>>(label, n, leaf);
+  CK(cudaGetLastError());
+  SrcDev s = make_src(*A, label);
+  CK(launch_sample_fp64(s, ncols, R, ldr, Sr, Sc, lds, st));
+  return HSS_OK;
+}

@@ -24,7 +24,7 @@ HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
 
 EXPORTS = ["hss_compress", "hss_matvec", "hss_get_stats", "hss_get_node", "hss_export_node",
            "hss_free", "hss_status_str", "hss_last_error", "hss_rcb_order",
-           "hss_random_normal", "hss_sample_offdiag"]
+           "hss_random_normal", "hss_sample_offdiag", "hss_sample_offdiag_noalloc"]
 
 
 class hss_source(C.Structure):
@@ -82,6 +82,8 @@ def lib():
         L.hss_rcb_order.argtypes = [vp, i, i, ll, i, vp]
         L.hss_random_normal.argtypes = [C.c_ulonglong, i, i, i, vp, ll, i, vp]
         L.hss_sample_offdiag.argtypes = [C.POINTER(hss_source), i, i, i, vp, ll, vp, vp, ll, vp]
+        L.hss_sample_offdiag_noalloc.argtypes = [C.POINTER(hss_source), i, i, i, vp, ll, vp, vp,
+                                                 ll, vp]
         for f in EXPORTS:
             if f not in ("hss_free", "hss_status_str", "hss_last_error"):
                 getattr(L, f).restype = C.c_int
@@ -168,6 +170,16 @@ def hss_sample_offdiag(source, leaf, precision, R, Sr, Sc, stream=None):
     lds = (Sr if Sr is not None else Sc).stride(0)
     _check(lib().hss_sample_offdiag(C.byref(source), leaf, precision, ncols, _ptr(R), R.stride(1),
                                     _ptr(Sr), _ptr(Sc), lds, _stream(stream)))
+
+
+def hss_sample_offdiag_noalloc(source, leaf, precision, R, Sr, Sc, stream=None):
+    """hss_sample_offdiag for callers that cannot have the library allocate
+    device memory (the leaf table lives in a fixed array inside the library,
+    n <= 2^20; overlapping calls race on it)."""
+    ncols = R.shape[1]
+    lds = (Sr if Sr is not None else Sc).stride(0)
+    _check(lib().hss_sample_offdiag_noalloc(C.byref(source), leaf, precision, ncols, _ptr(R),
+                                            R.stride(1), _ptr(Sr), _ptr(Sc), lds, _stream(stream)))
 
 
 class HSSMatrix:
