@@ -111,6 +111,9 @@ typedef struct hss_stats {
   long long sample_launches; /* of which sampling kernels                     */
   long long bytes_h2d;   /* host-to-device bytes copied by the call           */
   long long bytes_d2h;   /* device-to-host bytes copied by the call           */
+  double flop_id;        /* algorithmic flops of the QRCP/ID kernels: 2md for
+                            the norms, 4(d-j)(m-j-1) + 3(d-j) per pivot step
+                            j, k^2 (m-k) for X = R1^{-1} R2                   */
 } hss_stats;
 
 typedef struct hss_node_info {

@@ -82,7 +82,7 @@ struct Scratch {
   char* base = nullptr;
   size_t cap = 0, used = 0;
   std::vector<size_t> plan;
-  void reset() { used = 0; }
+  void reset() { used = 0; overflow = false; }
   static size_t rnd(size_t b) { return (b + 255) & ~size_t(255); }
   cudaError_t ensure(size_t bytes, cudaStream_t st) {
     if (bytes <= cap) return cudaSuccess;
@@ -97,7 +97,12 @@ struct Scratch {
     cap = sz;
     return cudaSuccess;
   }
+  bool overflow = false;   // a take() beyond the capacity (a sizing bug); checked by callers
   void* take(size_t bytes) {
+    if (used + rnd(bytes) > cap) {
+      overflow = true;
+      return base;
+    }
     void* r = base + used;
     used += rnd(bytes);
     return r;
@@ -185,11 +190,14 @@ struct hss_matrix_s {
   int* h_pinned = nullptr; // host pinned readback buffer
   size_t h_pinned_cap = 0;
   int d_final = 0, n_adapt = 0, converged = 0;
+  int qrcp_cap = -1;       // co-resident CTAs of the group QRCP kernel
+  void* packA = nullptr;   // packed tensor-core tiles of a dense A (during compress)
   bool usable = false;
   hss_stats st{};
   long long launches = 0;
   PhaseTimer timer;
   ~hss_matrix_s() {
+    if (packA) cudaFree(packA);
     timer.clear();
     scratch.release();
     arena.release();
@@ -340,30 +348,79 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
   const int n = H->n, w = c1 - c0;
   if (w <= 0) return HSS_OK;
   CK(H->timer.mark(PH_RNG, st));
-  if (own_R) {
-    int rm = H->o.precision == HSS_PREC_TF32X2 ? 1 : (H->o.precision == HSS_PREC_BF16X3 ? 2 : 0);
+  const int rm = H->o.precision == HSS_PREC_TF32X2 ? 1 : (H->o.precision == HSS_PREC_BF16X3 ? 2 : 0);
+  if (own_R && H->o.R == nullptr) {
     CK(launch_random_normal(H->o.seed, n, c0, w, H->R + (long long)c0 * n, n, rm, st));
+    H->launches++;
+  } else if (own_R) {
+    // caller's R made exactly representable in the tensor format (reading P10)
+    CK(launch_round_copy(H->o.R + (long long)c0 * n, n, H->R + (long long)c0 * n, n, n, w, rm, st));
     H->launches++;
   }
   SrcDev s = make_src(H->src, H->leaf_id);
   const double* Rc = H->R + (long long)c0 * n;
-  CK(H->timer.mark(PH_SAMPLE, st));
   if (H->o.precision == HSS_PREC_FP64) {
+    CK(H->timer.mark(PH_SAMPLE, st));
     CK(launch_sample_fp64(s, w, Rc, n, H->Sg_r + c0, H->Sg_c + c0, H->dmax, st));
     H->launches += 2;
     H->st.sample_launches += 2;
+  } else if (H->src.kind == HSS_SRC_DENSE) {
+    // dense A: split once per compression into packed tensor-core tiles
+    if (!H->packA) {
+      const size_t pb = packed_a_bytes(n, H->o.precision);
+      CK(cudaMallocAsync(&H->packA, pb, st));
+      CK(launch_pack_a(s, H->o.leaf, H->o.precision, H->packA, st));
+      H->launches++;
+    }
+    void* packR = nullptr;
+    CK(cudaMallocAsync(&packR, packed_r_bytes(n, w, H->o.precision), st));
+    CK(launch_pack_r(Rc, n, n, w, H->o.precision, packR, st));
+    H->launches++;
+    if (sample_tc_packed_ksplit(n, w, H->o.precision) > 1) {
+      CK(cudaMemset2DAsync(H->Sg_r + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
+      CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
+    }
+    CK(cudaMemsetAsync(H->d_flag + 1, 0, sizeof(int), st));
+    CK(H->timer.mark(PH_SAMPLE, st));
+    CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 0, H->Sg_r + c0, H->dmax,
+                               H->d_flag + 1, st));
+    CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 1, H->Sg_c + c0, H->dmax,
+                               H->d_flag + 1, st));
+    H->launches += 2;
+    H->st.sample_launches += 2;
+    CK(H->timer.mark(PH_RNG, st));
+    CK(cudaFreeAsync(packR, st));
   } else {
-    return fail(HSS_ERR_UNSUPPORTED, "mixed-precision sampling is not built in this library");
+    if (sample_tc_ksplit(n, w, H->o.precision) > 1) {
+      CK(cudaMemset2DAsync(H->Sg_r + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
+      CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
+    }
+    CK(cudaMemsetAsync(H->d_flag + 1, 0, sizeof(int), st));
+    CK(H->timer.mark(PH_SAMPLE, st));
+    int at = 0;
+    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 0, w, Rc, n, H->Sg_r + c0, H->dmax,
+                        H->d_flag + 1, &at, st));
+    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 1, w, Rc, n, H->Sg_c + c0, H->dmax,
+                        H->d_flag + 1, &at, st));
+    H->launches += 2;
+    H->st.sample_launches += 2;
   }
   CK(H->timer.mark(PH_RNG, st));
   H->st.flop_sample += 4.0 * (double)n * (double)n * (double)w;
-  H->st.bytes_sample += (H->src.kind == HSS_SRC_DENSE ? 8.0 * n * (double)n : 0.0) +
-                        3.0 * 8.0 * n * (double)w;
+  // algorithmic bytes of the sampling kernels: A read once per orientation
+  // (FP64: 8 B per entry; packed TF32x2: 8 B; packed BF16x3: 6 B), R read,
+  // S written
+  double abytes = 0.0;
+  if (H->src.kind == HSS_SRC_DENSE)
+    abytes = (H->o.precision == HSS_PREC_BF16X3 ? 6.0 : 8.0) * n * (double)n;
+  H->st.bytes_sample += 2.0 * (abytes + 2.0 * 8.0 * n * (double)w);
   CK(cudaMemsetAsync(H->d_flag, 0, sizeof(int), st));
   CK(launch_nonfinite(H->Sg_r, H->dmax, n, c0, c1, H->d_flag, st));
   CK(launch_nonfinite(H->Sg_c, H->dmax, n, c0, c1, H->d_flag, st));
   H->launches += 2;
-  CKS(readback(H, H->d_flag, sizeof(int), st));
+  CKS(readback(H, H->d_flag, 2 * sizeof(int), st));
+  if (H->o.precision != HSS_PREC_FP64 && H->h_pinned[1])
+    return fail(HSS_ERR_TIMEOUT, "tensor-core sampling gave up waiting (code %d)", H->h_pinned[1]);
   if (H->h_pinned[0]) return fail(HSS_ERR_NONFINITE, "NaN or Inf in the random samples (columns %d..%d)", c0, c1);
   return HSS_OK;
 }
@@ -454,6 +511,10 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     Side& s = q.side ? H->nodes[q.node].c : H->nodes[q.node].r;
     need += Scratch::rnd(sizeof(double) * (size_t)d * std::max(s.m, 1)) +
             Scratch::rnd(sizeof(double) * 2 * std::max(s.m, 1)) + Scratch::rnd(3 * sizeof(int));
+    // group form: barrier, partial maxima, broadcast words (at most one CTA per 8 rows)
+    const size_t pmax = (size_t)std::max(1, s.m / 8);
+    need += Scratch::rnd(sizeof(unsigned)) + Scratch::rnd(sizeof(double) * pmax) +
+            Scratch::rnd(sizeof(int) * pmax) + 2 * Scratch::rnd(32);
   }
   CK(H->scratch.ensure(need, st));
   std::vector<QrcpJob> jobs;
@@ -482,16 +543,83 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   for (size_t i = 0; i < jobs.size(); ++i) jobs[i].out = outs + 3 * i;
   if (jobs.empty()) return HSS_OK;
   CK(H->timer.mark(PH_ID, st));
-  QrcpJob* dj;
-  CKS(upload_jobs(H, jobs, &dj, st));
-  CK(launch_qrcp(dj, (int)jobs.size(), st));
-  H->launches++;
-  CK(cudaFreeAsync(dj, st));
+  // Few node sides (upper tree levels): a group of CTAs per job in one
+  // cooperative launch, sized by the job's work m d min(m, d).
+  if (H->qrcp_cap < 0) H->qrcp_cap = qrcp_group_capacity();
+  const int cap = H->qrcp_cap;
+  const size_t nj = jobs.size();
+  std::vector<int> P(nj, 1);
+  bool group = cap > 0 && (int)nj * 2 <= cap;
+  if (group) {
+    double tot = 0.0;
+    std::vector<double> wk(nj);
+    for (size_t i = 0; i < nj; ++i) {
+      wk[i] = (double)jobs[i].m * jobs[i].d * std::min(jobs[i].m, jobs[i].d) + 1.0;
+      tot += wk[i];
+    }
+    int used = 0;
+    for (size_t i = 0; i < nj; ++i) {
+      int p = (int)std::floor(cap * wk[i] / tot);
+      p = std::max(1, std::min(p, std::max(1, jobs[i].m / 8)));
+      P[i] = p;
+      used += p;
+    }
+    while (used > cap) {   // trim the largest groups
+      size_t b = 0;
+      for (size_t i = 1; i < nj; ++i) if (P[i] > P[b]) b = i;
+      if (P[b] == 1) break;
+      P[b]--;
+      used--;
+    }
+    int maxp = 0;
+    for (int p : P) maxp = std::max(maxp, p);
+    group = used <= cap && maxp > 1;
+  }
+  if (group) {
+    unsigned* bars = (unsigned*)H->scratch.take(sizeof(unsigned) * nj);
+    std::vector<int2> map;
+    for (size_t i = 0; i < nj; ++i) {
+      jobs[i].P = P[i];
+      jobs[i].bar = bars + i;
+      jobs[i].redv = (double*)H->scratch.take(sizeof(double) * P[i]);
+      jobs[i].redi = (int*)H->scratch.take(sizeof(int) * P[i]);
+      jobs[i].bcd = (double*)H->scratch.take(sizeof(double) * 4);
+      jobs[i].bci = (int*)H->scratch.take(sizeof(int) * 4);
+      for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
+    }
+    CK(cudaMemsetAsync(bars, 0, sizeof(unsigned) * nj, st));
+    CK(cudaMemsetAsync(H->d_flag + 2, 0, sizeof(int), st));
+    QrcpJob* dj;
+    int2* dm;
+    CKS(upload_jobs(H, jobs, &dj, st));
+    CKS(upload_jobs(H, map, &dm, st));
+    if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
+    CK(launch_qrcp_group(dj, dm, (int)map.size(), H->d_flag + 2, st));
+    H->launches++;
+    CK(cudaFreeAsync(dj, st));
+    CK(cudaFreeAsync(dm, st));
+    CKS(readback(H, H->d_flag + 2, sizeof(int), st));
+    if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "group QRCP barrier gave up (code %d)", H->h_pinned[0]);
+  } else {
+    QrcpJob* dj;
+    CKS(upload_jobs(H, jobs, &dj, st));
+    if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
+    CK(launch_qrcp(dj, (int)jobs.size(), st));
+    H->launches++;
+    CK(cudaFreeAsync(dj, st));
+  }
   CKS(readback(H, outs, sizeof(int) * 3 * jobs.size(), st));
   for (size_t i = 0; i < reqs.size(); ++i) {
     Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
     s.qr_k = H->h_pinned[3 * i];
     s.qr_acc = H->h_pinned[3 * i + 2];
+    // algorithmic flops: norms, k Householder steps (reflector + trailing
+    // dot and update of m-j-1 columns), back substitution for X
+    const double m = jobs[i].m, dd = jobs[i].d, k = s.qr_k;
+    double f = 2.0 * m * dd;
+    for (int j = 0; j < s.qr_k; ++j) f += 4.0 * (dd - j) * (m - j - 1) + 3.0 * (dd - j);
+    if (s.qr_acc && k > 0 && m > k) f += k * k * (m - k);
+    H->st.flop_id += f;
   }
   return HSS_OK;
 }
@@ -674,6 +802,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         }
         IncJob* dj;
         CKS(upload_jobs(H, ij, &dj, st));
+        if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "test scratch sized too small");
         CK(launch_inc_qr(dj, (int)ij.size(), st));
         H->launches++;
         CK(cudaFreeAsync(dj, st));
@@ -805,7 +934,6 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     return fail(HSS_ERR_NOMEM, "device allocation of %zu bytes for samples failed", 3 * nd * 8);
   CKS(upload(H, H->leaf_id, lid.data(), sizeof(int) * n, st));
   CKS(upload(H, H->iota, io.data(), sizeof(int) * n, st));
-  if (mixed && o->R) return fail(HSS_ERR_UNSUPPORTED, "caller R with mixed precision is not supported");
 
   CK(H->timer.mark(PH_OTHER, st));
   int d = std::min(o->d0, H->dmax), d_prev = 0;
@@ -822,6 +950,10 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     H->n_adapt++;
   }
   CK(H->timer.mark(PH_OTHER, st));
+  if (H->packA) {
+    CK(cudaFreeAsync(H->packA, st));
+    H->packA = nullptr;
+  }
   CK(cudaStreamSynchronize(st));
   H->d_final = d;
   H->usable = H->converged != 0;
@@ -1117,8 +1249,8 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
   const int n = A->n;
   if (leaf < 1 || ncols < 0 || !R || ldr < n || lds < ncols)
     return fail(HSS_ERR_ARG, "bad arguments to hss_sample_offdiag");
-  if (precision != HSS_PREC_FP64)
-    return fail(HSS_ERR_UNSUPPORTED, "mixed-precision sampling is not built in this library");
+  if (precision < HSS_PREC_FP64 || precision > HSS_PREC_BF16X3)
+    return fail(HSS_ERR_ARG, "unknown precision %d", precision);
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<Node> nodes;
   build_tree(n, leaf, nodes);
@@ -1133,8 +1265,47 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
   CK(cudaMallocAsync((void**)&d_lid, sizeof(int) * n, st));
   CK(cudaMemcpyAsync(d_lid, lid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   SrcDev s = make_src(*A, d_lid);
-  CK(launch_sample_fp64(s, ncols, R, ldr, Sr, Sc, lds, st));
+  if (precision == HSS_PREC_FP64) {
+    CK(launch_sample_fp64(s, ncols, R, ldr, Sr, Sc, lds, st));
+    CK(cudaFreeAsync(d_lid, st));
+    return HSS_OK;
+  }
+  // mixed forms: R rounded once to the tensor format, K split with atomics
+  double* Rr = nullptr;
+  int* err = nullptr;
+  CK(cudaMallocAsync((void**)&Rr, sizeof(double) * (size_t)n * std::max(ncols, 1), st));
+  CK(cudaMallocAsync((void**)&err, sizeof(int), st));
+  CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  CK(launch_round_copy(R, ldr, Rr, n, n, ncols, precision == HSS_PREC_TF32X2 ? 1 : 2, st));
+  void* pA = nullptr;
+  void* pR = nullptr;
+  const bool packed = A->kind == HSS_SRC_DENSE;
+  if (packed) {
+    CK(cudaMallocAsync(&pA, packed_a_bytes(n, precision), st));
+    CK(cudaMallocAsync(&pR, packed_r_bytes(n, ncols, precision), st));
+    CK(launch_pack_a(s, leaf, precision, pA, st));
+    CK(launch_pack_r(Rr, n, n, ncols, precision, pR, st));
+  }
+  for (int side = 0; side < 2; ++side) {
+    double* S = side ? Sc : Sr;
+    if (!S) continue;
+    const int ks = packed ? sample_tc_packed_ksplit(n, ncols, precision) : sample_tc_ksplit(n, ncols, precision);
+    if (ks > 1) CK(cudaMemset2DAsync(S, sizeof(double) * lds, 0, sizeof(double) * ncols, n, st));
+    int at = 0;
+    if (packed) CK(launch_sample_tc_packed(pA, pR, n, ncols, precision, side, S, lds, err, st));
+    else CK(launch_sample_tc(s, leaf, precision, side, ncols, Rr, n, S, lds, err, &at, st));
+  }
+  if (packed) {
+    CK(cudaFreeAsync(pA, st));
+    CK(cudaFreeAsync(pR, st));
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaFreeAsync(Rr, st));
+  CK(cudaFreeAsync(err, st));
   CK(cudaFreeAsync(d_lid, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) return fail(HSS_ERR_TIMEOUT, "tensor-core sampling gave up waiting (code %d)", herr);
   return HSS_OK;
 }
 

@@ -89,6 +89,13 @@ struct QrcpJob {
   int do_id;
   double er, ea;
   int* out;             // out[0] = k, out[1] = stopped, out[2] = accepted
+  // group (multi-CTA) form only
+  int P;                // CTAs working on this job
+  unsigned* bar;        // group barrier counter, zero before the launch
+  double* redv;         // P partial maxima
+  int* redi;            // P partial argmax indices
+  double* bcd;          // broadcast: [0] tau, [3] |R_11|
+  int* bci;             // broadcast: [0] stop flag
 };
 
 // One Incrementing block test on one side of a node (Algorithm 5):
@@ -122,11 +129,35 @@ cudaError_t launch_random_normal(unsigned long long seed, int n, int col0, int n
                                  double* R, long long ldr, int round_mode, cudaStream_t st);
 cudaError_t launch_sample_fp64(const SrcDev& src, int ncols, const double* R, long long ldr,
                                double* Sr, double* Sc, long long lds, cudaStream_t st);
+// tcgen05 mixed-precision sampling (k_sample_tc.cu); *used_atomic tells
+// whether S had to be zeroed beforehand (K split across CTAs).
+cudaError_t launch_sample_tc(const SrcDev& src, int leaf, int precision, int trans, int ncols,
+                             const double* R, long long ldr, double* S, long long lds, int* err,
+                             int* used_atomic, cudaStream_t st);
+int sample_tc_ksplit(int n, int ncols, int precision);
+// packed form for a dense A: operands split once into canonical tiles in
+// global memory, the main loop fed by bulk copies (k_sample_tc.cu)
+size_t packed_a_bytes(int n, int precision);
+size_t packed_r_bytes(int n, int ncols, int precision);
+cudaError_t launch_pack_a(const SrcDev& src, int leaf, int precision, void* out, cudaStream_t st);
+cudaError_t launch_pack_r(const double* R, long long ldr, int n, int ncols, int precision, void* out,
+                          cudaStream_t st);
+int sample_tc_packed_ksplit(int n, int ncols, int precision);
+cudaError_t launch_sample_tc_packed(const void* A, const void* Rp, int n, int ncols, int precision,
+                                    int trans, double* S, long long lds, int* err, cudaStream_t st);
+// out(:, c) = R rounded to the significand of the mixed format (mode 1: 11
+// bits, TF32; mode 2: 8 bits, BF16)
+cudaError_t launch_round_copy(const double* in, long long ldin, double* out, long long ldout, int n,
+                              int ncols, int mode, cudaStream_t st);
 cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int njobs,
                            int max_tiles, cudaStream_t st);
 cudaError_t launch_gemm(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles,
                         cudaStream_t st);
 cudaError_t launch_qrcp(const QrcpJob* jobs_dev, int njobs, cudaStream_t st);
+// cooperative form: map[cta] = (job, rank within the job's group)
+int qrcp_group_capacity();
+cudaError_t launch_qrcp_group(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int* err,
+                              cudaStream_t st);
 cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
 cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int c1,
                              int* flag, cudaStream_t st);

@@ -6,6 +6,8 @@
 // R(i, c) uses counter (i >> 1, c, 0, 0); words (w0, w1) and (w2, w3) give
 // two 53-bit uniforms; Box-Muller turns them into the pair used by rows
 // 2p (cosine branch) and 2p + 1 (sine branch).
+#include <algorithm>
+
 #include "hss_internal.h"
 
 namespace hss {
@@ -57,7 +59,28 @@ __global__ void k_random_normal(unsigned long long seed, int n, int col0, int nc
   }
 }
 
+__global__ void k_round_copy(const double* in, long long ldin, double* out, long long ldout, int n,
+                             int ncols, int mode) {
+  long long total = (long long)n * ncols;
+  const int bits = mode == 1 ? 11 : 8;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % n);
+    long long c = t / n;
+    out[i + c * ldout] = round_sig(in[i + c * ldin], bits);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_round_copy(const double* in, long long ldin, double* out, long long ldout, int n,
+                              int ncols, int mode, cudaStream_t st) {
+  if (n <= 0 || ncols <= 0) return cudaSuccess;
+  long long total = (long long)n * ncols;
+  int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
+  k_round_copy<<<blocks, 256, 0, st>>>(in, ldin, out, ldout, n, ncols, mode);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_random_normal(unsigned long long seed, int n, int col0, int ncols,
                                  double* R, long long ldr, int round_mode, cudaStream_t st) {

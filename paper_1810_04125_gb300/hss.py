@@ -48,7 +48,7 @@ class hss_stats(C.Structure):
                 ("ms_merge", C.c_double), ("flop_sample", C.c_double),
                 ("bytes_sample", C.c_double), ("launches", C.c_longlong),
                 ("sample_launches", C.c_longlong), ("bytes_h2d", C.c_longlong),
-                ("bytes_d2h", C.c_longlong)]
+                ("bytes_d2h", C.c_longlong), ("flop_id", C.c_double)]
 
 
 class hss_node_info(C.Structure):

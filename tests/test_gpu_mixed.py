@@ -1,0 +1,124 @@
+"""Mixed-precision sampling (tcgen05 TF32x2 / BF16x3) against the FP64
+oracle on the same R rounded to the tensor format (reading P10).
+
+Tolerance, from the arithmetic of the split: an entry a is rounded once to
+FP32 (2^-24 |a|) and split into terms that keep 22 (TF32x2) or 24 (BF16x3)
+significant bits, so each product a r carries a relative error below
+2^-21; the FP32 accumulation of K terms adds at most K 2^-24 of the sum of
+|a r| (a bound never approached: the observed error is ~sqrt(K) times
+smaller).  Element-wise the test allows 2^-21 + K 2^-24 relative to
+(|A_off| |R|); in the Frobenius norm it requires 2e-6 of ||S||."""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import apply, hss as ohss, tree as otree
+from oracle.hss import Options, compress
+
+import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1810_04125_gb300 import build
+    build.build()
+    return _t
+
+
+@pytest.fixture(scope="module")
+def hss(torch):
+    from paper_1810_04125_gb300 import hss as h
+    return h
+
+
+def _rcb(P, leaf):
+    return P[otree.rcb_order(P, leaf)]
+
+
+ROUND = {"tf32x2": w.round_to_tf32, "bf16x3": w.round_to_bf16}
+SOURCES = [
+    ("dense", lambda: w.dense_source(np.random.default_rng(4).standard_normal((700, 700))), 64, 70),
+    ("toeplitz", lambda: w.toeplitz_inverse_distance(1000), 64, 128),
+    ("toeplitz_cos", lambda: w.toeplitz_cos(1500), 100, 200),
+    ("gauss", lambda: w.gaussian_kernel(_rcb(w.uniform_points(1200, 8, seed=2), 128), 1.0, 1.0), 128, 40),
+    ("laplace", lambda: w.laplace_kernel(_rcb(w.fibonacci_sphere(1300), 100)), 100, 8),
+]
+
+
+@pytest.mark.parametrize("prec", ["tf32x2", "bf16x3"])
+@pytest.mark.parametrize("name,mk,leaf,nc", SOURCES, ids=[s[0] for s in SOURCES])
+def test_sample_offdiag_mixed(hss, torch, prec, name, mk, leaf, nc):
+    src = mk()
+    n = src.n
+    R = ROUND[prec](w.gaussian_matrix(3, n, 0, nc))
+    Sr = torch.full((n, nc), float("nan"), dtype=torch.float64, device=gu.dev())
+    Sc = torch.full((n, nc), float("nan"), dtype=torch.float64, device=gu.dev())
+    hss.hss_sample_offdiag(gu.device_source(src), leaf, gu.PREC[prec], gu.col_major(R), Sr, Sc)
+    torch.cuda.synchronize()
+    smp = ohss._Sampler(src)
+    er, ec = smp.sample(R)
+    A = src.to_dense()
+    absA = np.abs(A).copy()
+    for t in otree.halving_tree(n, leaf):
+        if t.is_leaf:
+            I = t.I
+            D = smp.entries(I, I)
+            er[I] -= D @ R[I]
+            ec[I] -= D.T @ R[I]
+            absA[np.ix_(I, I)] = 0.0
+    rel = 2.0 ** -21 + n * 2.0 ** -24
+    for got, ref, bnd in ((Sr, er, absA @ np.abs(R)), (Sc, ec, absA.T @ np.abs(R))):
+        g = got.cpu().numpy()
+        assert np.all(np.isfinite(g))
+        assert np.all(np.abs(g - ref) <= rel * bnd + 1e-300)
+        assert np.linalg.norm(g - ref) <= 2e-6 * np.linalg.norm(ref)
+
+
+MIXED_CASES = [
+    ("gauss8_2048_dbl_tf32", "tf32x2",
+     lambda: w.gaussian_kernel(_rcb(w.uniform_points(2048, 8, 0), 128), 1.0, 1.0),
+     Options(leaf=128, rtol=1e-4, atol=1e-8, d0=64, dd=64, d_max=2048, strategy="doubling")),
+    ("laplace2048_inc_bf16", "bf16x3",
+     lambda: w.laplace_kernel(_rcb(w.fibonacci_sphere(2048), 128)),
+     Options(leaf=128, rtol=1e-6, atol=1e-8, d0=64, dd=32, d_max=2048)),
+    ("toeplitzcos4096_inc_tf32", "tf32x2", lambda: w.toeplitz_cos(4096),
+     Options(leaf=256, rtol=1e-4, atol=1e-10, d0=128, dd=64, d_max=1024)),
+    ("toeplitz1024_inc_bf16", "bf16x3", lambda: w.toeplitz_inverse_distance(1024),
+     Options(leaf=64, rtol=1e-6, atol=1e-12, d0=64, dd=32, d_max=1024)),
+]
+
+
+@pytest.mark.parametrize("name,prec,mk,o", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_compress_mixed_parity(hss, torch, name, prec, mk, o):
+    src = mk()
+    n = src.n
+    R = ROUND[prec](w.gaussian_matrix(7, n, 0, o.d_max))
+    ref = compress(src, R, o)
+    H = gu.gpu_compress(src, R, o, precision=prec)
+    st = H.stats()
+    assert st.converged == 1 and ref.converged
+    assert st.d_final == ref.d_final
+    bad = gu.compare_with_oracle(H, ref, o, n)
+    assert not bad, bad
+    A = src.to_dense()
+    err_g = gu.rel_err(A, gu.gpu_dense(H, n))
+    err_o = apply.rel_error(ref, A)
+    assert err_g <= 1.1 * err_o + 1e-15, (err_g, err_o)
+
+
+def test_mixed_device_R_is_rounded(hss, torch):
+    """Without a caller R the library draws Philox values already rounded to
+    the tensor format, so the FP64 steps and the tensor cores see one R."""
+    src = w.toeplitz_inverse_distance(1024)
+    o = Options(leaf=64, rtol=1e-6, atol=1e-12, d0=64, dd=32, d_max=1024)
+    R = w.round_to_tf32(w.gaussian_matrix(11, 1024, 0, 1024))
+    ref = compress(src, R, o)
+    H = gu.gpu_compress(src, R, o, precision="tf32x2", pass_R=False, seed=11)
+    assert not gu.compare_with_oracle(H, ref, o, 1024)
+    A = src.to_dense()
+    assert gu.rel_err(A, gu.gpu_dense(H, 1024)) <= 1.1 * apply.rel_error(ref, A) + 1e-15

@@ -111,6 +111,10 @@ def _cases():
               Options(leaf=256, rtol=1e-4, atol=1e-10, d0=128, dd=64, d_max=1024)))
     c.append(("udv1000_ragged_inc", lambda: w.dense_source(w.udv_matrix(1000, 60, seed=3)),
               Options(leaf=64, rtol=1e-8, atol=1e-14, d0=32, dd=16, d_max=1000)))
+    # 256 leaves: the leaf level has more node sides than SMs (one CTA per
+    # node side), the upper levels use CTA groups
+    c.append(("toeplitz4096_leaf16_dbl", lambda: w.toeplitz_power(4096, 1.5),
+              Options(leaf=16, rtol=1e-8, atol=1e-14, d0=32, dd=32, d_max=1024, strategy="doubling")))
     return c
 
 
