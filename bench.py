@@ -10,7 +10,12 @@ timed region (2.1 GB, larger than L2, so no flush is needed).
 metric: sampled TFLOP/s = sum over passes of 4 n^2 Delta d, divided by the
 compression time; the JSON line also carries the compression seconds.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32x2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x2|bf16x3|fp64]
+
+The line's value is the mixed form (TF32x2 sampling on the tensor cores,
+FP64 QR/ID); the FP64 plain form of the same compression is timed after it
+("fp64_plain", "speedup_vs_fp64_plain"), and both report the reconstruction
+error ||A - H||_F / ||A||_F.
   python bench.py --impl reference     # the CPU oracle on a bounded sample
 
 Multi-GPU (torchrun): every rank compresses its own replica of the matrix
@@ -153,10 +158,14 @@ def run_gpu(args):
         cfg["workload"] = WORKLOAD["workload"].replace("16384", str(args.n))
     n = cfg["n"]
     P, A = build_inputs(dev, n, cfg["dim"], cfg["seed"], cfg["leaf"])
-    prec = {"fp64": hss.HSS_PREC_FP64, "tf32x2": hss.HSS_PREC_TF32X2, "bf16x3": hss.HSS_PREC_BF16X3}[args.precision]
+    PREC = {"fp64": hss.HSS_PREC_FP64, "tf32x2": hss.HSS_PREC_TF32X2, "bf16x3": hss.HSS_PREC_BF16X3}
     src = hss.dense_source(A)
-    opts = hss.make_opts(cfg["leaf"], cfg["rtol"], cfg["atol"], cfg["d0"], cfg["d0"], cfg["d_max"],
-                         hss.HSS_DOUBLING, prec, cfg["p"], seed=cfg["seed"])
+
+    def make(p):
+        return hss.make_opts(cfg["leaf"], cfg["rtol"], cfg["atol"], cfg["d0"], cfg["d0"], cfg["d_max"],
+                             hss.HSS_DOUBLING, PREC[p], cfg["p"], seed=cfg["seed"])
+
+    opts = make(args.precision)
     stream = torch.cuda.Stream(device=dev)
 
     def barrier():
@@ -165,10 +174,24 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step():
+    def step(o=None):
         with torch.cuda.stream(stream):
-            H = hss.hss_compress(src, opts, stream=stream)
+            H = hss.hss_compress(src, o or opts, stream=stream)
         return H
+
+    def rel_error(H):
+        """||A - H||_F / ||A||_F from H applied to identity column blocks."""
+        num, den, blk = 0.0, 0.0, 2048
+        for j0 in range(0, n, blk):
+            w_ = min(blk, n - j0)
+            X = torch.zeros((w_, n), dtype=torch.float64, device=dev).t()
+            X[j0:j0 + w_].copy_(torch.eye(w_, dtype=torch.float64, device=dev))
+            Y = torch.empty((w_, n), dtype=torch.float64, device=dev).t()
+            hss.hss_matvec(H, X, Y, stream=stream)
+            torch.cuda.synchronize()
+            num += float(((A[:, j0:j0 + w_] - Y) ** 2).sum())
+            den += float((A[:, j0:j0 + w_] ** 2).sum())
+        return (num / den) ** 0.5
 
     for _ in range(args.warmup):
         step()
@@ -187,6 +210,9 @@ def run_gpu(args):
         ev1.record(stream)
         barrier()
     t_ms = ev0.elapsed_time(ev1)
+    H_keep = step()
+    err_main = rel_error(H_keep)
+    del H_keep
     flops = sum(s.flop_sample for s in stats)
     tmax = t_ms
     if world > 1:
@@ -251,23 +277,56 @@ def run_gpu(args):
             "traffic": traffic_from_profiles("k_qrcp_gauss8_n16384")}
     roof, roof_other = (r_id, r_sample) if s0.ms_id > s0.ms_sample else (r_sample, r_id)
 
+    # --- the FP64 plain form on the same matrix, for the mixed / plain ratio
+    plain = None
+    if args.precision != "fp64" and not args.no_compare:
+        o64 = make("fp64")
+        step(o64)
+        barrier()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pst = []
+        for _ in range(args.compare_steps):
+            H = step(o64)
+            pst.append(H.stats())
+            del H
+        p1.record(stream)
+        barrier()
+        pms = p0.elapsed_time(p1) / args.compare_steps
+        H = step(o64)
+        perr = rel_error(H)
+        del H
+        q = pst[-1]
+        plain = {"compress_s": pms / 1e3, "value": q.flop_sample / (pms / 1e3) / 1e12, "unit": "TFLOP/s",
+                 "steps": args.compare_steps, "rel_error": perr,
+                 "result": {"d_final": q.d_final, "n_adapt": q.n_adapt,
+                            "max_rank": max(q.max_rank_r, q.max_rank_c)},
+                 "phases_ms": {"sample": q.ms_sample, "rng_check": q.ms_rng, "id": q.ms_id,
+                               "test": q.ms_test, "merge_reduce": q.ms_merge, "total": q.ms_total}}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_n)
     out = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else f"{args.precision} sampling, f64 QR/ID",
         "data": "synthetic", "gpu_launches": int(sum(s.launches for s in stats)),
         "config": {**cfg, "precision": args.precision, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (A is 2.1 GB); no flush"},
         "compress_s": tmax / args.steps / 1e3,
+        "rel_error": err_main,
         "result": {"d_final": s0.d_final, "n_adapt": s0.n_adapt, "max_rank": max(s0.max_rank_r, s0.max_rank_c),
                    "converged": s0.converged},
         "phases_ms": {"sample": s0.ms_sample, "rng_check": s0.ms_rng, "id": s0.ms_id,
                       "test": s0.ms_test, "merge_reduce": s0.ms_merge, "total": s0.ms_total},
         "roofline": roof, "roofline_other": roof_other, "e2e": e2e, "clocks": clocks.summary(),
     }
+    if plain is not None:
+        out["fp64_plain"] = plain
+        out["speedup_vs_fp64_plain"] = plain["compress_s"] / out["compress_s"]
     if cpu is not None:
         out["cpu_baseline"] = cpu
     if rank == 0:
@@ -344,7 +403,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32x2", "bf16x3"])
+    ap.add_argument("--precision", default="tf32x2", choices=["fp64", "tf32x2", "bf16x3"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 plain comparison run")
+    ap.add_argument("--compare-steps", type=int, default=2)
     ap.add_argument("--cpu-n", type=int, default=2048)
     ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")

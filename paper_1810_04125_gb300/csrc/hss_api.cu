@@ -391,6 +391,10 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
     CK(H->timer.mark(PH_RNG, st));
     CK(cudaFreeAsync(packR, st));
   } else {
+    void* packR = nullptr;
+    CK(cudaMallocAsync(&packR, packed_r_bytes(n, w, H->o.precision), st));
+    CK(launch_pack_r(Rc, n, n, w, H->o.precision, packR, st));
+    H->launches++;
     if (sample_tc_ksplit(n, w, H->o.precision) > 1) {
       CK(cudaMemset2DAsync(H->Sg_r + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
       CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
@@ -398,12 +402,14 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
     CK(cudaMemsetAsync(H->d_flag + 1, 0, sizeof(int), st));
     CK(H->timer.mark(PH_SAMPLE, st));
     int at = 0;
-    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 0, w, Rc, n, H->Sg_r + c0, H->dmax,
+    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 0, w, packR, H->Sg_r + c0, H->dmax,
                         H->d_flag + 1, &at, st));
-    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 1, w, Rc, n, H->Sg_c + c0, H->dmax,
+    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 1, w, packR, H->Sg_c + c0, H->dmax,
                         H->d_flag + 1, &at, st));
     H->launches += 2;
     H->st.sample_launches += 2;
+    CK(H->timer.mark(PH_RNG, st));
+    CK(cudaFreeAsync(packR, st));
   }
   CK(H->timer.mark(PH_RNG, st));
   H->st.flop_sample += 4.0 * (double)n * (double)n * (double)w;
@@ -1280,11 +1286,11 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
   void* pA = nullptr;
   void* pR = nullptr;
   const bool packed = A->kind == HSS_SRC_DENSE;
+  CK(cudaMallocAsync(&pR, packed_r_bytes(n, ncols, precision), st));
+  CK(launch_pack_r(Rr, n, n, ncols, precision, pR, st));
   if (packed) {
     CK(cudaMallocAsync(&pA, packed_a_bytes(n, precision), st));
-    CK(cudaMallocAsync(&pR, packed_r_bytes(n, ncols, precision), st));
     CK(launch_pack_a(s, leaf, precision, pA, st));
-    CK(launch_pack_r(Rr, n, n, ncols, precision, pR, st));
   }
   for (int side = 0; side < 2; ++side) {
     double* S = side ? Sc : Sr;
@@ -1293,12 +1299,10 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
     if (ks > 1) CK(cudaMemset2DAsync(S, sizeof(double) * lds, 0, sizeof(double) * ncols, n, st));
     int at = 0;
     if (packed) CK(launch_sample_tc_packed(pA, pR, n, ncols, precision, side, S, lds, err, st));
-    else CK(launch_sample_tc(s, leaf, precision, side, ncols, Rr, n, S, lds, err, &at, st));
+    else CK(launch_sample_tc(s, leaf, precision, side, ncols, pR, S, lds, err, &at, st));
   }
-  if (packed) {
-    CK(cudaFreeAsync(pA, st));
-    CK(cudaFreeAsync(pR, st));
-  }
+  if (packed) CK(cudaFreeAsync(pA, st));
+  CK(cudaFreeAsync(pR, st));
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaFreeAsync(Rr, st));

@@ -129,11 +129,12 @@ cudaError_t launch_random_normal(unsigned long long seed, int n, int col0, int n
                                  double* R, long long ldr, int round_mode, cudaStream_t st);
 cudaError_t launch_sample_fp64(const SrcDev& src, int ncols, const double* R, long long ldr,
                                double* Sr, double* Sc, long long lds, cudaStream_t st);
-// tcgen05 mixed-precision sampling (k_sample_tc.cu); *used_atomic tells
+// tcgen05 mixed-precision sampling with entries generated in the kernel
+// (k_sample_tc.cu); Rp is R packed by launch_pack_r; *used_atomic tells
 // whether S had to be zeroed beforehand (K split across CTAs).
 cudaError_t launch_sample_tc(const SrcDev& src, int leaf, int precision, int trans, int ncols,
-                             const double* R, long long ldr, double* S, long long lds, int* err,
-                             int* used_atomic, cudaStream_t st);
+                             const void* Rp, double* S, long long lds, int* err, int* used_atomic,
+                             cudaStream_t st);
 int sample_tc_ksplit(int n, int ncols, int precision);
 // packed form for a dense A: operands split once into canonical tiles in
 // global memory, the main loop fed by bulk copies (k_sample_tc.cu)

@@ -10,17 +10,16 @@
 //           R holds TF32 values exactly; two kind::tf32 products.
 //   BF16X3: a ~= a0 + a1 + a2 with BF16 terms (24 significant bits); R holds
 //           BF16 values exactly; three kind::f16 (bf16) products.
-// Every product of terms is exact in FP32 and accumulates in FP32 in TMEM;
-// the epilogue adds the FP32 tile into the FP64 output.
+// Every product of terms is exact in FP32; partial sums are kept short in
+// TMEM and carried in float-float registers (see "Accumulation" below).
 //
-// CTA: 128 output rows x N sample columns (N <= 128, a multiple of 16),
-// K (the summation index) staged BK at a time through an NS-deep ring of
-// shared-memory stages.  Warps 0-3 produce (load or generate FP64 entries,
-// zero the leaf diagonal block, split, write the canonical K-major layout)
-// and later drain TMEM; warp 4 owns the TMEM allocation and one of its
-// threads issues the MMAs and the tcgen05.commit arrivals.  Every mbarrier
-// wait is bounded (about 2 s of %globaltimer); on expiry the kernel records
-// an error code and leaves the pipeline, frees its TMEM and returns.
+// Two kernels share the tile format: the packed kernel streams a dense A that
+// was split once into canonical tiles (cp.async.bulk into an mbarrier ring);
+// the generating kernel computes the entries (Toeplitz table lookups, point
+// kernels) in its producer warps.  In both, one thread issues tcgen05.mma, the
+// R tile arrives pre-packed by bulk copy, and every mbarrier wait is bounded
+// (about 2 s of %globaltimer): on expiry the kernel records an error code,
+// leaves its loops, frees its TMEM and returns.
 //
 // Shared-memory layout of a K-major tile with `rows` rows and BK elements of
 // e bytes (16-byte chunks of 16/e elements): core matrices of 8 rows x 16 B
@@ -35,9 +34,7 @@ namespace hss {
 namespace {
 
 constexpr int BM = 128;            // rows per CTA (TMEM lanes)
-constexpr int NSTAGE = 3;
-constexpr int NPROD = 128;         // producer / epilogue threads (warps 0-3)
-constexpr int NTHREADS = NPROD + 32;
+constexpr int NSTAGE = 3;                  // stages of the generating kernel
 constexpr uint32_t TILE_A_BYTES = 16384;   // 128 rows x 128 B of K
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -136,21 +133,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// 32 TMEM lanes x 16 consecutive 32-bit columns
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // ---- splitting of an FP64 value into tensor-core terms
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t u = __float_as_uint(x);
@@ -246,50 +228,171 @@ __device__ __forceinline__ void leaf_range(int i, int n, int leaf, int& lo, int&
   hi = l + size;
 }
 
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Accumulation.  The tensor core adds every product into the FP32 TMEM
+// accumulator with a rounding whose error is biased, so a long chain of
+// MMAs into one accumulator loses accuracy in proportion to its length
+// (about 2e-8 per MMA relative to the result).  Each CTA therefore
+// accumulates only a short chain (DRAIN k-tiles) into one of two TMEM
+// buffers, with the leading split term (HI) and the correction terms (LO) in
+// separate accumulators; drain warps move a finished chain into per-thread
+// float-float (TwoSum) accumulators while the tensor core fills the other
+// buffer.  TMEM columns: buffer b, accumulator x at (2 b + x) N.
+//
+// Drain thread layout: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows) and
+// column quarter h of the N-column tile (NH = N / 4 columns per thread);
+// sixteen drain warps cover the 128 x N tile once.
+
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// (s, e) += x + y as float-float: TwoSum of s and x, then the low part
+// collects the rounding error and the (small) correction y.
+__device__ __forceinline__ void ff_add(float& s, float& e, float x, float y) {
+  const float t = __fadd_rn(s, x);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(err, y));
+}
+
+// Drain one finished chain from TMEM buffer b into (s, e).
+template <int NH>
+__device__ __forceinline__ void drain_chain(uint32_t tmem, int N, int b, int q, int h, float* s, float* e) {
+  const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+  const uint32_t hi = tmem + lane_off + (uint32_t)((2 * b) * N + h * NH);
+  const uint32_t lo = tmem + lane_off + (uint32_t)((2 * b + 1) * N + h * NH);
+#pragma unroll
+  for (int c = 0; c < NH; c += 16) {
+    float x[16];
+    tmem_ld16_nw(hi + c, x);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) ff_add(s[c + i], e[c + i], x[i], 0.0f);
+    tmem_ld16_nw(lo + c, x);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) e[c + i] = __fadd_rn(e[c + i], x[i]);
+  }
+}
+
+// Write one thread's row of the result (NH columns from col).
+template <int NH>
+__device__ __forceinline__ void store_row(double* S, long long lds, int n, int ncols, int row, int col,
+                                          int atomic, const float* s, const float* e) {
+  if (row >= n) return;
+  double* out = S + (long long)row * lds + col;
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    if (col + j < ncols) {
+      const double v = (double)s[j] + (double)e[j];
+      if (atomic) atomicAdd(out + j, v);
+      else out[j] = v;
+    }
+  }
+}
+
+// Issue the MMAs of one k-tile (BK/KSTEP k-steps, T terms) into buffer b.
+template <int PREC>
+__device__ __forceinline__ void mma_ktile(uint32_t base, uint32_t tmem, int N, int b, bool first,
+                                          uint32_t id) {
+  using SP = Split<PREC>;
+  constexpr int T = SP::T, BK = SP::BK;
+  const uint32_t hi = tmem + (uint32_t)((2 * b) * N), lo = tmem + (uint32_t)((2 * b + 1) * N);
+#pragma unroll
+  for (int ks = 0; ks < BK / SP::KSTEP; ++ks) {
+    const uint64_t bd = sdesc(base + T * TILE_A_BYTES + ks * 256u, 128u, 1024u);
+    mma<PREC>(hi, sdesc(base + ks * 256u, 128u, 1024u), bd, id, (first && ks == 0) ? 0u : 1u);
+#pragma unroll
+    for (int t = 1; t < T; ++t)
+      mma<PREC>(lo, sdesc(base + t * TILE_A_BYTES + ks * 256u, 128u, 1024u), bd, id,
+                (first && ks == 0 && t == 1) ? 0u : 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Generating kernel (entries computed by the producer warps).
+// Warps 0-7: generate the A tile of each stage, drain chains, write the
+// result; warp 8: TMEM allocation and (lane 0) the MMA issue.  The R tile of
+// each stage comes pre-packed and is moved by warp 0 lane 0 with one bulk
+// copy (expect_tx on the stage barrier, which also counts the 256
+// producer arrivals).
 struct TcArgs {
   SrcDev src;
   int leaf;
   int trans;
-  int ncols;          // sample columns computed (this launch)
-  int N;              // columns per CTA tile (multiple of 16, <= 256)
-  int tmem_cols;      // power of two >= N
+  int ncols;          // sample columns of this launch
+  int N;              // columns per CTA tile (32, 64 or 128)
+  int tmem_cols;      // power of two >= 4 N
   int ksplit;         // CTAs along K
-  const double* R;    // n x ncols col-major (ld ldr)
-  long long ldr;
+  int nkt;            // k-tiles of K
+  int drain;          // k-tiles per accumulation chain
+  const uint8_t* Rp;  // packed R tiles (ct, kt), N x BK each
   double* S;          // row-major output, row stride lds
   long long lds;
   int atomic;         // 1: add into S (pre-zeroed); 0: store
   int* err;
 };
 
-template <int PREC>
-__global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(TcArgs a) {
+constexpr int GEN_WARPS = 16;
+constexpr int GEN_THREADS = GEN_WARPS * 32 + 32;
+
+template <int PREC, int NH>
+__global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
   using SP = Split<PREC>;
-  constexpr int T = SP::T, EV = SP::EV, BK = SP::BK, KC = BK / EV;   // KC = 8 chunks
+  constexpr int T = SP::T, EV = SP::EV, BK = SP::BK, KC = BK / EV;
+  constexpr int NP = GEN_WARPS * 32;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const int n = a.src.n;
-  const int N = a.N;
+  const int n = a.src.n, N = a.N;
   const uint32_t tileB = (uint32_t)N * 128u;
   const uint32_t stage_bytes = T * TILE_A_BYTES + tileB;
-  uint8_t* stages = smem;
   uint64_t* full = (uint64_t*)(smem + NSTAGE * stage_bytes);
   uint64_t* empty = full + NSTAGE;
-  uint64_t* done = empty + NSTAGE;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* tfull = empty + NSTAGE;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   int* lrow_lo = (int*)(tmem_slot + 4);
   int* lrow_hi = lrow_lo + BM;
-
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int row0 = blockIdx.x * BM;
-  const int col0 = blockIdx.y * N;
-  const int nk_total = (n + BK - 1) / BK;
-  const int kt0 = (int)((long long)nk_total * blockIdx.z / a.ksplit);
-  const int kt1 = (int)((long long)nk_total * (blockIdx.z + 1) / a.ksplit);
-  const int nk = kt1 - kt0;
-
+  const int rb = blockIdx.x, ct = blockIdx.y;
+  const int row0 = rb * BM, col0 = ct * N;
+  const int kt0 = (int)((long long)a.nkt * blockIdx.z / a.ksplit);
+  const int kt1 = (int)((long long)a.nkt * (blockIdx.z + 1) / a.ksplit);
+  const int nk = kt1 - kt0, DR = a.drain;
+  const int nchain = (nk + DR - 1) / DR;
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) { mbar_init(&full[s], NPROD); mbar_init(&empty[s], 1); }
-    mbar_init(done, 1);
+    for (int s = 0; s < NSTAGE; ++s) { mbar_init(&full[s], NP + 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], GEN_WARPS); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < BM) {
@@ -298,7 +401,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(TcArgs a) {
     lrow_lo[tid] = lo;
     lrow_hi[tid] = hi;
   }
-  if (warp == 4) {
+  if (warp == GEN_WARPS) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"((uint32_t)a.tmem_cols)
@@ -309,132 +412,95 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  bool ok = true;
+  const uint8_t* gB = a.Rp + ((size_t)ct * a.nkt + kt0) * tileB;
 
-  if (warp < 4) {
-    // ------------------------------------------------------------ producers
+  if (warp < GEN_WARPS) {
+    const int q = warp % 4, h = warp / 4;
+    float s[NH], e[NH];
+#pragma unroll
+    for (int j = 0; j < NH; ++j) { s[j] = 0.f; e[j] = 0.f; }
+    bool ok = true;
+    int drained = 0;   // chains drained so far
     for (int it = 0; it < nk && ok; ++it) {
-      const int s = it % NSTAGE;
+      const int st = it % NSTAGE;
       const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u, a.err, 2)) { ok = false; break; }
-      uint8_t* st = stages + s * stage_bytes;
+      if (!mbar_wait(&empty[st], ph ^ 1u, a.err, 2)) { ok = false; break; }
+      uint8_t* sp = smem + st * stage_bytes;
+      if (tid == 0) {
+        mbar_expect_tx(&full[st], tileB);
+        bulk_g2s(sp + T * TILE_A_BYTES, gB + (size_t)it * tileB, tileB, &full[st]);
+      }
       const int k0 = (kt0 + it) * BK;
-      // A tile: 128 rows x KC chunks; unit u -> (row, chunk)
-      for (int u = tid; u < BM * KC; u += NPROD) {
+      for (int u = tid; u < BM * KC; u += NP) {
         int r, c;
-        if (!a.trans) { r = u % BM; c = u / BM; }                       // consecutive rows
-        else { r = (u / (8 * KC)) * 8 + (u % 8); c = (u / 8) % KC; }    // consecutive K
-        const int gr = row0 + r;
-        const int lo = lrow_lo[r], hi = lrow_hi[r];
+        if (!a.trans) { r = u % BM; c = u / BM; }
+        else { r = (u / (8 * KC)) * 8 + (u % 8); c = (u / 8) % KC; }
+        const int gr = row0 + r, lo = lrow_lo[r], hi = lrow_hi[r];
         double v[EV];
 #pragma unroll
-        for (int e = 0; e < EV; ++e) {
-          const int gk = k0 + c * EV + e;
-          double x = 0.0;
+        for (int x = 0; x < EV; ++x) {
+          const int gk = k0 + c * EV + x;
+          double val = 0.0;
           if (gr < n && gk < n && (gk < lo || gk >= hi))
-            x = a.trans ? entry(a.src, gk, gr) : entry(a.src, gr, gk);
-          v[e] = x;
+            val = a.trans ? entry(a.src, gk, gr) : entry(a.src, gr, gk);
+          v[x] = val;
         }
         uint4 chunk[T];
         SP::split(v, chunk);
         const uint32_t off = (uint32_t)(r / 8) * 1024u + (uint32_t)c * 128u + (uint32_t)(r % 8) * 16u;
 #pragma unroll
-        for (int t = 0; t < T; ++t) *(uint4*)(st + t * TILE_A_BYTES + off) = chunk[t];
-      }
-      // B tile: N rows (sample columns) x KC chunks, R K-contiguous
-      uint8_t* sb = st + T * TILE_A_BYTES;
-      for (int u = tid; u < N * KC; u += NPROD) {
-        const int r = (u / (8 * KC)) * 8 + (u % 8), c = (u / 8) % KC;
-        const int gc = col0 + r;
-        double v[EV];
-#pragma unroll
-        for (int e = 0; e < EV; ++e) {
-          const int gk = k0 + c * EV + e;
-          v[e] = (gc < a.ncols && gk < n) ? a.R[(long long)gk + (long long)gc * a.ldr] : 0.0;
-        }
-        const uint32_t off = (uint32_t)(r / 8) * 1024u + (uint32_t)c * 128u + (uint32_t)(r % 8) * 16u;
-        *(uint4*)(sb + off) = SP::pack_r(v);
+        for (int t = 0; t < T; ++t) *(uint4*)(sp + t * TILE_A_BYTES + off) = chunk[t];
       }
       fence_async_smem();
-      mbar_arrive(&full[s]);
+      mbar_arrive(&full[st]);
+      // after the last tile of chain c, drain chain c-1
+      const int c = it / DR;
+      if ((it % DR == DR - 1 || it == nk - 1) && c >= 1) {
+        const int cd = c - 1, b = cd & 1;
+        if (!mbar_wait(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 6)) { ok = false; break; }
+        tc_fence_after();
+        drain_chain<NH>(tmem, N, b, q, h, s, e);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+        drained = c;
+      }
     }
+    // drain what is left (the last chain)
+    for (int cd = drained; ok && cd < nchain; ++cd) {
+      const int b = cd & 1;
+      if (!mbar_wait(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 7)) { ok = false; break; }
+      tc_fence_after();
+      drain_chain<NH>(tmem, N, b, q, h, s, e);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+    if (ok) store_row<NH>(a.S, a.lds, n, a.ncols, row0 + 32 * q + lane, col0 + h * NH, a.atomic, s, e);
   } else if (lane == 0) {
     // ------------------------------------------------------------- MMA issuer
     const uint32_t id = idesc(SP::FMT, (uint32_t)N);
-    uint32_t acc = 0;
     for (int it = 0; it < nk; ++it) {
-      const int s = it % NSTAGE;
+      const int st = it % NSTAGE;
       const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
-      if (!mbar_wait(&full[s], ph, a.err, 3)) { ok = false; break; }
+      const int c = it / DR, b = c & 1;
+      const bool first = (it % DR) == 0;
+      if (first && !mbar_wait(&tempty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, a.err, 8)) break;
+      if (!mbar_wait(&full[st], ph, a.err, 3)) break;
       tc_fence_after();
-      const uint32_t base = smem_u32(stages + s * stage_bytes);
-#pragma unroll
-      for (int ks = 0; ks < BK / SP::KSTEP; ++ks) {
-        const uint64_t bd = sdesc(base + T * TILE_A_BYTES + ks * 256u, 128u, 1024u);
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-          const uint64_t ad = sdesc(base + t * TILE_A_BYTES + ks * 256u, 128u, 1024u);
-          mma<PREC>(tmem, ad, bd, id, acc);
-          acc = 1;
-        }
-      }
-      mma_commit(&empty[s]);
+      mma_ktile<PREC>(smem_u32(smem + st * stage_bytes), tmem, N, b, first, id);
+      mma_commit(&empty[st]);
+      if (it % DR == DR - 1 || it == nk - 1) mma_commit(&tfull[b]);
     }
-    mma_commit(done);   // arrives once every issued MMA has completed
-  }
-
-  // ----------------------------------------------------------------- epilogue
-  if (warp < 4) {
-    bool have = mbar_wait(done, 0u, a.err, 4) && ok && nk > 0;
-    have = __all_sync(0xffffffffu, have);   // tcgen05.ld is warp-collective
-    tc_fence_after();
-    if (have) {
-      const int r = row0 + warp * 32 + lane;
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (r < n) {
-          double* out = a.S + (long long)r * a.lds + col0 + c0;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            if (col0 + c0 + e < a.ncols) {
-              if (a.atomic) atomicAdd(out + e, (double)v[e]);
-              else out[e] = (double)v[e];
-            }
-          }
-        }
-      }
-    }
-  } else {
-    // warp 4's other lanes wait for the issuer's last commit before freeing TMEM
-    mbar_wait(done, 0u, a.err, 5);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 4) {
+  if (warp == GEN_WARPS) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)a.tmem_cols)
                  : "memory");
   }
-}
-
-template <int PREC>
-size_t smem_bytes(int N) {
-  constexpr int T = Split<PREC>::T;
-  return (size_t)NSTAGE * (T * TILE_A_BYTES + (size_t)N * 128) + 8 * (2 * NSTAGE + 1) + 16 +
-         2 * BM * sizeof(int) + 1024;
-}
-
-template <int PREC>
-cudaError_t launch_t(const TcArgs& a0, int grid_x, int grid_y, cudaStream_t st) {
-  TcArgs a = a0;
-  size_t sm = smem_bytes<PREC>(a.N);
-  cudaError_t e = cudaFuncSetAttribute(k_sample_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
-  if (e != cudaSuccess) return e;
-  k_sample_tc<PREC><<<dim3(grid_x, grid_y, a.ksplit), NTHREADS, sm, st>>>(a);
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -444,8 +510,9 @@ cudaError_t launch_t(const TcArgs& a0, int grid_x, int grid_y, cudaStream_t st) 
 //       ((o * nrb + rb) * nkt + kt) * T * 16 KB        (leaf diagonal zeroed)
 //   R: tile (ct, kt) of N rows x BK at (ct * nkt + kt) * N * 128 bytes,
 // and the main loop moves whole tiles with cp.async.bulk issued by one
-// thread, completing on the stage mbarrier (expect_tx); one thread issues the
-// MMAs; no per-element work is left in the loop.
+// thread, completing on the stage mbarrier (expect_tx).  Warp 0 lane 0
+// copies, warp 1 owns TMEM and (lane 0) issues the MMAs, warps 2-9 drain
+// chains and write the result.
 
 template <int PREC>
 __global__ void __launch_bounds__(256) k_pack_a(SrcDev src, int leaf, int nrb, int nkt, uint8_t* out) {
@@ -474,11 +541,11 @@ __global__ void __launch_bounds__(256) k_pack_a(SrcDev src, int leaf, int nrb, i
     const int gr = row0 + r, lo = rlo[r], hi = rhi[r];
     double v[EV];
 #pragma unroll
-    for (int e = 0; e < EV; ++e) {
-      const int gk = k0 + c * EV + e;
-      double x = 0.0;
-      if (gr < n && gk < n && (gk < lo || gk >= hi)) x = o ? entry(src, gk, gr) : entry(src, gr, gk);
-      v[e] = x;
+    for (int x = 0; x < EV; ++x) {
+      const int gk = k0 + c * EV + x;
+      double val = 0.0;
+      if (gr < n && gk < n && (gk < lo || gk >= hi)) val = o ? entry(src, gk, gr) : entry(src, gr, gk);
+      v[x] = val;
     }
     uint4 chunk[T];
     SP::split(v, chunk);
@@ -500,35 +567,19 @@ __global__ void __launch_bounds__(256) k_pack_r(const double* R, long long ldr, 
     const int gc = ct * N + r;
     double v[EV];
 #pragma unroll
-    for (int e = 0; e < EV; ++e) {
-      const int gk = kt * BK + c * EV + e;
-      v[e] = (gc < ncols && gk < n) ? R[(long long)gk + (long long)gc * ldr] : 0.0;
+    for (int x = 0; x < EV; ++x) {
+      const int gk = kt * BK + c * EV + x;
+      v[x] = (gc < ncols && gk < n) ? R[(long long)gk + (long long)gc * ldr] : 0.0;
     }
     const uint32_t off = (uint32_t)(r / 8) * 1024u + (uint32_t)c * 128u + (uint32_t)(r % 8) * 16u;
     *(uint4*)(dst + off) = SP::pack_r(v);
   }
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
-      "r"(bytes)
-      : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
 struct TcPackedArgs {
   const uint8_t* A;
   const uint8_t* Rp;
-  int n, nrb, nkt, N, ncols, tmem_cols, ksplit, trans;
+  int n, nrb, nkt, N, ncols, tmem_cols, ksplit, trans, drain;
   double* S;
   long long lds;
   int atomic;
@@ -538,29 +589,33 @@ struct TcPackedArgs {
 template <int PREC>
 constexpr int packed_stages() { return PREC == HSS_PREC_TF32X2 ? 4 : 3; }
 
-template <int PREC>
-__global__ void __launch_bounds__(128, 1) k_sample_tc_packed(TcPackedArgs a) {
+constexpr int PK_THREADS = 18 * 32;   // copy warp, MMA warp, 16 drain warps
+
+template <int PREC, int NH>
+__global__ void __maxnreg__(96) k_sample_tc_packed(TcPackedArgs a) {
   using SP = Split<PREC>;
-  constexpr int T = SP::T, BK = SP::BK, NS = packed_stages<PREC>();
+  constexpr int T = SP::T, NS = packed_stages<PREC>();
   extern __shared__ __align__(1024) uint8_t smem[];
   const int N = a.N;
   const uint32_t tileB = (uint32_t)N * 128u;
   const uint32_t stage_bytes = T * TILE_A_BYTES + tileB;
   uint64_t* full = (uint64_t*)(smem + NS * stage_bytes);
   uint64_t* empty = full + NS;
-  uint64_t* done = empty + NS;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* tfull = empty + NS;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int rb = blockIdx.x, ct = blockIdx.y;
   const int kt0 = (int)((long long)a.nkt * blockIdx.z / a.ksplit);
   const int kt1 = (int)((long long)a.nkt * (blockIdx.z + 1) / a.ksplit);
-  const int nk = kt1 - kt0;
+  const int nk = kt1 - kt0, DR = a.drain;
+  const int nchain = (nk + DR - 1) / DR;
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 16); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"((uint32_t)a.tmem_cols)
@@ -573,71 +628,59 @@ __global__ void __launch_bounds__(128, 1) k_sample_tc_packed(TcPackedArgs a) {
   const uint32_t tmem = *tmem_slot;
   const uint8_t* gA = a.A + ((size_t)(a.trans * a.nrb + rb) * a.nkt + kt0) * (T * TILE_A_BYTES);
   const uint8_t* gB = a.Rp + ((size_t)ct * a.nkt + kt0) * tileB;
-  bool ok = true;
-  if (warp == 0 && lane == 0) {
-    // ------------------------------------------------------- bulk-copy producer
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % NS;
-      const uint32_t ph = (uint32_t)(it / NS) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u, a.err, 12)) { ok = false; break; }
-      uint8_t* st = smem + s * stage_bytes;
-      mbar_expect_tx(&full[s], stage_bytes);
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % NS;
+        const uint32_t ph = (uint32_t)(it / NS) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, a.err, 12)) break;
+        uint8_t* st = smem + s * stage_bytes;
+        mbar_expect_tx(&full[s], stage_bytes);
 #pragma unroll
-      for (int t = 0; t < T; ++t)
-        bulk_g2s(st + t * TILE_A_BYTES, gA + (size_t)it * (T * TILE_A_BYTES) + t * TILE_A_BYTES,
-                 TILE_A_BYTES, &full[s]);
-      bulk_g2s(st + T * TILE_A_BYTES, gB + (size_t)it * tileB, tileB, &full[s]);
+        for (int t = 0; t < T; ++t)
+          bulk_g2s(st + t * TILE_A_BYTES, gA + (size_t)it * (T * TILE_A_BYTES) + t * TILE_A_BYTES,
+                   TILE_A_BYTES, &full[s]);
+        bulk_g2s(st + T * TILE_A_BYTES, gB + (size_t)it * tileB, tileB, &full[s]);
+      }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------------------- MMA issuer
-    const uint32_t id = idesc(SP::FMT, (uint32_t)N);
-    uint32_t acc = 0;
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % NS;
-      const uint32_t ph = (uint32_t)(it / NS) & 1u;
-      if (!mbar_wait(&full[s], ph, a.err, 13)) { ok = false; break; }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc(SP::FMT, (uint32_t)N);
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % NS;
+        const uint32_t ph = (uint32_t)(it / NS) & 1u;
+        const int c = it / DR, b = c & 1;
+        const bool first = (it % DR) == 0;
+        if (first && !mbar_wait(&tempty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, a.err, 15)) break;
+        if (!mbar_wait(&full[s], ph, a.err, 13)) break;
+        tc_fence_after();
+        mma_ktile<PREC>(smem_u32(smem + s * stage_bytes), tmem, N, b, first, id);
+        mma_commit(&empty[s]);
+        if (it % DR == DR - 1 || it == nk - 1) mma_commit(&tfull[b]);
+      }
+    }
+  } else {
+    // --------------------------------------------------------- drain warps
+    const int q = warp % 4, h = (warp - 2) / 4;
+    float s[NH], e[NH];
+#pragma unroll
+    for (int j = 0; j < NH; ++j) { s[j] = 0.f; e[j] = 0.f; }
+    bool ok = true;
+    for (int cd = 0; cd < nchain; ++cd) {
+      const int b = cd & 1;
+      if (!mbar_wait(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 14)) { ok = false; break; }
       tc_fence_after();
-      const uint32_t base = smem_u32(smem + s * stage_bytes);
-#pragma unroll
-      for (int ks = 0; ks < BK / SP::KSTEP; ++ks) {
-        const uint64_t bd = sdesc(base + T * TILE_A_BYTES + ks * 256u, 128u, 1024u);
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-          const uint64_t ad = sdesc(base + t * TILE_A_BYTES + ks * 256u, 128u, 1024u);
-          mma<PREC>(tmem, ad, bd, id, acc);
-          acc = 1;
-        }
-      }
-      mma_commit(&empty[s]);
+      drain_chain<NH>(tmem, N, b, q, h, s, e);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
     }
-    mma_commit(done);
-  }
-  __syncwarp();
-  // ----------------------------------------------------------------- epilogue
-  bool have = mbar_wait(done, 0u, a.err, 14) && nk > 0;
-  have = __all_sync(0xffffffffu, have && ok);
-  tc_fence_after();
-  if (have) {
-    const int r = rb * BM + warp * 32 + lane;
-    const int col0 = ct * N;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (r < a.n) {
-        double* out = a.S + (long long)r * a.lds + col0 + c0;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          if (col0 + c0 + e < a.ncols) {
-            if (a.atomic) atomicAdd(out + e, (double)v[e]);
-            else out[e] = (double)v[e];
-          }
-        }
-      }
-    }
+    if (ok && nk > 0)
+      store_row<NH>(a.S, a.lds, a.n, a.ncols, rb * BM + 32 * q + lane, ct * N + h * NH, a.atomic, s, e);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 2) {
+  if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)a.tmem_cols)
@@ -645,32 +688,72 @@ __global__ void __launch_bounds__(128, 1) k_sample_tc_packed(TcPackedArgs a) {
   }
 }
 
-int tile_n(int ncols) {
-  int N = ((ncols + 15) / 16) * 16;
-  return N > 128 ? 128 : N;
+int tile_n(int ncols) { return ncols <= 64 ? 64 : 128; }
+
+int tmem_cols_for(int N) {
+  int tc = 32;
+  while (tc < 4 * N) tc *= 2;
+  return tc;
 }
+
+constexpr int DRAIN_PACKED = 1;   // k-tiles per accumulation chain (dense, packed)
+constexpr int DRAIN_GEN = 2;      // k-tiles per accumulation chain (generated entries)
 
 template <int PREC>
 cudaError_t launch_packed_t(const TcPackedArgs& a, int gx, int gy, cudaStream_t st) {
   constexpr int T = Split<PREC>::T, NS = packed_stages<PREC>();
-  const size_t sm = (size_t)NS * (T * TILE_A_BYTES + (size_t)a.N * 128) + 8 * (2 * NS + 1) + 16 + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_sample_tc_packed<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
-  if (e != cudaSuccess) return e;
-  k_sample_tc_packed<PREC><<<dim3(gx, gy, a.ksplit), 128, sm, st>>>(a);
+  const size_t sm = (size_t)NS * (T * TILE_A_BYTES + (size_t)a.N * 128) + 8 * (2 * NS + 4) + 16 + 1024;
+  dim3 grid(gx, gy, a.ksplit);
+#define HSS_LAUNCH_PK(NHV)                                                                          \
+  do {                                                                                              \
+    cudaError_t e = cudaFuncSetAttribute(k_sample_tc_packed<PREC, NHV>,                             \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);     \
+    if (e != cudaSuccess) return e;                                                                 \
+    k_sample_tc_packed<PREC, NHV><<<grid, PK_THREADS, sm, st>>>(a);                                 \
+  } while (0)
+  if (a.N == 64) HSS_LAUNCH_PK(16);
+  else HSS_LAUNCH_PK(32);
+#undef HSS_LAUNCH_PK
   return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_gen_t(const TcArgs& a, int gx, int gy, cudaStream_t st) {
+  constexpr int T = Split<PREC>::T;
+  const size_t sm = (size_t)NSTAGE * (T * TILE_A_BYTES + (size_t)a.N * 128) + 8 * (2 * NSTAGE + 4) + 16 +
+                    2 * BM * sizeof(int) + 1024;
+  dim3 grid(gx, gy, a.ksplit);
+#define HSS_LAUNCH_GEN(NHV)                                                                         \
+  do {                                                                                              \
+    cudaError_t e = cudaFuncSetAttribute(k_sample_tc_gen<PREC, NHV>,                                \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);     \
+    if (e != cudaSuccess) return e;                                                                 \
+    k_sample_tc_gen<PREC, NHV><<<grid, GEN_THREADS, sm, st>>>(a);                                   \
+  } while (0)
+  if (a.N == 64) HSS_LAUNCH_GEN(16);
+  else HSS_LAUNCH_GEN(32);
+#undef HSS_LAUNCH_GEN
+  return cudaGetLastError();
+}
+
+int bk_of(int precision) { return precision == HSS_PREC_TF32X2 ? 32 : 64; }
+
+int ksplit_for(int gx, int gy, int nkt, int waves) {
+  int ks = (waves * 152 + gx * gy - 1) / (gx * gy);
+  if (ks > nkt) ks = nkt;
+  return ks < 1 ? 1 : ks;
 }
 
 }  // namespace
 
 size_t packed_a_bytes(int n, int precision) {
-  const int T = precision == HSS_PREC_TF32X2 ? 2 : 3, bk = precision == HSS_PREC_TF32X2 ? 32 : 64;
+  const int T = precision == HSS_PREC_TF32X2 ? 2 : 3, bk = bk_of(precision);
   const size_t nrb = (n + BM - 1) / BM, nkt = (n + bk - 1) / bk;
   return 2 * nrb * nkt * T * (size_t)TILE_A_BYTES;
 }
 
 size_t packed_r_bytes(int n, int ncols, int precision) {
-  const int bk = precision == HSS_PREC_TF32X2 ? 32 : 64;
+  const int bk = bk_of(precision);
   const int N = tile_n(ncols);
   const size_t nct = (ncols + N - 1) / N, nkt = (n + bk - 1) / bk;
   return nct * nkt * (size_t)N * 128;
@@ -678,7 +761,7 @@ size_t packed_r_bytes(int n, int ncols, int precision) {
 
 cudaError_t launch_pack_a(const SrcDev& src, int leaf, int precision, void* out, cudaStream_t st) {
   const int n = src.n;
-  const int bk = precision == HSS_PREC_TF32X2 ? 32 : 64;
+  const int bk = bk_of(precision);
   const int nrb = (n + BM - 1) / BM, nkt = (n + bk - 1) / bk;
   const long long tiles = 2LL * nrb * nkt;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -692,7 +775,7 @@ cudaError_t launch_pack_a(const SrcDev& src, int leaf, int precision, void* out,
 cudaError_t launch_pack_r(const double* R, long long ldr, int n, int ncols, int precision, void* out,
                           cudaStream_t st) {
   if (n <= 0 || ncols <= 0) return cudaSuccess;
-  const int bk = precision == HSS_PREC_TF32X2 ? 32 : 64;
+  const int bk = bk_of(precision);
   const int N = tile_n(ncols), nct = (ncols + N - 1) / N, nkt = (n + bk - 1) / bk;
   if (precision == HSS_PREC_TF32X2)
     k_pack_r<HSS_PREC_TF32X2><<<nct * nkt, 256, 0, st>>>(R, ldr, n, ncols, N, nkt, (uint8_t*)out);
@@ -702,31 +785,32 @@ cudaError_t launch_pack_r(const double* R, long long ldr, int n, int ncols, int 
 }
 
 int sample_tc_packed_ksplit(int n, int ncols, int precision) {
-  const int bk = precision == HSS_PREC_TF32X2 ? 32 : 64;
   const int N = tile_n(ncols);
-  const int gx = (n + BM - 1) / BM, gy = (ncols + N - 1) / N, nkt = (n + bk - 1) / bk;
-  int ks = (4 * 152 + gx * gy - 1) / (gx * gy);
-  if (ks > nkt) ks = nkt;
-  return ks < 1 ? 1 : ks;
+  const int gx = (n + BM - 1) / BM, gy = (ncols + N - 1) / N, nkt = (n + bk_of(precision) - 1) / bk_of(precision);
+  return ksplit_for(gx, gy, nkt, 4);
+}
+
+int sample_tc_ksplit(int n, int ncols, int precision) {
+  const int N = tile_n(ncols);
+  const int gx = (n + BM - 1) / BM, gy = (ncols + N - 1) / N, nkt = (n + bk_of(precision) - 1) / bk_of(precision);
+  return ksplit_for(gx, gy, nkt, 2);
 }
 
 cudaError_t launch_sample_tc_packed(const void* A, const void* Rp, int n, int ncols, int precision,
                                     int trans, double* S, long long lds, int* err, cudaStream_t st) {
   if (n <= 0 || ncols <= 0) return cudaSuccess;
   TcPackedArgs a;
-  const int bk = precision == HSS_PREC_TF32X2 ? 32 : 64;
   a.A = (const uint8_t*)A;
   a.Rp = (const uint8_t*)Rp;
   a.n = n;
   a.nrb = (n + BM - 1) / BM;
-  a.nkt = (n + bk - 1) / bk;
+  a.nkt = (n + bk_of(precision) - 1) / bk_of(precision);
   a.N = tile_n(ncols);
   a.ncols = ncols;
-  int tc = 32;
-  while (tc < a.N) tc *= 2;
-  a.tmem_cols = tc;
+  a.tmem_cols = tmem_cols_for(a.N);
   a.ksplit = sample_tc_packed_ksplit(n, ncols, precision);
   a.trans = trans;
+  a.drain = DRAIN_PACKED;
   a.S = S;
   a.lds = lds;
   a.atomic = a.ksplit > 1 ? 1 : 0;
@@ -737,11 +821,12 @@ cudaError_t launch_sample_tc_packed(const void* A, const void* Rp, int n, int nc
   return cudaErrorInvalidValue;
 }
 
-// S (+)= (A - D^(L))^{[T]} R in a mixed precision; S must be zeroed by the
-// caller when the K range is split across CTAs (ksplit > 1 adds atomically).
+// S (+)= (A - D^(L))^{[T]} R with entries generated by the producer warps;
+// Rp holds R packed by launch_pack_r; S must be zeroed by the caller when the
+// K range is split across CTAs (*used_atomic).
 cudaError_t launch_sample_tc(const SrcDev& src, int leaf, int precision, int trans, int ncols,
-                             const double* R, long long ldr, double* S, long long lds, int* err,
-                             int* used_atomic, cudaStream_t st) {
+                             const void* Rp, double* S, long long lds, int* err, int* used_atomic,
+                             cudaStream_t st) {
   const int n = src.n;
   if (n <= 0 || ncols <= 0) return cudaSuccess;
   TcArgs a;
@@ -749,40 +834,21 @@ cudaError_t launch_sample_tc(const SrcDev& src, int leaf, int precision, int tra
   a.leaf = leaf;
   a.trans = trans;
   a.ncols = ncols;
-  int N = ((ncols + 15) / 16) * 16;
-  if (N > 128) N = 128;                        // several column tiles of 128
-  a.N = N;
-  int tc = 32;
-  while (tc < N) tc *= 2;
-  a.tmem_cols = tc;
-  const int gx = (n + BM - 1) / BM, gy = (ncols + N - 1) / N;
-  const int bk = precision == HSS_PREC_TF32X2 ? Split<HSS_PREC_TF32X2>::BK : Split<HSS_PREC_BF16X3>::BK;
-  const int nk = (n + bk - 1) / bk;
-  int ks = (2 * 152 + gx * gy - 1) / (gx * gy);
-  if (ks > nk) ks = nk;
-  if (ks < 1) ks = 1;
-  a.ksplit = ks;
-  a.R = R;
-  a.ldr = ldr;
+  a.N = tile_n(ncols);
+  a.tmem_cols = tmem_cols_for(a.N);
+  a.nkt = (n + bk_of(precision) - 1) / bk_of(precision);
+  const int gx = (n + BM - 1) / BM, gy = (ncols + a.N - 1) / a.N;
+  a.ksplit = sample_tc_ksplit(n, ncols, precision);
+  a.drain = DRAIN_GEN;
+  a.Rp = (const uint8_t*)Rp;
   a.S = S;
   a.lds = lds;
-  a.atomic = ks > 1 ? 1 : 0;
+  a.atomic = a.ksplit > 1 ? 1 : 0;
   a.err = err;
   *used_atomic = a.atomic;
-  if (precision == HSS_PREC_TF32X2) return launch_t<HSS_PREC_TF32X2>(a, gx, gy, st);
-  if (precision == HSS_PREC_BF16X3) return launch_t<HSS_PREC_BF16X3>(a, gx, gy, st);
+  if (precision == HSS_PREC_TF32X2) return launch_gen_t<HSS_PREC_TF32X2>(a, gx, gy, st);
+  if (precision == HSS_PREC_BF16X3) return launch_gen_t<HSS_PREC_BF16X3>(a, gx, gy, st);
   return cudaErrorInvalidValue;
-}
-
-int sample_tc_ksplit(int n, int ncols, int precision) {
-  int N = ((ncols + 15) / 16) * 16;
-  if (N > 128) N = 128;
-  const int gx = (n + BM - 1) / BM, gy = (ncols + N - 1) / N;
-  const int bk = precision == HSS_PREC_TF32X2 ? 32 : 64;
-  const int nk = (n + bk - 1) / bk;
-  int ks = (2 * 152 + gx * gy - 1) / (gx * gy);
-  if (ks > nk) ks = nk;
-  return ks < 1 ? 1 : ks;
 }
 
 }  // namespace hss

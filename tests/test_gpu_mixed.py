@@ -5,9 +5,11 @@ Tolerance, from the arithmetic of the split: an entry a is rounded once to
 FP32 (2^-24 |a|) and split into terms that keep 22 (TF32x2) or 24 (BF16x3)
 significant bits, so each product a r carries a relative error below
 2^-21; the FP32 accumulation of K terms adds at most K 2^-24 of the sum of
-|a r| (a bound never approached: the observed error is ~sqrt(K) times
-smaller).  Element-wise the test allows 2^-21 + K 2^-24 relative to
-(|A_off| |R|); in the Frobenius norm it requires 2e-6 of ||S||."""
+|a r| (a bound never approached).  Element-wise the test allows
+2^-21 + K 2^-24 relative to (|A_off| |R|).  The kernels keep every TMEM
+accumulation chain to one or two k-tiles and carry the chains in float-float
+registers, so the observed error is ~1e-7 of ||S|| (measured: TF32x2
+1.0-1.7e-7, BF16x3 0.4-1.2e-7 at n = 8192-16384); the test requires 5e-7."""
 import numpy as np
 import pytest
 
@@ -76,7 +78,8 @@ def test_sample_offdiag_mixed(hss, torch, prec, name, mk, leaf, nc):
         g = got.cpu().numpy()
         assert np.all(np.isfinite(g))
         assert np.all(np.abs(g - ref) <= rel * bnd + 1e-300)
-        assert np.linalg.norm(g - ref) <= 2e-6 * np.linalg.norm(ref)
+        # short accumulation chains carried in float-float: ~1e-7 of ||S||
+        assert np.linalg.norm(g - ref) <= 5e-7 * np.linalg.norm(ref)
 
 
 MIXED_CASES = [
@@ -85,7 +88,7 @@ MIXED_CASES = [
      Options(leaf=128, rtol=1e-4, atol=1e-8, d0=64, dd=64, d_max=2048, strategy="doubling")),
     ("laplace2048_inc_bf16", "bf16x3",
      lambda: w.laplace_kernel(_rcb(w.fibonacci_sphere(2048), 128)),
-     Options(leaf=128, rtol=1e-6, atol=1e-8, d0=64, dd=32, d_max=2048)),
+     Options(leaf=128, rtol=1e-5, atol=1e-8, d0=64, dd=32, d_max=2048)),
     ("toeplitzcos4096_inc_tf32", "tf32x2", lambda: w.toeplitz_cos(4096),
      Options(leaf=256, rtol=1e-4, atol=1e-10, d0=128, dd=64, d_max=1024)),
     ("toeplitz1024_inc_bf16", "bf16x3", lambda: w.toeplitz_inverse_distance(1024),
@@ -109,6 +112,25 @@ def test_compress_mixed_parity(hss, torch, name, prec, mk, o):
     err_g = gu.rel_err(A, gu.gpu_dense(H, n))
     err_o = apply.rel_error(ref, A)
     assert err_g <= 1.1 * err_o + 1e-15, (err_g, err_o)
+
+
+def test_mixed_at_the_noise_floor(hss, torch):
+    """rtol 1e-6 on the Laplace sphere kernel: the leaf tolerance (1e-6/4)
+    is only ~3x the measured sampling noise of BF16x3 (~7e-8), so the
+    stopping test may need one more increment than the FP64 oracle.  What
+    must still hold: convergence, an error no larger than the oracle's, and
+    ranks within a small band of the oracle's."""
+    src = w.laplace_kernel(_rcb(w.fibonacci_sphere(2048), 128))
+    o = Options(leaf=128, rtol=1e-6, atol=1e-8, d0=64, dd=32, d_max=2048)
+    R = w.round_to_bf16(w.gaussian_matrix(7, 2048, 0, 2048))
+    ref = compress(src, R, o)
+    H = gu.gpu_compress(src, R, o, precision="bf16x3")
+    st = H.stats()
+    assert st.converged == 1 and st.d_final >= ref.d_final
+    assert st.d_final <= ref.d_final + 2 * o.dd
+    A = src.to_dense()
+    assert gu.rel_err(A, gu.gpu_dense(H, 2048)) <= 1.1 * apply.rel_error(ref, A) + 1e-15
+    assert max(st.max_rank_r, st.max_rank_c) <= 1.1 * ref.max_rank() + 2
 
 
 def test_mixed_device_R_is_rounded(hss, torch):
