@@ -250,7 +250,7 @@ def _node_sufficient(ctx, t) -> bool:
             if not ok:
                 return False
             out.append((piv, Rf, k))
-        _set_id(t, out)
+        _set_id(t, out, d)
         return True
     # Incrementing (Algorithm 5 applied to the node's samples, P18)
     for side, S in (("r", t.Sr), ("c", t.Sc)):
@@ -268,7 +268,7 @@ def _node_sufficient(ctx, t) -> bool:
     for S in (t.Sr, t.Sc):
         piv, Rf, k, _ = qrcp(S[:, :d].T, plain_rule(er, ea))
         out.append((piv, Rf, k))
-    _set_id(t, out)
+    _set_id(t, out, d)
     return True
 
 
@@ -300,7 +300,8 @@ def incrementing_block_test(Sk: np.ndarray, st: dict, er: float, ea: float) -> b
     return st["Q"].shape[1] >= m
 
 
-def _set_id(t, out):
+def _set_id(t, out, d):
+    t.d_id = d
     (pr, Rr_, kr), (pc, Rc_, kc) = out
     t.Jr, t.Xr, t.U = interpolative(pr, Rr_, kr)
     t.Jc, t.Xc, t.V = interpolative(pc, Rc_, kc)

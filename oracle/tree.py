@@ -36,6 +36,7 @@ class Node:
         self.Jr = self.Jc = None   # skeleton rows (local indices, pivot order)
         self.Xr = self.Xc = None   # R1^{-1} R2  (E^T)
         self.piv_r = self.piv_c = None
+        self.d_id = None           # sample columns the ID was taken from
         self.Ir = self.Ic = None   # skeleton rows as global indices
         self.inc = {}              # Incrementing per-side state
 

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -191,6 +192,8 @@ struct hss_matrix_s {
   size_t h_pinned_cap = 0;
   int d_final = 0, n_adapt = 0, converged = 0;
   int qrcp_cap = -1;       // co-resident CTAs of the group QRCP kernel
+  bool trace = false;      // HSS_TRACE=1: one stderr line per QRCP launch
+  cudaEvent_t trace_ev[2] = {nullptr, nullptr};
   void* packA = nullptr;   // packed tensor-core tiles of a dense A (during compress)
   bool usable = false;
   hss_stats st{};
@@ -198,6 +201,8 @@ struct hss_matrix_s {
   PhaseTimer timer;
   ~hss_matrix_s() {
     if (packA) cudaFree(packA);
+    for (auto& e : trace_ev)
+      if (e) cudaEventDestroy(e);
     timer.clear();
     scratch.release();
     arena.release();
@@ -520,7 +525,8 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     // group form: barrier, partial maxima, broadcast words (at most one CTA per 8 rows)
     const size_t pmax = (size_t)std::max(1, s.m / 8);
     need += Scratch::rnd(sizeof(unsigned)) + Scratch::rnd(sizeof(double) * pmax) +
-            Scratch::rnd(sizeof(int) * pmax) + 2 * Scratch::rnd(32);
+            Scratch::rnd(sizeof(int) * pmax) +
+            Scratch::rnd(sizeof(double) * (size_t)std::max(1, std::min(s.m, d)));   // diag
   }
   CK(H->scratch.ensure(need, st));
   std::vector<QrcpJob> jobs;
@@ -549,72 +555,109 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   for (size_t i = 0; i < jobs.size(); ++i) jobs[i].out = outs + 3 * i;
   if (jobs.empty()) return HSS_OK;
   CK(H->timer.mark(PH_ID, st));
-  // Few node sides (upper tree levels): a group of CTAs per job in one
-  // cooperative launch, sized by the job's work m d min(m, d).
+  // Launch shape.  The jobs of a level may be split into batches by a
+  // workspace budget (one batch at present, see below).  A batch with fewer
+  // jobs than half the co-resident CTAs gives each job a group of CTAs in
+  // one cooperative launch, sized by its work m d min(m, d); otherwise one
+  // CTA per job.
   if (H->qrcp_cap < 0) H->qrcp_cap = qrcp_group_capacity();
   const int cap = H->qrcp_cap;
   const size_t nj = jobs.size();
+  // (one batch: measured on the Gaussian 8-D n=16384 case, splitting a level
+  // into L2-sized batches only serialised the latency-bound pivot steps)
+  const double l2_budget = 1e30;
   std::vector<int> P(nj, 1);
-  bool group = cap > 0 && (int)nj * 2 <= cap;
-  if (group) {
-    double tot = 0.0;
-    std::vector<double> wk(nj);
-    for (size_t i = 0; i < nj; ++i) {
-      wk[i] = (double)jobs[i].m * jobs[i].d * std::min(jobs[i].m, jobs[i].d) + 1.0;
-      tot += wk[i];
-    }
-    int used = 0;
-    for (size_t i = 0; i < nj; ++i) {
-      int p = (int)std::floor(cap * wk[i] / tot);
-      p = std::max(1, std::min(p, std::max(1, jobs[i].m / 8)));
-      P[i] = p;
-      used += p;
-    }
-    while (used > cap) {   // trim the largest groups
-      size_t b = 0;
-      for (size_t i = 1; i < nj; ++i) if (P[i] > P[b]) b = i;
-      if (P[b] == 1) break;
-      P[b]--;
-      used--;
-    }
-    int maxp = 0;
-    for (int p : P) maxp = std::max(maxp, p);
-    group = used <= cap && maxp > 1;
+  for (size_t i = 0; i < nj; ++i)
+    jobs[i].diag = (double*)H->scratch.take(sizeof(double) * std::max(1, std::min(jobs[i].m, d)));
+  unsigned* bars = (unsigned*)H->scratch.take(sizeof(unsigned) * nj);
+  for (size_t i = 0; i < nj; ++i) {
+    jobs[i].bar = bars + i;
+    const int pmax = std::max(1, jobs[i].m / 8);
+    jobs[i].redv = (double*)H->scratch.take(sizeof(double) * pmax);
+    jobs[i].redi = (int*)H->scratch.take(sizeof(int) * pmax);
   }
-  if (group) {
-    unsigned* bars = (unsigned*)H->scratch.take(sizeof(unsigned) * nj);
-    std::vector<int2> map;
-    for (size_t i = 0; i < nj; ++i) {
-      jobs[i].P = P[i];
-      jobs[i].bar = bars + i;
-      jobs[i].redv = (double*)H->scratch.take(sizeof(double) * P[i]);
-      jobs[i].redi = (int*)H->scratch.take(sizeof(int) * P[i]);
-      jobs[i].bcd = (double*)H->scratch.take(sizeof(double) * 4);
-      jobs[i].bci = (int*)H->scratch.take(sizeof(int) * 4);
-      for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
+  if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
+  CK(cudaMemsetAsync(bars, 0, sizeof(unsigned) * nj, st));
+  CK(cudaMemsetAsync(H->d_flag + 2, 0, sizeof(int), st));
+  if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
+  struct Batch { size_t b0, b1; bool group; };
+  std::vector<Batch> batches;
+  for (size_t b0 = 0; b0 < nj;) {
+    size_t b1 = b0;
+    double bytes = 0.0;
+    while (b1 < nj) {
+      const double wb = 8.0 * jobs[b1].d * std::max(jobs[b1].m, 1);
+      if (b1 > b0 && bytes + wb > l2_budget) break;
+      bytes += wb;
+      ++b1;
     }
-    CK(cudaMemsetAsync(bars, 0, sizeof(unsigned) * nj, st));
-    CK(cudaMemsetAsync(H->d_flag + 2, 0, sizeof(int), st));
-    QrcpJob* dj;
-    int2* dm;
-    CKS(upload_jobs(H, jobs, &dj, st));
-    CKS(upload_jobs(H, map, &dm, st));
-    if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
-    CK(launch_qrcp_group(dj, dm, (int)map.size(), H->d_flag + 2, st));
-    H->launches++;
-    CK(cudaFreeAsync(dj, st));
-    CK(cudaFreeAsync(dm, st));
-    CKS(readback(H, H->d_flag + 2, sizeof(int), st));
-    if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "group QRCP barrier gave up (code %d)", H->h_pinned[0]);
-  } else {
-    QrcpJob* dj;
-    CKS(upload_jobs(H, jobs, &dj, st));
-    if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
-    CK(launch_qrcp(dj, (int)jobs.size(), st));
-    H->launches++;
-    CK(cudaFreeAsync(dj, st));
+    const size_t bn = b1 - b0;
+    bool group = cap > 0 && (int)bn * 2 <= cap;
+    if (group) {
+      double tot = 0.0;
+      std::vector<double> wk(bn);
+      for (size_t i = 0; i < bn; ++i) {
+        const QrcpJob& q = jobs[b0 + i];
+        wk[i] = (double)q.m * q.d * std::min(q.m, q.d) + 1.0;
+        tot += wk[i];
+      }
+      int used = 0;
+      for (size_t i = 0; i < bn; ++i) {
+        int p = (int)std::floor(cap * wk[i] / tot);
+        p = std::max(1, std::min(p, std::max(1, jobs[b0 + i].m / 8)));
+        P[b0 + i] = p;
+        used += p;
+      }
+      while (used > cap) {   // trim the largest groups
+        size_t b = 0;
+        for (size_t i = 1; i < bn; ++i) if (P[b0 + i] > P[b0 + b]) b = i;
+        if (P[b0 + b] == 1) break;
+        P[b0 + b]--;
+        used--;
+      }
+      int maxp = 0;
+      for (size_t i = 0; i < bn; ++i) maxp = std::max(maxp, P[b0 + i]);
+      group = used <= cap && maxp > 1;
+    }
+    if (!group)
+      for (size_t i = b0; i < b1; ++i) P[i] = 1;
+    batches.push_back({b0, b1, group});
+    b0 = b1;
   }
+  for (size_t i = 0; i < nj; ++i) jobs[i].P = P[i];
+  QrcpJob* dj;
+  CKS(upload_jobs(H, jobs, &dj, st));
+  int ctas_total = 0;
+  for (const Batch& b : batches) {
+    if (b.group) {
+      std::vector<int2> map;
+      for (size_t i = b.b0; i < b.b1; ++i)
+        for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
+      int2* dm;
+      CKS(upload_jobs(H, map, &dm, st));
+      CK(launch_qrcp(dj, dm, (int)map.size(), d, 0, H->d_flag + 2, st));
+      CK(cudaFreeAsync(dm, st));
+      ctas_total += (int)map.size();
+    } else {
+      // W in shared memory for the jobs that fit (up to 200 KB)
+      size_t smem_w = 0;
+      for (size_t i = b.b0; i < b.b1; ++i) {
+        const size_t need = sizeof(double) * (size_t)(jobs[i].m + 1) * d;
+        if (need <= 200 * 1024 && need > smem_w) smem_w = need;
+      }
+      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), d, smem_w, H->d_flag + 2, st));
+      ctas_total += (int)(b.b1 - b.b0);
+    }
+    H->launches++;
+  }
+  const int nbatch = (int)batches.size();
+  CK(cudaFreeAsync(dj, st));
+  if (H->trace) CK(cudaEventRecord(H->trace_ev[1], st));
+  CKS(readback(H, H->d_flag + 2, sizeof(int), st));
+  if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "group QRCP barrier gave up (code %d)", H->h_pinned[0]);
   CKS(readback(H, outs, sizeof(int) * 3 * jobs.size(), st));
+  double tr_flop = 0.0;
+  int tr_m = 0, tr_k = 0;
   for (size_t i = 0; i < reqs.size(); ++i) {
     Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
     s.qr_k = H->h_pinned[3 * i];
@@ -626,6 +669,16 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     for (int j = 0; j < s.qr_k; ++j) f += 4.0 * (dd - j) * (m - j - 1) + 3.0 * (dd - j);
     if (s.qr_acc && k > 0 && m > k) f += k * k * (m - k);
     H->st.flop_id += f;
+    tr_flop += f;
+    tr_m = std::max(tr_m, jobs[i].m);
+    tr_k = std::max(tr_k, s.qr_k);
+  }
+  if (H->trace) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, H->trace_ev[0], H->trace_ev[1]);
+    fprintf(stderr,
+            "[hss trace] qrcp level %d jobs %zu batches %d ctas %d max_m %d d %d max_k %d  %.3f ms  %.1f GFLOP/s\n",
+            H->nodes[reqs[0].node].level, nj, nbatch, ctas_total, tr_m, d, tr_k, ms, tr_flop / (ms * 1e6));
   }
   return HSS_OK;
 }
@@ -642,11 +695,12 @@ hss_status finalize_id(hss_matrix_s* H, int node, int side, const double* W, int
   s.I = (int*)H->arena.alloc(sizeof(int) * (size_t)std::max(k, 1));
   if (!s.X || !s.I) return fail(HSS_ERR_NOMEM, "device arena allocation failed (ID)");
   if (k > 0 && m > k) {
+    // X(:, t) = W(0:k, piv[k + t]): element (t, i) of the copy's transposed view
     GemmJob j = gemm_job();
-    j.M = k; j.N = m - k; j.K = 0;
-    j.C0 = opnd(W + (long long)k * d, 1, d);
+    j.M = m - k; j.N = k; j.K = 0;
+    j.C0 = opnd(W, d, 1, s.piv + k);
     j.beta = 1.0;
-    j.C = s.X; j.c_rs = 1; j.c_cs = k;
+    j.C = s.X; j.c_rs = k; j.c_cs = 1;
     copies.push_back(j);
   }
   if (k > 0) {
@@ -910,6 +964,14 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
   H->src = *A;
   H->dmax = std::min(o->d_max, n);
   CK(cudaGetDevice(&H->device));
+  {
+    const char* tr = getenv("HSS_TRACE");
+    H->trace = tr && tr[0] == '1';
+    if (H->trace) {
+      CK(cudaEventCreate(&H->trace_ev[0]));
+      CK(cudaEventCreate(&H->trace_ev[1]));
+    }
+  }
   build_tree(n, o->leaf, H->nodes);
   H->max_level = 0;
   for (auto& t : H->nodes) H->max_level = std::max(H->max_level, t.level);

@@ -75,7 +75,9 @@ struct GemmTile { int job, ti, tj; };
 
 // QR with column pivoting of W = S^T (S: m x d rows, row-major ld lds),
 // truncated by the plain rule (rule 0) or the HMT-scaled rule (rule 1),
-// followed by X = R1^{-1} R2 in place when accepted and do_id.
+// followed by X = R1^{-1} R2 when accepted and do_id.  Columns are not
+// swapped: piv[0:k] lists the pivot columns, piv[k:m] the others in column
+// order, and X(:, t) is left in W(0:k, piv[k + t]).
 struct QrcpJob {
   const double* S;
   long long lds;
@@ -83,6 +85,7 @@ struct QrcpJob {
   double* W;            // workspace, col-major d x m, ld = ldw
   long long ldw;
   double* nrm;          // workspace 2*m
+  double* diag;         // workspace min(d, m): R_jj
   int* piv;             // out: m entries
   int rule;             // 0 plain, 1 HMT
   int mh, nh, p;        // Hankel block sizes and oversampling (HMT)
@@ -94,8 +97,6 @@ struct QrcpJob {
   unsigned* bar;        // group barrier counter, zero before the launch
   double* redv;         // P partial maxima
   int* redi;            // P partial argmax indices
-  double* bcd;          // broadcast: [0] tau, [3] |R_11|
-  int* bci;             // broadcast: [0] stop flag
 };
 
 // One Incrementing block test on one side of a node (Algorithm 5):
@@ -154,11 +155,11 @@ cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int nj
                            int max_tiles, cudaStream_t st);
 cudaError_t launch_gemm(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles,
                         cudaStream_t st);
-cudaError_t launch_qrcp(const QrcpJob* jobs_dev, int njobs, cudaStream_t st);
-// cooperative form: map[cta] = (job, rank within the job's group)
+// map == nullptr: one CTA per job; otherwise map[cta] = (job, rank within
+// the job's group) and the launch is cooperative.  d_max: largest d.
 int qrcp_group_capacity();
-cudaError_t launch_qrcp_group(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int* err,
-                              cudaStream_t st);
+cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, size_t smem_w,
+                        int* err, cudaStream_t st);
 cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
 cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int c1,
                              int* flag, cudaStream_t st);

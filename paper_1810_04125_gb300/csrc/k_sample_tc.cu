@@ -306,6 +306,21 @@ __device__ __forceinline__ void drain_chain(uint32_t tmem, int N, int b, int q, 
   }
 }
 
+// float -> double by integer operations (exact; the FP64 conversion unit is
+// as slow as the FP64 pipe on this part).  Zero and normal floats only: the
+// float-float parts of a sample are never subnormal, infinite or NaN unless
+// the input is (the samples are checked for NaN/Inf afterwards).
+__device__ __forceinline__ double f2d_exact(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t ex = (u >> 23) & 0xFFu;
+  if (ex == 0u) return 0.0;
+  if (ex == 0xFFu) return (double)x;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint64_t e64 = (uint64_t)(ex - 127u + 1023u) << 52;
+  const uint64_t man = (uint64_t)(u & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sign | e64 | man));
+}
+
 // Write one thread's row of the result (NH columns from col).
 template <int NH>
 __device__ __forceinline__ void store_row(double* S, long long lds, int n, int ncols, int row, int col,
@@ -315,7 +330,7 @@ __device__ __forceinline__ void store_row(double* S, long long lds, int n, int n
 #pragma unroll
   for (int j = 0; j < NH; ++j) {
     if (col + j < ncols) {
-      const double v = (double)s[j] + (double)e[j];
+      const double v = f2d_exact(s[j]) + f2d_exact(e[j]);
       if (atomic) atomicAdd(out + j, v);
       else out[j] = v;
     }
@@ -696,7 +711,7 @@ int tmem_cols_for(int N) {
   return tc;
 }
 
-constexpr int DRAIN_PACKED = 1;   // k-tiles per accumulation chain (dense, packed)
+constexpr int DRAIN_PACKED = 2;   // k-tiles per accumulation chain (dense, packed)
 constexpr int DRAIN_GEN = 2;      // k-tiles per accumulation chain (generated entries)
 
 template <int PREC>
@@ -738,9 +753,13 @@ cudaError_t launch_gen_t(const TcArgs& a, int gx, int gy, cudaStream_t st) {
 
 int bk_of(int precision) { return precision == HSS_PREC_TF32X2 ? 32 : 64; }
 
+// K split across CTAs: enough CTAs for `waves` waves, but at least 64 k-tiles
+// per CTA so that the epilogue (one pass over the 128 x N tile) stays small
+// against the main loop.
 int ksplit_for(int gx, int gy, int nkt, int waves) {
   int ks = (waves * 152 + gx * gy - 1) / (gx * gy);
-  if (ks > nkt) ks = nkt;
+  const int cap = nkt / 64;
+  if (ks > cap) ks = cap;
   return ks < 1 ? 1 : ks;
 }
 
