@@ -315,24 +315,43 @@ GemmJob gemm_job() {
 }
 
 // Runs a list of tile-product jobs (one launch).
-hss_status run_gemms(hss_matrix_s* H, const std::vector<GemmJob>& jobs, cudaStream_t st) {
+// tc: products that only form samples (merge, reduce) go to the tensor-core
+// kernel in the mixed precisions.
+hss_status run_gemms(hss_matrix_s* H, const std::vector<GemmJob>& jobs, cudaStream_t st,
+                     const char* tag = "gemm", bool tc = false) {
+  tc = tc && H->o.precision != HSS_PREC_FP64;
+  int max_n = 0;
+  for (const GemmJob& j : jobs) max_n = std::max(max_n, j.N);
+  const int tm = tc ? 128 : 64, tn = tc ? gemm_tc_tile_n(max_n) : 64;
   std::vector<GemmTile> tiles;
+  double flop = 0.0;
   for (size_t i = 0; i < jobs.size(); ++i) {
     const GemmJob& j = jobs[i];
     if (j.M <= 0 || j.N <= 0) continue;
-    for (int ti = 0; ti < (j.M + 63) / 64; ++ti)
-      for (int tj = 0; tj < (j.N + 63) / 64; ++tj) tiles.push_back({(int)i, ti, tj});
+    flop += 2.0 * j.M * j.N * j.K;
+    for (int ti = 0; ti < (j.M + tm - 1) / tm; ++ti)
+      for (int tj = 0; tj < (j.N + tn - 1) / tn; ++tj) tiles.push_back({(int)i, ti, tj});
   }
   if (tiles.empty()) return HSS_OK;
+  if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
   size_t bj = jobs.size() * sizeof(GemmJob), bt = tiles.size() * sizeof(GemmTile);
   void* dj = nullptr;
   CK(cudaMallocAsync(&dj, Scratch::rnd(bj) + bt, st));
   GemmTile* dt = (GemmTile*)((char*)dj + Scratch::rnd(bj));
   CKS(upload(H, dj, jobs.data(), bj, st));
   CKS(upload(H, dt, tiles.data(), bt, st));
-  CK(launch_gemm((const GemmJob*)dj, dt, (int)tiles.size(), st));
+  if (tc) CK(launch_gemm_tc((const GemmJob*)dj, dt, (int)tiles.size(), tn, H->d_flag + 3, st));
+  else CK(launch_gemm((const GemmJob*)dj, dt, (int)tiles.size(), st));
   H->launches++;
   CK(cudaFreeAsync(dj, st));
+  if (H->trace) {
+    CK(cudaEventRecord(H->trace_ev[1], st));
+    CK(cudaEventSynchronize(H->trace_ev[1]));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, H->trace_ev[0], H->trace_ev[1]);
+    fprintf(stderr, "[hss trace] %s jobs %zu tiles %zu  %.3f ms  %.1f GFLOP/s\n", tag, jobs.size(),
+            tiles.size(), ms, flop / (ms * 1e6));
+  }
   return HSS_OK;
 }
 
@@ -653,8 +672,9 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   const int nbatch = (int)batches.size();
   CK(cudaFreeAsync(dj, st));
   if (H->trace) CK(cudaEventRecord(H->trace_ev[1], st));
-  CKS(readback(H, H->d_flag + 2, sizeof(int), st));
+  CKS(readback(H, H->d_flag + 2, 2 * sizeof(int), st));
   if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "group QRCP barrier gave up (code %d)", H->h_pinned[0]);
+  if (H->h_pinned[1]) return fail(HSS_ERR_TIMEOUT, "tensor-core tile product gave up waiting (code %d)", H->h_pinned[1]);
   CKS(readback(H, outs, sizeof(int) * 3 * jobs.size(), st));
   double tr_flop = 0.0;
   int tr_m = 0, tr_k = 0;
@@ -777,7 +797,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
       Node& t = H->nodes[id];
       if (!t.leaf) merge_jobs(H, t, d_prev, d, mj);
     }
-    CKS(run_gemms(H, mj, st));
+    CKS(run_gemms(H, mj, st, "merge", true));
 
     // --- strategy test on the candidates
     std::vector<int> accepted;
@@ -909,10 +929,10 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         t.state = HSS_PARTIALLY_COMPRESSED;
       }
     }
-    CKS(run_gemms(H, copies, st));
+    CKS(run_gemms(H, copies, st, "x-copy"));
     for (int id : accepted) reduce_jobs(H, H->nodes[id], 0, d, rj);
     for (int id : lw.upd) reduce_jobs(H, H->nodes[id], d_prev, d, rj);
-    CKS(run_gemms(H, rj, st));
+    CKS(run_gemms(H, rj, st, "reduce", true));
   }
   Node& root = H->nodes[0];
   if (root.leaf || (H->nodes[root.ch[0]].state == HSS_COMPRESSED &&
@@ -1002,6 +1022,7 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     return fail(HSS_ERR_NOMEM, "device allocation of %zu bytes for samples failed", 3 * nd * 8);
   CKS(upload(H, H->leaf_id, lid.data(), sizeof(int) * n, st));
   CKS(upload(H, H->iota, io.data(), sizeof(int) * n, st));
+  CK(cudaMemsetAsync(H->d_flag, 0, 256, st));
 
   CK(H->timer.mark(PH_OTHER, st));
   int d = std::min(o->d0, H->dmax), d_prev = 0;
@@ -1022,7 +1043,8 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     CK(cudaFreeAsync(H->packA, st));
     H->packA = nullptr;
   }
-  CK(cudaStreamSynchronize(st));
+  CKS(readback(H, H->d_flag + 3, sizeof(int), st));
+  if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "tensor-core tile product gave up waiting (code %d)", H->h_pinned[0]);
   H->d_final = d;
   H->usable = H->converged != 0;
   double ph[PH_N];

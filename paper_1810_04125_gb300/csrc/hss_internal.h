@@ -155,6 +155,12 @@ cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int nj
                            int max_tiles, cudaStream_t st);
 cudaError_t launch_gemm(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles,
                         cudaStream_t st);
+// The same contract with the product on tcgen05 tensor cores, operands split
+// into three TF32 terms (k_gemm_tc.cu): tiles of 128 rows x tile_n columns
+// (gemm_tc_tile_n); *err records a wait that gave up.
+int gemm_tc_tile_n(int max_n);
+cudaError_t launch_gemm_tc(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles, int tile_n,
+                           int* err, cudaStream_t st);
 // map == nullptr: one CTA per job; otherwise map[cta] = (job, rank within
 // the job's group) and the launch is cooperative.  d_max: largest d.
 int qrcp_group_capacity();

@@ -158,11 +158,19 @@ __global__ void __launch_bounds__(NT) k_qrcp(const QrcpJob* __restrict__ jobs,
     }
     if (!group_barrier(jb.bar, P, epoch, err, &s_ok)) return;
     // every CTA: the pivot, the exact pivot norm and the reflector
-    if (tid == 0 && P > 1) {
-      double v = __ldcg(jb.redv);
-      int i = __ldcg(jb.redi);
-      for (int q = 1; q < P; ++q) argmax_pair(v, i, __ldcg(jb.redv + q), __ldcg(jb.redi + q));
-      si[0] = i;
+    if (P > 1 && warp == 0) {
+      // the P partial maxima, read by the 32 lanes at once (the order of
+      // the reduction does not matter: ties go to the lowest index)
+      double v = -2.0;
+      int i = 0x7fffffff;
+      for (int q = lane; q < P; q += 32) argmax_pair(v, i, __ldcg(jb.redv + q), __ldcg(jb.redi + q));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        argmax_pair(v, i, v2, i2);
+      }
+      if (lane == 0) si[0] = i;
     }
     __syncthreads();
     const int p = si[0];
