@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <queue>
 #include <vector>
 
 #include "hss_internal.h"
@@ -191,7 +192,8 @@ struct hss_matrix_s {
   int* h_pinned = nullptr; // host pinned readback buffer
   size_t h_pinned_cap = 0;
   int d_final = 0, n_adapt = 0, converged = 0;
-  int qrcp_cap = -1;       // co-resident CTAs of the group QRCP kernel
+  int qrcp_cap = -1;       // co-resident CTAs of the QRCP kernel at width qrcp_cap_d
+  int qrcp_cap_d = -1;
   bool trace = false;      // HSS_TRACE=1: one stderr line per QRCP launch
   cudaEvent_t trace_ev[2] = {nullptr, nullptr};
   void* packA = nullptr;   // packed tensor-core tiles of a dense A (during compress)
@@ -536,114 +538,101 @@ struct QrcpReq { int node; int side; int rule; };
 hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cudaStream_t st,
                     std::vector<double*>& wbuf) {
   H->scratch.reset();
-  size_t need = 0;
-  for (auto& q : reqs) {
-    Side& s = q.side ? H->nodes[q.node].c : H->nodes[q.node].r;
-    need += Scratch::rnd(sizeof(double) * (size_t)d * std::max(s.m, 1)) +
-            Scratch::rnd(sizeof(double) * 2 * std::max(s.m, 1)) + Scratch::rnd(3 * sizeof(int));
-    // group form: barrier, partial maxima, broadcast words (at most one CTA per 8 rows)
-    const size_t pmax = (size_t)std::max(1, s.m / 8);
-    need += Scratch::rnd(sizeof(unsigned)) + Scratch::rnd(sizeof(double) * pmax) +
-            Scratch::rnd(sizeof(int) * pmax) +
-            Scratch::rnd(sizeof(double) * (size_t)std::max(1, std::min(s.m, d)));   // diag
+  if (reqs.empty()) return HSS_OK;
+  const long long ldw = ((long long)d + 3) / 4 * 4;   // 32-byte aligned columns
+  const size_t nj = reqs.size();
+  // Launch shape.  Every job gets a group of P CTAs, each owning about g of
+  // its m columns (g a multiple of 32, at most qrcp_cols_per_cta()), with g
+  // the smallest width for which the groups of a batch fit the co-resident
+  // CTAs; one cooperative launch per batch (plain launch when every P is 1).
+  if (H->qrcp_cap_d != d) {
+    H->qrcp_cap = qrcp_group_capacity(d);
+    H->qrcp_cap_d = d;
   }
+  const int cap = H->qrcp_cap, NL = qrcp_cols_per_cta();
+  if (cap <= 0) return fail(HSS_ERR_CUDA, "QRCP kernel cannot be resident (d = %d)", d);
+  std::vector<int> mj(nj), P(nj, 1);
+  for (size_t i = 0; i < nj; ++i) {
+    const Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
+    mj[i] = std::max(s.m, 1);
+  }
+  struct Batch { size_t b0, b1; bool group; };
+  std::vector<Batch> batches;
+  for (size_t b0 = 0; b0 < nj;) {
+    // the largest prefix whose groups fit at width NL
+    size_t b1 = b0;
+    int used = 0;
+    while (b1 < nj) {
+      const int p = (mj[b1] + NL - 1) / NL;
+      if (b1 > b0 && used + p > cap) break;
+      used += p;
+      ++b1;
+    }
+    // groups proportional to m filling every co-resident slot (an equal
+    // number of CTAs on every SM, so that no SM runs a double share), each
+    // CTA with at most NL columns
+    for (size_t i = b0; i < b1; ++i) P[i] = std::max(1, (mj[i] + NL - 1) / NL);
+    // hand the remaining slots to the jobs with the most columns per CTA
+    std::priority_queue<std::pair<double, size_t>> pq;
+    for (size_t i = b0; i < b1; ++i) pq.push({(double)mj[i] / P[i], i});
+    while (used < cap && !pq.empty()) {
+      auto top = pq.top();
+      pq.pop();
+      const size_t i = top.second;
+      if (mj[i] / (P[i] + 1) < 4) continue;   // keep at least four columns per CTA
+      P[i]++;
+      used++;
+      pq.push({(double)mj[i] / P[i], i});
+    }
+    bool group = false;
+    for (size_t i = b0; i < b1; ++i) group = group || P[i] > 1;
+    batches.push_back({b0, b1, group});
+    b0 = b1;
+  }
+  size_t need = 0;
+  for (size_t i = 0; i < nj; ++i) {
+    need += Scratch::rnd(sizeof(double) * (size_t)ldw * mj[i]) + Scratch::rnd(sizeof(double) * mj[i]) +
+            Scratch::rnd(sizeof(double) * (size_t)std::max(1, std::min(mj[i], d))) +
+            Scratch::rnd(sizeof(unsigned)) + 2 * Scratch::rnd(sizeof(double) * 2 * P[i]) +
+            Scratch::rnd(sizeof(int) * 2 * P[i]);
+  }
+  need += Scratch::rnd(sizeof(int) * 3 * nj);
   CK(H->scratch.ensure(need, st));
   std::vector<QrcpJob> jobs;
   wbuf.clear();
-  int* outs = nullptr;
-  for (size_t i = 0; i < reqs.size(); ++i) {
+  unsigned* bars = (unsigned*)H->scratch.take(sizeof(unsigned) * nj);
+  int* outs = (int*)H->scratch.take(sizeof(int) * 3 * nj);
+  for (size_t i = 0; i < nj; ++i) {
     const QrcpReq& q = reqs[i];
     Node& t = H->nodes[q.node];
     Side& s = q.side ? t.c : t.r;
     QrcpJob j;
     memset(&j, 0, sizeof j);
     j.S = s.S; j.lds = H->dmax; j.m = s.m; j.d = d;
-    j.W = (double*)H->scratch.take(sizeof(double) * (size_t)d * std::max(s.m, 1));
-    j.ldw = d;
-    j.nrm = (double*)H->scratch.take(sizeof(double) * 2 * std::max(s.m, 1));
+    j.W = (double*)H->scratch.take(sizeof(double) * (size_t)ldw * mj[i]);
+    j.ldw = ldw;
+    j.nrm = (double*)H->scratch.take(sizeof(double) * mj[i]);
+    j.diag = (double*)H->scratch.take(sizeof(double) * std::max(1, std::min(mj[i], d)));
     j.piv = s.piv;
     j.rule = q.rule;
     j.mh = t.size; j.nh = H->n - t.size; j.p = H->o.oversample_p;
     j.do_id = 1;
     double sc = tol_scale(H, t.level);
     j.er = H->o.rtol * sc; j.ea = H->o.atol * sc;
+    j.out = outs + 3 * i;
+    j.P = P[i];
+    j.bar = bars + i;
+    j.redv = (double*)H->scratch.take(sizeof(double) * 2 * P[i]);
+    j.redt = (double*)H->scratch.take(sizeof(double) * 2 * P[i]);
+    j.redi = (int*)H->scratch.take(sizeof(int) * 2 * P[i]);
     wbuf.push_back(j.W);
     jobs.push_back(j);
   }
-  outs = (int*)H->scratch.take(sizeof(int) * 3 * std::max<size_t>(reqs.size(), 1));
-  for (size_t i = 0; i < jobs.size(); ++i) jobs[i].out = outs + 3 * i;
-  if (jobs.empty()) return HSS_OK;
-  CK(H->timer.mark(PH_ID, st));
-  // Launch shape.  The jobs of a level may be split into batches by a
-  // workspace budget (one batch at present, see below).  A batch with fewer
-  // jobs than half the co-resident CTAs gives each job a group of CTAs in
-  // one cooperative launch, sized by its work m d min(m, d); otherwise one
-  // CTA per job.
-  if (H->qrcp_cap < 0) H->qrcp_cap = qrcp_group_capacity();
-  const int cap = H->qrcp_cap;
-  const size_t nj = jobs.size();
-  // (one batch: measured on the Gaussian 8-D n=16384 case, splitting a level
-  // into L2-sized batches only serialised the latency-bound pivot steps)
-  const double l2_budget = 1e30;
-  std::vector<int> P(nj, 1);
-  for (size_t i = 0; i < nj; ++i)
-    jobs[i].diag = (double*)H->scratch.take(sizeof(double) * std::max(1, std::min(jobs[i].m, d)));
-  unsigned* bars = (unsigned*)H->scratch.take(sizeof(unsigned) * nj);
-  for (size_t i = 0; i < nj; ++i) {
-    jobs[i].bar = bars + i;
-    const int pmax = std::max(1, jobs[i].m / 8);
-    jobs[i].redv = (double*)H->scratch.take(sizeof(double) * pmax);
-    jobs[i].redi = (int*)H->scratch.take(sizeof(int) * pmax);
-  }
   if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
+  CK(H->timer.mark(PH_ID, st));
   CK(cudaMemsetAsync(bars, 0, sizeof(unsigned) * nj, st));
   CK(cudaMemsetAsync(H->d_flag + 2, 0, sizeof(int), st));
   if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
-  struct Batch { size_t b0, b1; bool group; };
-  std::vector<Batch> batches;
-  for (size_t b0 = 0; b0 < nj;) {
-    size_t b1 = b0;
-    double bytes = 0.0;
-    while (b1 < nj) {
-      const double wb = 8.0 * jobs[b1].d * std::max(jobs[b1].m, 1);
-      if (b1 > b0 && bytes + wb > l2_budget) break;
-      bytes += wb;
-      ++b1;
-    }
-    const size_t bn = b1 - b0;
-    bool group = cap > 0 && (int)bn * 2 <= cap;
-    if (group) {
-      double tot = 0.0;
-      std::vector<double> wk(bn);
-      for (size_t i = 0; i < bn; ++i) {
-        const QrcpJob& q = jobs[b0 + i];
-        wk[i] = (double)q.m * q.d * std::min(q.m, q.d) + 1.0;
-        tot += wk[i];
-      }
-      int used = 0;
-      for (size_t i = 0; i < bn; ++i) {
-        int p = (int)std::floor(cap * wk[i] / tot);
-        p = std::max(1, std::min(p, std::max(1, jobs[b0 + i].m / 8)));
-        P[b0 + i] = p;
-        used += p;
-      }
-      while (used > cap) {   // trim the largest groups
-        size_t b = 0;
-        for (size_t i = 1; i < bn; ++i) if (P[b0 + i] > P[b0 + b]) b = i;
-        if (P[b0 + b] == 1) break;
-        P[b0 + b]--;
-        used--;
-      }
-      int maxp = 0;
-      for (size_t i = 0; i < bn; ++i) maxp = std::max(maxp, P[b0 + i]);
-      group = used <= cap && maxp > 1;
-    }
-    if (!group)
-      for (size_t i = b0; i < b1; ++i) P[i] = 1;
-    batches.push_back({b0, b1, group});
-    b0 = b1;
-  }
-  for (size_t i = 0; i < nj; ++i) jobs[i].P = P[i];
   QrcpJob* dj;
   CKS(upload_jobs(H, jobs, &dj, st));
   int ctas_total = 0;
@@ -654,17 +643,11 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
         for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
       int2* dm;
       CKS(upload_jobs(H, map, &dm, st));
-      CK(launch_qrcp(dj, dm, (int)map.size(), d, 0, H->d_flag + 2, st));
+      CK(launch_qrcp(dj, dm, (int)map.size(), d, H->d_flag + 2, st));
       CK(cudaFreeAsync(dm, st));
       ctas_total += (int)map.size();
     } else {
-      // W in shared memory for the jobs that fit (up to 200 KB)
-      size_t smem_w = 0;
-      for (size_t i = b.b0; i < b.b1; ++i) {
-        const size_t need = sizeof(double) * (size_t)(jobs[i].m + 1) * d;
-        if (need <= 200 * 1024 && need > smem_w) smem_w = need;
-      }
-      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), d, smem_w, H->d_flag + 2, st));
+      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), d, H->d_flag + 2, st));
       ctas_total += (int)(b.b1 - b.b0);
     }
     H->launches++;
@@ -718,7 +701,7 @@ hss_status finalize_id(hss_matrix_s* H, int node, int side, const double* W, int
     // X(:, t) = W(0:k, piv[k + t]): element (t, i) of the copy's transposed view
     GemmJob j = gemm_job();
     j.M = m - k; j.N = k; j.K = 0;
-    j.C0 = opnd(W, d, 1, s.piv + k);
+    j.C0 = opnd(W, ((long long)d + 3) / 4 * 4, 1, s.piv + k);   // QRCP workspace, ldw
     j.beta = 1.0;
     j.C = s.X; j.c_rs = k; j.c_cs = 1;
     copies.push_back(j);

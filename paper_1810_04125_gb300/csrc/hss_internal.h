@@ -84,7 +84,7 @@ struct QrcpJob {
   int m, d;
   double* W;            // workspace, col-major d x m, ld = ldw
   long long ldw;
-  double* nrm;          // workspace 2*m
+  double* nrm;          // workspace m (column liveness)
   double* diag;         // workspace min(d, m): R_jj
   int* piv;             // out: m entries
   int rule;             // 0 plain, 1 HMT
@@ -95,8 +95,9 @@ struct QrcpJob {
   // group (multi-CTA) form only
   int P;                // CTAs working on this job
   unsigned* bar;        // group barrier counter, zero before the launch
-  double* redv;         // P partial maxima
-  int* redi;            // P partial argmax indices
+  double* redv;         // 2 P partial maxima (two steps in flight)
+  int* redi;            // 2 P partial argmax indices
+  double* redt;         // 2 P pending-update coefficients of the candidates
 };
 
 // One Incrementing block test on one side of a node (Algorithm 5):
@@ -162,10 +163,13 @@ int gemm_tc_tile_n(int max_n);
 cudaError_t launch_gemm_tc(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles, int tile_n,
                            int* err, cudaStream_t st);
 // map == nullptr: one CTA per job; otherwise map[cta] = (job, rank within
-// the job's group) and the launch is cooperative.  d_max: largest d.
-int qrcp_group_capacity();
-cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, size_t smem_w,
-                        int* err, cudaStream_t st);
+// the job's group) and the launch is cooperative.  d_max: largest d.  A CTA
+// owns at most qrcp_cols_per_cta() columns (m / P); W is col-major with
+// ldw a multiple of 4; nrm holds m doubles.
+int qrcp_cols_per_cta();
+int qrcp_group_capacity(int d_max);
+cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, int* err,
+                        cudaStream_t st);
 cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
 cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int c1,
                              int* flag, cudaStream_t st);

@@ -12,28 +12,40 @@
 //                    (eq. RRQRHMTstop, section 2.4.1); accepted when the
 //                    stop came at k <= d - p, or when every row was selected.
 //
-// One kernel serves two launch shapes: one CTA per job (many node sides on a
-// level), or a group of P CTAs per job in one cooperative launch (upper
-// levels with fewer node sides than SMs).  Column c of W is owned by CTA
-// rank c mod P and never moves: a pivot column is "retired" (its norm set to
-// -1) instead of being swapped, every CTA reads it where it lives and builds
-// the same Householder reflector in shared memory, so a pivot step needs a
-// single group barrier (after the partial argmaxes are published).  Row j
-// of W then holds row j of R for every column; R1(i, i') = W(i, piv[i']) for
-// i < i', R1(i, i) = diag[i]; the surviving columns keep R2 in place.
+// Work split.  A job is worked on by a group of P CTAs (P = 1 for small
+// jobs; all groups of a launch are co-resident, cooperative launch when
+// P > 1).  Column c of W (contiguous, leading dimension ldw) is owned by
+// CTA rank c mod P and never moves: a pivot column is retired from its
+// owner's list of live columns instead of being swapped; every CTA reads it
+// where it lives and builds the same Householder reflector in shared
+// memory.  Row j of W then holds row j of R for every column; R1(i, i') =
+// W(i, piv[i']) for i < i', R1(i, i) = diag[i]; the surviving columns keep
+// R2 in place.
 //
-// Pivot = largest down-dated column norm (lowest index on ties), recomputed
-// when cancellation has eaten half of the digits; the stop test uses the
-// exact norm of the pivot column.  The group barrier is a monotonic counter
-// per job with a bounded wait (about 2 s of %globaltimer, or as soon as
-// another CTA has recorded an error); data written by one CTA and read by
-// another goes through L2 (ld/st .cg).
+// One pass over the trailing matrix per pivot step.  Applying reflector
+// H_{j-1} to a column and forming the dot product with the next reflector
+// v_j are fused: the pass of step j reads W(r, c) (r >= j), subtracts
+// tw_{j-1}(c) v_{j-1}(r), stores it and accumulates v_j(r) times it.  Row
+// j-1 and the norm down-date only need tw_{j-1}(c) and the old W(j-1, c),
+// so the next pivot is known before the pass; the pivot column is brought
+// up to date on the fly when it is read.  Inside a CTA eight lanes share a
+// live column (a quad of 4 rows each, 16-byte loads) and the eight warps
+// split the rows; the partial dot products meet in shared memory.
+//
+// Pivot = largest down-dated squared column norm (lowest index on ties),
+// recomputed from the column when cancellation has left less than
+// sqrt(eps) of its last exact value; the stop test uses the exact norm of
+// the pivot column.  The group barrier is a monotonic counter per job with a
+// bounded wait (about 2 s of %globaltimer, or as soon as another CTA has
+// recorded an error); data written by one CTA and read by another goes
+// through L2 (ld/st .cg).
 #include "hss_internal.h"
 
 namespace hss {
 namespace {
 
 constexpr int NT = 256, NW = NT / 32;
+constexpr int NLMAX = 256;   // own columns per CTA (host sizes the groups)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -41,8 +53,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__device__ __forceinline__ void argmax_pair(double& v, int& i, double v2, int i2) {
-  if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+// (v, i) <- the larger norm, lowest column index on ties
+__device__ __forceinline__ void argmax_pair(double& v, int& i, int& pos, double v2, int i2, int pos2) {
+  if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; pos = pos2; }
 }
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -93,194 +106,333 @@ __device__ double block_sum(double v, double* sh) {
   return t;
 }
 
-__global__ void __launch_bounds__(NT) k_qrcp(const QrcpJob* __restrict__ jobs,
-                                             const int2* __restrict__ map, int* err,
-                                             size_t smem_bytes) {
-  extern __shared__ double vs[];   // reflector of the current step (d), then W if it fits
+// Stop thresholds of pivot step j (0-based): eps_a and eps_r |R_11|, both
+// divided by the HMT factor f(j + 1) under rule 1 (zero when f is infinite).
+__device__ __forceinline__ void rank_thresholds(const QrcpJob& jb, int d, int j, double r11, double& ta,
+                                                double& tr) {
+  ta = jb.ea;
+  tr = jb.er * r11;
+  if (jb.rule == 1) {
+    const double den = (double)(d - (j + 1) - 1);
+    if (den <= 0.0) { ta = 0.0; tr = 0.0; }
+    else {
+      const double f = 1.0 + 4.0 * sqrt((double)d) / den * sqrt((double)min(jb.mh, jb.nh));
+      ta /= f;
+      tr /= f;
+    }
+  }
+}
+
+// shared-memory carve-up (dynamic part): two reflectors of d_max entries,
+// then per own live column: partial dots of the eight warps, tw, top, norm^2,
+// norm^2 at the last exact computation, column index
+struct Carve {
+  double *v0, *v1, *part, *tw, *top, *nrm, *orig;
+  int* lc;
+  int* rc;   // columns whose norm is recomputed this step
+};
+
+__device__ __forceinline__ Carve carve(double* base, int dmax) {
+  const int dp = (dmax + 3) & ~3;   // 32-byte aligned reflectors, whole quads
+  Carve c;
+  c.v0 = base;
+  c.v1 = c.v0 + dp;
+  c.part = c.v1 + dp;
+  c.tw = c.part + NW * NLMAX;
+  c.top = c.tw + NLMAX;
+  c.nrm = c.top + NLMAX;
+  c.orig = c.nrm + NLMAX;
+  c.lc = (int*)(c.orig + NLMAX);
+  c.rc = c.lc + NLMAX;
+  return c;
+}
+
+__global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs,
+                                             const int2* __restrict__ map, int* err, int dmax) {
+  extern __shared__ __align__(16) double smem_d[];
   const int2 me = map ? map[blockIdx.x] : make_int2(blockIdx.x, 0);
   const QrcpJob jb = jobs[me.x];
   const int rank = me.y, P = map ? jb.P : 1;
   const int m = jb.m, d = jb.d, tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  // A job worked on by one CTA whose W fits in the dynamic shared memory of
-  // the launch keeps W there (written back at the end); all other jobs work
-  // on W in global memory (L2).
-  const bool own = (P == 1);
-  const bool in_smem = own && (size_t)(m + 1) * d * sizeof(double) <= smem_bytes;
-  const long long ldw = in_smem ? d : jb.ldw;
-  double* W = in_smem ? vs + d : jb.W;
-  double* nrm = jb.nrm;          // own columns only; -1 once retired
-  double* orig = jb.nrm + m;
+  const long long ldw = jb.ldw;
+  double* W = jb.W;
   double* diag = jb.diag;
+  double* liveg = jb.nrm;   // global: +1 live, -1 retired (read by rank 0 at the end)
+  Carve S = carve(smem_d, dmax);
+  double* vp = S.v0;        // v_{j-1}
+  double* vc = S.v1;        // v_j
   __shared__ double sh[NW];
-  __shared__ int si[NW];
-  __shared__ int s_ok;
+  __shared__ double shv[NW], sht[NW];
+  __shared__ int shi[NW], shp[NW];
+  __shared__ int s_ok, s_p, s_pos, s_stop, s_nl, s_nrc;
+  __shared__ double s_twp, s_tau, s_scal, s_r11, s_tha, s_thr;
   unsigned epoch = 0;
 
-  // W = S^T for the own columns, initial norms
-  for (int c = rank + P * warp; c < m; c += P * NW) {
+  // own columns, W = S^T for them, initial squared norms
+  int nl = 0;
+  if (rank < m) nl = (m - 1 - rank) / P + 1;
+  if (nl > NLMAX || d > dmax) {   // sized by the host; never expected
+    if (tid == 0) atomicCAS(err, 0, 9);
+    return;
+  }
+  for (int t = tid; t < nl; t += NT) S.lc[t] = rank + P * t;
+  for (int r = tid; r < 2 * ((dmax + 3) & ~3); r += NT) S.v0[r] = 0.0;
+  __syncthreads();
+  for (int t = warp; t < nl; t += NW) {
+    const int c = S.lc[t];
     const double* src = jb.S + (long long)c * jb.lds;
     double* dst = W + (long long)c * ldw;
     double s = 0.0;
     for (int r = lane; r < d; r += 32) {
-      double v = src[r];
+      const double v = src[r];
       dst[r] = v;
       s = __fma_rn(v, v, s);
     }
     s = warp_sum(s);
-    if (lane == 0) { nrm[c] = s; orig[c] = s; }   // squared norms
+    if (lane == 0) {
+      S.nrm[t] = s;
+      S.orig[t] = s;
+      S.tw[t] = 0.0;
+      liveg[c] = 1.0;
+    }
   }
   __syncthreads();
 
   const int kmax = min(d, m);
   int k = kmax, stopped = 0;
-  __shared__ double s_tau, s_scal, s_r11;
-  __shared__ int s_stop;
   const double tol3z = 1.4901161193847656e-08;   // sqrt(2^-52)
-  for (int j = 0; j < kmax; ++j) {
-    // largest (squared) norm among the own live columns
+  double tau = 0.0;
+  for (int j = 0; j <= kmax; ++j) {
+    // ---- (a) finish step j-1 on the own live columns: tw_{j-1} from the
+    // partial dots, row j-1 of R, norm down-date; local argmax
+    if (tid == 0) s_nrc = 0;
+    // the thresholds of step j (R_11 known from step 0 on), off the
+    // critical path of the pivot step
+    if (tid == 64 && j >= 1 && j < kmax) rank_thresholds(jb, d, j, s_r11, s_tha, s_thr);
+    __syncthreads();
     double bv = -1.0;
-    int bi = 0x7fffffff;
-    for (int c = rank + P * tid; c < m; c += P * NT) argmax_pair(bv, bi, nrm[c], c);
+    int bi = 0x7fffffff, bp = -1;
+    for (int t = tid; t < nl; t += NT) {
+      if (j >= 1) {
+        double dot = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) dot += S.part[w * NLMAX + t];
+        const double twv = tau * dot;
+        S.tw[t] = twv;
+        const double rjc = S.top[t] - twv;
+        W[(long long)S.lc[t] * ldw + (j - 1)] = rjc;
+        const double v = __fma_rn(-rjc, rjc, S.nrm[t]);
+        if (v <= tol3z * S.orig[t]) S.rc[atomicAdd(&s_nrc, 1)] = t;
+        else S.nrm[t] = v;
+      }
+    }
+    __syncthreads();
+    if (j == kmax) break;
+    if (s_nrc > 0) {
+      // exact norm^2 of rows >= j of the columns (with H_{j-1} applied)
+      for (int q = warp; q < s_nrc; q += NW) {
+        const int t = S.rc[q];
+        const double* col = W + (long long)S.lc[t] * ldw;
+        const double twv = S.tw[t];
+        double s2 = 0.0;
+        for (int r = j + lane; r < d; r += 32) {
+          const double x = __fma_rn(-twv, vp[r], col[r]);
+          s2 = __fma_rn(x, x, s2);
+        }
+        s2 = warp_sum(s2);
+        if (lane == 0) { S.nrm[t] = s2; S.orig[t] = s2; }
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < nl; t += NT) argmax_pair(bv, bi, bp, S.nrm[t], S.lc[t], t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-      int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-      argmax_pair(bv, bi, v2, i2);
+      const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      const int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
+      argmax_pair(bv, bi, bp, v2, i2, p2);
     }
-    if (lane == 0) { sh[warp] = bv; si[warp] = bi; }
+    if (lane == 0) { shv[warp] = bv; shi[warp] = bi; shp[warp] = bp; }
     __syncthreads();
     if (tid == 0) {
-      double v = sh[0];
-      int i = si[0];
-      for (int w = 1; w < NW; ++w) argmax_pair(v, i, sh[w], si[w]);
-      if (P > 1) { __stcg(jb.redv + rank, v); __stcg(jb.redi + rank, i); }
-      else { sh[0] = v; si[0] = i; }
+      double v = shv[0];
+      int i = shi[0], pos = shp[0];
+      for (int w = 1; w < NW; ++w) argmax_pair(v, i, pos, shv[w], shi[w], shp[w]);
+      const double twc = pos >= 0 ? S.tw[pos] : 0.0;
+      if (P > 1) {
+        // partials of step j in buffer j & 1: a CTA that runs ahead writes the
+        // next step's into the other buffer while the group still reads these
+        const int pb = (j & 1) * P + rank;
+        __stcg(jb.redv + pb, v);
+        __stcg(jb.redi + pb, i);
+        __stcg(jb.redt + pb, twc);
+      }
+      s_p = i;
+      s_pos = pos;
+      s_twp = twc;
     }
+    // ---- (b) the pivot of step j over the group
     if (!group_barrier(jb.bar, P, epoch, err, &s_ok)) return;
-    // every CTA: the pivot, the exact pivot norm and the reflector
     if (P > 1 && warp == 0) {
-      // the P partial maxima, read by the 32 lanes at once (the order of
-      // the reduction does not matter: ties go to the lowest index)
-      double v = -2.0;
-      int i = 0x7fffffff;
-      for (int q = lane; q < P; q += 32) argmax_pair(v, i, __ldcg(jb.redv + q), __ldcg(jb.redi + q));
+      double v = -2.0, tw2 = 0.0;
+      int i = 0x7fffffff, q2 = -1;
+      const int pb = (j & 1) * P;
+      for (int q = lane; q < P; q += 32) {
+        double v2 = __ldcg(jb.redv + pb + q);
+        int i2 = __ldcg(jb.redi + pb + q);
+        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; q2 = pb + q; }
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        argmax_pair(v, i, v2, i2);
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        const int qq = __shfl_xor_sync(0xffffffffu, q2, o);
+        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; q2 = qq; }
       }
-      if (lane == 0) si[0] = i;
+      if (lane == 0) {
+        tw2 = __ldcg(jb.redt + q2);
+        if (s_p != i) s_pos = -1;   // the pivot is another CTA's column
+        s_p = i;
+        s_twp = tw2;
+      }
     }
     __syncthreads();
-    const int p = si[0];
-    const double* pc = W + (long long)p * ldw;
-    double s = 0.0;
-    for (int r = j + tid; r < d; r += NT) {
-      const double v = own ? pc[r] : __ldcg(pc + r);
-      vs[r] = v;
-      s = __fma_rn(v, v, s);
-    }
-    const double ss = block_sum(s, sh);
-    // the step's scalars once (thread 0), broadcast through shared memory:
-    // on this part a replicated FP64 sqrt or divide costs more than a column
-    if (tid == 0) {
-      const double alpha = sqrt(ss);
-      if (j == 0) s_r11 = alpha;
-      double thr_a = jb.ea, thr_r = jb.er * s_r11;
-      if (jb.rule == 1) {
-        const double den = (double)(d - (j + 1) - 1);
-        if (den <= 0.0) { thr_a = 0.0; thr_r = 0.0; }
-        else {
-          const double f = 1.0 + 4.0 * sqrt((double)d) / den * sqrt((double)min(jb.mh, jb.nh));
-          thr_a /= f;
-          thr_r /= f;
-        }
+    const int p = s_p;
+    // ---- (c) pivot column with H_{j-1} applied, exact norm, reflector
+    {
+      const double* pc = W + (long long)p * ldw;
+      const double twp = s_twp;
+      double s = 0.0;
+      for (int r = j + tid; r < d; r += NT) {
+        const double x = __fma_rn(-twp, vp[r], P > 1 ? __ldcg(pc + r) : pc[r]);
+        vc[r] = x;
+        s = __fma_rn(x, x, s);
       }
-      s_stop = (alpha <= thr_a || alpha <= thr_r) ? 1 : 0;
-      if (!s_stop) {
-        const double x0 = vs[j];
+      const double ss = block_sum(s, sh);
+      // thread 0: norm, stop test, tau; thread 32 (another warp, so the two
+      // FP64 divisions run side by side): the scaling of the reflector
+      if (tid == 0 || tid == 32) {
+        const double alpha = sqrt(ss);
+        double thr_a = s_tha, thr_r = s_thr;
+        if (j == 0) {
+          s_r11 = alpha;
+          rank_thresholds(jb, d, 0, alpha, thr_a, thr_r);
+        }
+        const int stop = (alpha <= thr_a || alpha <= thr_r) ? 1 : 0;
+        const double x0 = vc[j];
         const double beta = x0 >= 0.0 ? -alpha : alpha;
-        s_tau = (beta - x0) / beta;
-        s_scal = 1.0 / (x0 - beta);
-        if (p % P == rank) {
-          nrm[p] = -1.0;               // retired
-          __stcg(diag + j, beta);
-          __stcg(jb.piv + j, p);
+        if (tid == 32) {
+          if (!stop) s_scal = 1.0 / (x0 - beta);
+        } else {
+          s_stop = stop;
+          if (!stop) {
+            s_tau = (beta - x0) / beta;
+            const int pos = s_pos;
+            if (pos >= 0) {
+              // the own pivot column leaves the live list
+              __stcg(diag + j, beta);
+              __stcg(jb.piv + j, p);
+              liveg[p] = -1.0;
+              const int last = nl - 1;
+              S.lc[pos] = S.lc[last];
+              S.tw[pos] = S.tw[last];
+              S.nrm[pos] = S.nrm[last];
+              S.orig[pos] = S.orig[last];
+              s_nl = last;
+            } else {
+              s_nl = nl;
+            }
+          }
         }
       }
+      __syncthreads();
+      if (s_stop) { k = j; stopped = 1; break; }
+      nl = s_nl;
+      tau = s_tau;
+      const double scal = s_scal;
+      for (int r = j + 1 + tid; r < d; r += NT) vc[r] *= scal;
+      if (tid == 0) vc[j] = 1.0;
+      __syncthreads();
     }
-    __syncthreads();
-    if (s_stop) { k = j; stopped = 1; break; }
-    const double tau = s_tau, scal = s_scal;
-    for (int r = j + 1 + tid; r < d; r += NT) vs[r] *= scal;
-    if (tid == 0) vs[j] = 1.0;
-    __syncthreads();
-    // reflector on the own live columns, two per warp at a time (eight
-    // independent load streams per lane), then norm down-dating
-    for (int c1 = rank + P * warp; c1 < m; c1 += 2 * P * NW) {
-      const int c2 = c1 + P * NW;
-      const bool l1 = nrm[c1] >= 0.0, l2 = c2 < m && nrm[c2] >= 0.0;
-      if (!l1 && !l2) continue;
-      const int ca = l1 ? c1 : c2;
-      const int cb = (l1 && l2) ? c2 : ca;   // cb == ca: a single column
-      double* colA = W + (long long)ca * ldw;
-      double* colB = W + (long long)cb * ldw;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
-      int r = j + 1 + lane;
-      for (; r + 96 < d; r += 128) {
-        const double v0 = vs[r], v1 = vs[r + 32], v2 = vs[r + 64], v3 = vs[r + 96];
-        a0 = __fma_rn(v0, colA[r], a0);
-        a1 = __fma_rn(v1, colA[r + 32], a1);
-        a2 = __fma_rn(v2, colA[r + 64], a2);
-        a3 = __fma_rn(v3, colA[r + 96], a3);
-        b0 = __fma_rn(v0, colB[r], b0);
-        b1 = __fma_rn(v1, colB[r + 32], b1);
-        b2 = __fma_rn(v2, colB[r + 64], b2);
-        b3 = __fma_rn(v3, colB[r + 96], b3);
-      }
-      for (; r < d; r += 32) {
-        const double v0 = vs[r];
-        a0 = __fma_rn(v0, colA[r], a0);
-        b0 = __fma_rn(v0, colB[r], b0);
-      }
-      const double topA = colA[j], topB = colB[j];
-      const double twA = tau * (warp_sum((a0 + a1) + (a2 + a3)) + topA);
-      const double twB = tau * (warp_sum((b0 + b1) + (b2 + b3)) + topB);
-      const bool two = cb != ca;
-      for (int r2 = j + 1 + lane; r2 < d; r2 += 32) {
-        const double v = vs[r2];
-        colA[r2] = __fma_rn(-twA, v, colA[r2]);
-        if (two) colB[r2] = __fma_rn(-twB, v, colB[r2]);
-      }
-      __syncwarp();
-      for (int q = 0; q < (two ? 2 : 1); ++q) {
-        const int c = q ? cb : ca;
-        double* col = q ? colB : colA;
-        const double rjc = (q ? topB - twB : topA - twA);
-        int recompute = 0;
-        if (lane == 0) {
-          col[j] = rjc;
-          // squared-norm down-date; a result that lost most of its digits
-          // to cancellation (below tol3z of the norm^2 at its last exact
-          // computation) is recomputed from the column
-          const double v = __fma_rn(-rjc, rjc, nrm[c]);
-          if (v <= tol3z * orig[c]) recompute = 1;
-          else nrm[c] = v;
+    // ---- (d) the fused pass: rows r >= j of the own live columns,
+    //   x = W(r,c) - tw_{j-1}(c) v_{j-1}(r);  W(r,c) = x;  dot += v_j(r) x
+    // A warp takes four live columns at a time, eight lanes per column, lane
+    // i of a group one quad (4 rows) of each block of 8 quads, so that every
+    // 16-byte load of the warp touches four 128-byte lines.  Blocks of a
+    // column batch are dealt to the warps round robin; the eight lanes of a
+    // column add their partial dots with three shuffles.
+    {
+      const int q0 = j >> 2, q1 = (d + 3) >> 2;
+      const int B0 = q0 >> 3, NB = ((q1 + 7) >> 3) - B0;
+      const int g = lane >> 3, i8 = lane & 7;
+      for (int b = 0; 4 * b < nl; ++b) {
+        const int t = 4 * b + g;
+        const bool act = t < nl;
+        double* col = W + (long long)(act ? S.lc[t] : 0) * ldw;
+        const double twv = act ? S.tw[t] : 0.0;
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;   // four short chains
+        // two blocks at a time: four 16-byte loads in flight per lane
+        for (int blk = (warp - (b * NB) % NW + NW) % NW; blk < NB; blk += 2 * NW) {
+          int qa = 8 * (B0 + blk) + i8, qb = qa + 8 * NW;
+          const bool va = act && qa >= q0 && qa < q1;
+          const bool vb = act && blk + NW < NB && qb >= q0 && qb < q1;
+          double2 a01, a23, b01, b23;
+          if (va) { const double2* pp = (const double2*)(col + 4 * qa); a01 = pp[0]; a23 = pp[1]; }
+          if (vb) { const double2* pp = (const double2*)(col + 4 * qb); b01 = pp[0]; b23 = pp[1]; }
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const bool v = h2 ? vb : va;
+            if (!v) continue;
+            const int r = 4 * (h2 ? qb : qa);
+            double x[4] = {h2 ? b01.x : a01.x, h2 ? b01.y : a01.y, h2 ? b23.x : a23.x, h2 ? b23.y : a23.y};
+            const double2 p01 = *(const double2*)(vp + r), p23 = *(const double2*)(vp + r + 2);
+            const double2 c01 = *(const double2*)(vc + r), c23 = *(const double2*)(vc + r + 2);
+            const double pv[4] = {p01.x, p01.y, p23.x, p23.y};
+            const double cv[4] = {c01.x, c01.y, c23.x, c23.y};
+            if (r >= j && r + 4 <= d) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) x[u] = __fma_rn(-twv, pv[u], x[u]);
+              acc0 = __fma_rn(cv[0], x[0], acc0);
+              acc1 = __fma_rn(cv[1], x[1], acc1);
+              acc2 = __fma_rn(cv[2], x[2], acc2);
+              acc3 = __fma_rn(cv[3], x[3], acc3);
+              if (r == j) S.top[t] = x[0];
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if (r + u >= j && r + u < d) {
+                  x[u] = __fma_rn(-twv, pv[u], x[u]);
+                  if (u == 0) acc0 = __fma_rn(cv[u], x[u], acc0);
+                  else if (u == 1) acc1 = __fma_rn(cv[u], x[u], acc1);
+                  else if (u == 2) acc2 = __fma_rn(cv[u], x[u], acc2);
+                  else acc3 = __fma_rn(cv[u], x[u], acc3);
+                }
+              }
+              if (r <= j && j < r + 4) {
+                const int u = j - r;   // select without indexing x (keeps it in registers)
+                S.top[t] = u == 0 ? x[0] : (u == 1 ? x[1] : (u == 2 ? x[2] : x[3]));
+              }
+            }
+            double2* pp = (double2*)(col + r);
+            pp[0] = make_double2(x[0], x[1]);
+            pp[1] = make_double2(x[2], x[3]);
+          }
         }
-        recompute = __shfl_sync(0xffffffffu, recompute, 0);
-        if (recompute) {
-          __syncwarp();
-          double s2 = 0.0;
-          for (int r2 = j + 1 + lane; r2 < d; r2 += 32) s2 = __fma_rn(col[r2], col[r2], s2);
-          s2 = warp_sum(s2);
-          if (lane == 0) { nrm[c] = s2; orig[c] = s2; }
-        }
+        double acc = (acc0 + acc1) + (acc2 + acc3);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (act && i8 == 0) S.part[warp * NLMAX + t] = acc;
       }
+      // swap the reflectors: v_j becomes the one to apply next
+      double* tmp = vp;
+      vp = vc;
+      vc = tmp;
+      __syncthreads();
     }
-    __syncthreads();
   }
-  // every R entry and pivot of the group visible before the solve
+
+  // every R entry, pivot and liveness flag of the group visible before the solve
   if (!group_barrier(jb.bar, P, epoch, err, &s_ok)) return;
 
   int accepted = 1;
@@ -290,83 +442,74 @@ __global__ void __launch_bounds__(NT) k_qrcp(const QrcpJob* __restrict__ jobs,
     int base = k;
     for (int c0 = 0; c0 < m; c0 += NT) {
       const int c = c0 + tid;
-      int live = 0;
-      if (c < m) {
-        const double nc = (c % P == 0) ? nrm[c] : __ldcg(nrm + c);
-        live = nc >= 0.0;
-        // columns that were never pivoted (a stop leaves its pivot live)
-        if (live && stopped) live = 1;
-      }
-      // block exclusive scan of `live`
+      const int live = (c < m) && __ldcg(liveg + c) > 0.0;
       const unsigned bal = __ballot_sync(0xffffffffu, live);
       const int wpre = __popc(bal & ((1u << lane) - 1u));
-      if (lane == 0) si[warp] = __popc(bal);
+      if (lane == 0) shi[warp] = __popc(bal);
       __syncthreads();
       int off = base;
-      for (int w = 0; w < warp; ++w) off += si[w];
+      for (int w = 0; w < warp; ++w) off += shi[w];
       int tot = 0;
-      for (int w = 0; w < NW; ++w) tot += si[w];
+      for (int w = 0; w < NW; ++w) tot += shi[w];
       if (live) __stcg(jb.piv + off + wpre, c);
       __syncthreads();
       base += tot;
     }
   }
   if (jb.do_id && accepted && k > 0 && k < m) {
-    // X = R1^{-1} R2 in place on the own surviving columns
-    for (int c = rank + P * warp; c < m; c += P * NW) {
-      if (nrm[c] < 0.0) continue;
-      double* col = W + (long long)c * ldw;
+    // X = R1^{-1} R2 in place on the own surviving columns (warp per column)
+    double* rd = S.v0;   // 1 / R_ii
+    for (int i = tid; i < k; i += NT) rd[i] = 1.0 / __ldcg(diag + i);
+    __syncthreads();
+    for (int t = warp; t < nl; t += NW) {
+      double* col = W + (long long)S.lc[t] * ldw;
       for (int i = k - 1; i >= 0; --i) {
         __syncwarp();
-        const double xi = col[i] / __ldcg(diag + i);
+        const double xi = col[i] * rd[i];
         __syncwarp();
         if (lane == 0) col[i] = xi;
         const double* ri = W + (long long)__ldcg(jb.piv + i) * ldw;
-        for (int r = lane; r < i; r += 32)
-          col[r] = __fma_rn(-(own ? ri[r] : __ldcg(ri + r)), xi, col[r]);
-      }
-    }
-    if (in_smem) {
-      // X back to the global workspace: W(0:k, c) of the surviving columns
-      __syncthreads();
-      for (int c = warp; c < m; c += NW) {
-        if (nrm[c] < 0.0) continue;
-        for (int r = lane; r < k; r += 32) jb.W[r + (long long)c * jb.ldw] = W[r + (long long)c * ldw];
+        for (int r = lane; r < i; r += 32) col[r] = __fma_rn(-__ldcg(ri + r), xi, col[r]);
       }
     }
   }
   if (rank == 0 && tid == 0) { jb.out[0] = k; jb.out[1] = stopped; jb.out[2] = accepted; }
 }
 
+size_t smem_for(int dmax) {
+  const size_t dp = ((size_t)dmax + 3) & ~(size_t)3;
+  return sizeof(double) * (2 * dp + (NW + 4) * (size_t)NLMAX) + 2 * sizeof(int) * NLMAX;
+}
+
 }  // namespace
 
-int qrcp_group_capacity() {
+int qrcp_cols_per_cta() { return NLMAX; }
+
+// Co-resident CTAs of k_qrcp on this device for sample width dmax.
+int qrcp_group_capacity(int dmax) {
   int dev = 0, sms = 0, per = 0;
+  const size_t sm = smem_for(dmax);
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qrcp, NT, 64 * 1024) != cudaSuccess) return 0;
-  return sms * (per < 2 ? per : 2);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qrcp, NT, sm) != cudaSuccess) return 0;
+  return sms * per;
 }
 
 // map == nullptr: one CTA per job (ordinary launch); otherwise map[cta] =
-// (job, rank) and the launch is cooperative.  d_max: largest d of the jobs;
-// smem_w: dynamic shared memory to request so that single-CTA jobs with
-// (m + 1) d doubles up to that size keep W in shared memory (0: none).
-cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, size_t smem_w,
-                        int* err, cudaStream_t st) {
+// (job, rank) and the launch is cooperative.  dmax: largest d of the jobs.
+cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int dmax, int* err,
+                        cudaStream_t st) {
   if (nctas <= 0) return cudaSuccess;
-  size_t sm = sizeof(double) * (size_t)(d_max > 0 ? d_max : 1);
-  if (!map_dev && smem_w > sm) sm = smem_w;
-  cudaError_t e = cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sm > 64 * 1024 ? sm : 64 * 1024));
+  const size_t sm = smem_for(dmax);
+  cudaError_t e = cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (!map_dev) {
-    k_qrcp<<<nctas, NT, sm, st>>>(jobs_dev, nullptr, err, sm);
+    k_qrcp<<<nctas, NT, sm, st>>>(jobs_dev, nullptr, err, dmax);
     return cudaGetLastError();
   }
-  void* args[] = {(void*)&jobs_dev, (void*)&map_dev, (void*)&err, (void*)&sm};
+  void* args[] = {(void*)&jobs_dev, (void*)&map_dev, (void*)&err, (void*)&dmax};
   return cudaLaunchCooperativeKernel((const void*)k_qrcp, dim3(nctas), dim3(NT), args, sm, st);
 }
 
