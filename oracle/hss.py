@@ -33,10 +33,12 @@ Readings (see the design notes for the full list):
      an Incrementing basis Q with m columns is sufficient.
  P17 the column ranges of Algorithm 3 are "all columns so far" for an
      UNTOUCHED node and "the columns added by the last growth" otherwise.
- P18 Incrementing at a node touched for the first time tests all of its
-     columns as the first block; later blocks are the newly added columns;
-     a side that passed stays passed; the node is COMPRESSED when both
-     sides have passed.
+ P18 Incrementing tests a side's columns in the blocks in which they were
+     drawn (d0 columns, then Delta d per growth), in order, stopping at the
+     first sufficient block: a node touched for the first time after growth
+     runs Algorithm 5 over its earlier blocks within the pass, exactly as if
+     it had been tested at every pass.  A side that passed stays passed; the
+     node is COMPRESSED when both sides have passed.
  P19 the loop ends after a failed pass at d = d_max (NOT_CONVERGED); the
      last growth is clipped so that d <= d_max.
 """
@@ -120,7 +122,7 @@ def compress(src, R: np.ndarray, opts: Options) -> Result:
     d_max = min(opts.d_max, R.shape[1])
     d = min(opts.d0, d_max)
     Sr, Sc = A.sample(R[:, :d])
-    ctx = dict(A=A, R=R, opts=opts, nodes=nodes, d_prev=0, d=d)
+    ctx = dict(A=A, R=R, opts=opts, nodes=nodes, d_prev=0, d=d, bounds=[d])
     n_adapt = 0
     passes = []
     while True:
@@ -138,6 +140,7 @@ def compress(src, R: np.ndarray, opts: Options) -> Result:
         Sc = np.hstack([Sc, Scn])
         ctx["d_prev"], ctx["d"] = d, d + dd
         d += dd
+        ctx["bounds"].append(d)
         n_adapt += 1
 
 
@@ -252,16 +255,18 @@ def _node_sufficient(ctx, t) -> bool:
             out.append((piv, Rf, k))
         _set_id(t, out, d)
         return True
-    # Incrementing (Algorithm 5 applied to the node's samples, P18)
+    # Incrementing (Algorithm 5 applied to the node's samples, block by
+    # block as they were drawn, P18)
     for side, S in (("r", t.Sr), ("c", t.Sc)):
         st = t.inc.setdefault(side, dict(Q=np.zeros((S.shape[0], 0)), rho=None,
                                          tested=0, done=False))
+        while not st["done"] and st["tested"] < d:
+            end = min(b for b in ctx["bounds"] if b > st["tested"])
+            blk = S[:, st["tested"]:end]
+            st["tested"] = end
+            st["done"] = incrementing_block_test(blk, st, er, ea)
         if st["done"]:
             st["tested"] = d
-            continue
-        blk = S[:, st["tested"]:d]
-        st["tested"] = d
-        st["done"] = incrementing_block_test(blk, st, er, ea)
     if not (t.inc["r"]["done"] and t.inc["c"]["done"]):
         return False
     out = []

@@ -181,6 +181,7 @@ struct hss_matrix_s {
   std::vector<Node> nodes;
   std::vector<std::vector<int>> by_level;
   int max_level = 0;
+  std::vector<int> bounds;   // sample widths after each growth (Incrementing blocks)
   Arena arena;
   Scratch scratch;
   double* R = nullptr;     // n x dmax col-major (ld n)
@@ -791,24 +792,32 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         reqs.push_back({id, 1, 1});
       }
     } else {
-      // Incrementing: project the untested columns and run the block test
+      // Incrementing: test the untested columns of every side block by block
+      // as they were drawn (d0, then each growth), all sides of the level
+      // together, one round per block, until each side passes or runs out
       struct Sd { int node, side; };
-      std::vector<Sd> sides;
-      for (int id : lw.cand) {
-        Node& t = H->nodes[id];
-        for (int sd = 0; sd < 2; ++sd) {
-          Side& s = sd ? t.c : t.r;
-          if (s.done) s.tested = d;
-          else if (d > s.tested) sides.push_back({id, sd});
+      for (;;) {
+        std::vector<Sd> sides;
+        for (int id : lw.cand) {
+          Node& t = H->nodes[id];
+          for (int sd = 0; sd < 2; ++sd) {
+            Side& s = sd ? t.c : t.r;
+            if (s.done) s.tested = d;
+            else if (d > s.tested) sides.push_back({id, sd});
+          }
         }
-      }
-      if (!sides.empty()) {
+        if (sides.empty()) break;
         CK(H->timer.mark(PH_TEST, st));
         H->scratch.reset();
+        auto block_end = [&](int tested) {
+          for (int bnd : H->bounds)
+            if (bnd > tested) return std::min(bnd, d);
+          return d;
+        };
         size_t need = 0;
         for (auto& x : sides) {
           Side& s = x.side ? H->nodes[x.node].c : H->nodes[x.node].r;
-          size_t b = d - s.tested, m = std::max(s.m, 1);
+          size_t b = block_end(s.tested) - s.tested, m = std::max(s.m, 1);
           need += Scratch::rnd(8 * m * b) + Scratch::rnd(8 * std::max<size_t>(std::max(s.q, s.m), 1) * b) +
                   Scratch::rnd(8 * b) + Scratch::rnd(8 * 4) + Scratch::rnd(8);
         }
@@ -817,12 +826,14 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         std::vector<GemmJob> g1, g2, g3;
         double* res0 = nullptr;
         int* flag0 = nullptr;
+        int bmax = 0;
         for (auto& x : sides) {
           Node& t = H->nodes[x.node];
           Side& s = x.side ? t.c : t.r;
           IncJob j;
           memset(&j, 0, sizeof j);
-          const int b = d - s.tested, m = s.m;
+          const int b = block_end(s.tested) - s.tested, m = s.m;
+          bmax = std::max(bmax, b);
           j.S = s.S; j.lds = H->dmax; j.m = m; j.c0 = s.tested; j.b = b;
           j.Q = s.Q; j.q = s.q;
           j.Sh = (double*)H->scratch.take(8 * (size_t)std::max(m, 1) * b);
@@ -832,7 +843,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
           j.er = H->o.rtol * sc; j.ea = H->o.atol * sc;
           j.rho = s.rho;
           ij.push_back(j);
-          // Sh = S(:, tested:d)
+          // Sh = S(:, tested:tested+b)
           GemmJob c = gemm_job();
           c.M = m; c.N = b; c.K = 0;
           c.C0 = opnd(s.S + s.tested, H->dmax, 1);
@@ -858,18 +869,33 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         res0 = (double*)H->scratch.take(sizeof(double) * 4 * ij.size());
         flag0 = (int*)H->scratch.take(sizeof(int) * 2 * ij.size());
         for (size_t i = 0; i < ij.size(); ++i) { ij[i].res = res0 + 4 * i; ij[i].flag = flag0 + 2 * i; }
-        CKS(run_gemms(H, g1, st));
+        CKS(run_gemms(H, g1, st, "test-copy"));
         for (int rep = 0; rep < 2; ++rep) {   // (I - Q Q^T)^2
-          CKS(run_gemms(H, g2, st));
-          CKS(run_gemms(H, g3, st));
+          CKS(run_gemms(H, g2, st, "test-QtS"));
+          CKS(run_gemms(H, g3, st, "test-S-QT"));
         }
         IncJob* dj;
         CKS(upload_jobs(H, ij, &dj, st));
         if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "test scratch sized too small");
+        if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
         CK(launch_inc_qr(dj, (int)ij.size(), st));
         H->launches++;
+        if (H->trace) {
+          CK(cudaEventRecord(H->trace_ev[1], st));
+          CK(cudaEventSynchronize(H->trace_ev[1]));
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, H->trace_ev[0], H->trace_ev[1]);
+          int mm = 0, qq = 0;
+          for (auto& x : sides) {
+            const Side& s = x.side ? H->nodes[x.node].c : H->nodes[x.node].r;
+            mm = std::max(mm, s.m);
+            qq = std::max(qq, s.q);
+          }
+          fprintf(stderr, "[hss trace] inc_qr level %d sides %zu max_m %d max_q %d b %d  %.3f ms\n", lev,
+                  sides.size(), mm, qq, bmax, ms);
+        }
         CK(cudaFreeAsync(dj, st));
-        // read flags and res together: copy both into the pinned buffer
+        // read flags and res together
         std::vector<int> flags(2 * ij.size());
         std::vector<double> res(4 * ij.size());
         CK(cudaMemcpyAsync(flags.data(), flag0, sizeof(int) * flags.size(), cudaMemcpyDeviceToHost, st));
@@ -878,7 +904,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         H->st.bytes_d2h += (long long)(sizeof(int) * flags.size() + sizeof(double) * res.size());
         for (size_t i = 0; i < sides.size(); ++i) {
           Side& s = sides[i].side ? H->nodes[sides[i].node].c : H->nodes[sides[i].node].r;
-          s.tested = d;
+          s.tested = block_end(s.tested);
           s.q = flags[2 * i + 1];
           if (s.rho < 0.0 && res[4 * i + 3] >= 0.0) s.rho = res[4 * i + 3];
           s.done = flags[2 * i] != 0;
@@ -1009,6 +1035,7 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
 
   CK(H->timer.mark(PH_OTHER, st));
   int d = std::min(o->d0, H->dmax), d_prev = 0;
+  H->bounds.assign(1, d);
   CKS(sample_columns(H, 0, d, st, own_R));
   for (;;) {
     CKS(run_pass(H, d_prev, d, st));
@@ -1019,6 +1046,7 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     CKS(sample_columns(H, d, d + dd, st, own_R));
     d_prev = d;
     d += dd;
+    H->bounds.push_back(d);
     H->n_adapt++;
   }
   CK(H->timer.mark(PH_OTHER, st));
