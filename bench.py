@@ -273,7 +273,7 @@ def run_gpu(args):
                     "traffic": traffic_from_profiles("k_sample_tc_gauss8_n16384")}
     ach_id = s0.flop_id / max(s0.ms_id / 1e3, 1e-12) / 1e12
     r_id = {"bound": "alu", "achieved": ach_id, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach_id / FP64_PEAK_TFLOPS, "kernel": "k_qrcp (+ k_qrcp_group)", "peak_source": fp64_src,
+            "frac": ach_id / FP64_PEAK_TFLOPS, "kernel": "k_qrcp", "peak_source": fp64_src,
             "traffic": traffic_from_profiles("k_qrcp_gauss8_n16384")}
     roof, roof_other = (r_id, r_sample) if s0.ms_id > s0.ms_sample else (r_sample, r_id)
 
@@ -305,6 +305,25 @@ def run_gpu(args):
                  "phases_ms": {"sample": q.ms_sample, "rng_check": q.ms_rng, "id": q.ms_id,
                                "test": q.ms_test, "merge_reduce": q.ms_merge, "total": q.ms_total}}
 
+    # --- noise floor of the mixed sampling on this matrix (outside the timed
+    # region): ||S_mixed - S_fp64||_F / ||S_fp64||_F over 128 columns, R
+    # rounded to the tensor format as in the compression
+    noise = None
+    if args.precision != "fp64":
+        nc = 128
+        Rn = torch.empty((nc, n), dtype=torch.float64, device=dev).t()
+        hss.hss_random_normal(cfg["seed"] + 101, n, 0, nc, Rn,
+                              round_mode=1 if args.precision == "tf32x2" else 2, stream=stream)
+        S = [torch.empty((n, nc), dtype=torch.float64, device=dev) for _ in range(4)]   # row-major samples
+        hss.hss_sample_offdiag(src, cfg["leaf"], PREC["fp64"], Rn, S[0], S[1], stream=stream)
+        hss.hss_sample_offdiag(src, cfg["leaf"], PREC[args.precision], Rn, S[2], S[3], stream=stream)
+        torch.cuda.synchronize()
+        noise = {"columns": nc,
+                 "rel_r": float(torch.linalg.norm(S[2] - S[0]) / torch.linalg.norm(S[0])),
+                 "rel_c": float(torch.linalg.norm(S[3] - S[1]) / torch.linalg.norm(S[1])),
+                 "rtol": cfg["rtol"]}
+        del S, Rn
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_n)
@@ -324,6 +343,8 @@ def run_gpu(args):
                       "test": s0.ms_test, "merge_reduce": s0.ms_merge, "total": s0.ms_total},
         "roofline": roof, "roofline_other": roof_other, "e2e": e2e, "clocks": clocks.summary(),
     }
+    if noise is not None:
+        out["noise_floor"] = noise
     if plain is not None:
         out["fp64_plain"] = plain
         out["speedup_vs_fp64_plain"] = plain["compress_s"] / out["compress_s"]
