@@ -573,9 +573,19 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     // number of CTAs on every SM, so that no SM runs a double share), each
     // CTA with at most NL columns
     for (size_t i = b0; i < b1; ++i) P[i] = std::max(1, (mj[i] + NL - 1) / NL);
-    // hand the remaining slots to the jobs with the most columns per CTA
+    // hand the remaining slots to the jobs with the most work per CTA; the
+    // work of a side is sum_j (d - j)(m - j) over its expected pivot steps:
+    // the rank of its previous attempt (Doubling repeats a failed side at
+    // twice the width) with some growth, else min(m, d)
+    std::vector<double> wk(nj, 0.0);
+    for (size_t i = b0; i < b1; ++i) {
+      const Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
+      const double m = mj[i], dd = d, kmx = std::min(m, dd);
+      const double k = s.qr_k > 0 ? std::min(kmx, 1.25 * s.qr_k + 16.0) : kmx;
+      wk[i] = dd * m * k - 0.5 * (dd + m) * k * k + k * k * k / 3.0 + 1.0;
+    }
     std::priority_queue<std::pair<double, size_t>> pq;
-    for (size_t i = b0; i < b1; ++i) pq.push({(double)mj[i] / P[i], i});
+    for (size_t i = b0; i < b1; ++i) pq.push({wk[i] / P[i], i});
     while (used < cap && !pq.empty()) {
       auto top = pq.top();
       pq.pop();
@@ -583,7 +593,7 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
       if (mj[i] / (P[i] + 1) < 4) continue;   // keep at least four columns per CTA
       P[i]++;
       used++;
-      pq.push({(double)mj[i] / P[i], i});
+      pq.push({wk[i] / P[i], i});
     }
     bool group = false;
     for (size_t i = b0; i < b1; ++i) group = group || P[i] > 1;
@@ -594,8 +604,8 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   for (size_t i = 0; i < nj; ++i) {
     need += Scratch::rnd(sizeof(double) * (size_t)ldw * mj[i]) + Scratch::rnd(sizeof(double) * mj[i]) +
             Scratch::rnd(sizeof(double) * (size_t)std::max(1, std::min(mj[i], d))) +
-            Scratch::rnd(sizeof(unsigned)) + 2 * Scratch::rnd(sizeof(double) * 2 * P[i]) +
-            Scratch::rnd(sizeof(int) * 2 * P[i]);
+            Scratch::rnd(sizeof(unsigned)) + Scratch::rnd(sizeof(double) * 4 * P[i]) +
+            Scratch::rnd(sizeof(double) * 2 * P[i]);
   }
   need += Scratch::rnd(sizeof(int) * 3 * nj);
   CK(H->scratch.ensure(need, st));
@@ -623,9 +633,8 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     j.out = outs + 3 * i;
     j.P = P[i];
     j.bar = bars + i;
-    j.redv = (double*)H->scratch.take(sizeof(double) * 2 * P[i]);
+    j.redv = (double*)H->scratch.take(sizeof(double) * 4 * P[i]);   // 2 P (key, index) pairs
     j.redt = (double*)H->scratch.take(sizeof(double) * 2 * P[i]);
-    j.redi = (int*)H->scratch.take(sizeof(int) * 2 * P[i]);
     wbuf.push_back(j.W);
     jobs.push_back(j);
   }
@@ -662,6 +671,7 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   CKS(readback(H, outs, sizeof(int) * 3 * jobs.size(), st));
   double tr_flop = 0.0;
   int tr_m = 0, tr_k = 0;
+  double tr_wmax = 0.0;
   for (size_t i = 0; i < reqs.size(); ++i) {
     Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
     s.qr_k = H->h_pinned[3 * i];
@@ -676,13 +686,17 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     tr_flop += f;
     tr_m = std::max(tr_m, jobs[i].m);
     tr_k = std::max(tr_k, s.qr_k);
+    tr_wmax = std::max(tr_wmax, f / P[i]);
   }
   if (H->trace) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, H->trace_ev[0], H->trace_ev[1]);
+    // balance: the work per CTA of the busiest group against the mean
     fprintf(stderr,
-            "[hss trace] qrcp level %d jobs %zu batches %d ctas %d max_m %d d %d max_k %d  %.3f ms  %.1f GFLOP/s\n",
-            H->nodes[reqs[0].node].level, nj, nbatch, ctas_total, tr_m, d, tr_k, ms, tr_flop / (ms * 1e6));
+            "[hss trace] qrcp level %d jobs %zu batches %d ctas %d max_m %d d %d max_k %d  %.3f ms  %.1f GFLOP/s"
+            "  balance %.2f\n",
+            H->nodes[reqs[0].node].level, nj, nbatch, ctas_total, tr_m, d, tr_k, ms, tr_flop / (ms * 1e6),
+            tr_flop / std::max(1.0, tr_wmax * ctas_total));
   }
   return HSS_OK;
 }

@@ -95,8 +95,8 @@ struct QrcpJob {
   // group (multi-CTA) form only
   int P;                // CTAs working on this job
   unsigned* bar;        // group barrier counter, zero before the launch
-  double* redv;         // 2 P partial maxima (two steps in flight)
-  int* redi;            // 2 P partial argmax indices
+  double* redv;         // 2 P partial maxima as 16-byte (norm bits, column) pairs,
+                        // two steps in flight, 16-byte aligned
   double* redt;         // 2 P pending-update coefficients of the candidates
 };
 

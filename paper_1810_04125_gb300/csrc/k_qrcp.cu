@@ -53,9 +53,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// (v, i) <- the larger norm, lowest column index on ties
-__device__ __forceinline__ void argmax_pair(double& v, int& i, int& pos, double v2, int i2, int pos2) {
-  if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; pos = pos2; }
+// (k, i) <- the larger key (a non-negative norm's bit pattern), lowest
+// column index on ties
+__device__ __forceinline__ void key_max(unsigned long long& k, int& i, int& pos, unsigned long long k2, int i2,
+                                        int pos2) {
+  if (k2 > k || (k2 == k && i2 < i)) { k = k2; i = i2; pos = pos2; }
 }
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -162,10 +164,11 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
   double* vp = S.v0;        // v_{j-1}
   double* vc = S.v1;        // v_j
   __shared__ double sh[NW];
-  __shared__ double shv[NW], sht[NW];
+  __shared__ unsigned long long shk[NW];
   __shared__ int shi[NW], shp[NW];
   __shared__ int s_ok, s_p, s_pos, s_stop, s_nl, s_nrc;
-  __shared__ double s_twp, s_tau, s_scal, s_r11, s_tha, s_thr;
+  __shared__ double s_twp, s_tau, s_scal, s_r11;
+  __shared__ double s_th[2][2];   // stop thresholds (eps_a, eps_r |R_11|) by step parity
   unsigned epoch = 0;
 
   // own columns, W = S^T for them, initial squared norms
@@ -200,23 +203,18 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
 
   const int kmax = min(d, m);
   int k = kmax, stopped = 0;
+  if (tid == 0) s_nrc = 0;
+  __syncthreads();
   const double tol3z = 1.4901161193847656e-08;   // sqrt(2^-52)
   double tau = 0.0;
   for (int j = 0; j <= kmax; ++j) {
     // ---- (a) finish step j-1 on the own live columns: tw_{j-1} from the
     // partial dots, row j-1 of R, norm down-date; local argmax
-    if (tid == 0) s_nrc = 0;
-    // the thresholds of step j (R_11 known from step 0 on), off the
-    // critical path of the pivot step
-    if (tid == 64 && j >= 1 && j < kmax) rank_thresholds(jb, d, j, s_r11, s_tha, s_thr);
-    __syncthreads();
-    double bv = -1.0;
-    int bi = 0x7fffffff, bp = -1;
     for (int t = tid; t < nl; t += NT) {
       if (j >= 1) {
-        double dot = 0.0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) dot += S.part[w * NLMAX + t];
+        const double* pt = S.part + t;
+        const double dot = ((pt[0] + pt[NLMAX]) + (pt[2 * NLMAX] + pt[3 * NLMAX])) +
+                           ((pt[4 * NLMAX] + pt[5 * NLMAX]) + (pt[6 * NLMAX] + pt[7 * NLMAX]));
         const double twv = tau * dot;
         S.tw[t] = twv;
         const double rjc = S.top[t] - twv;
@@ -244,27 +242,31 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
       }
       __syncthreads();
     }
-    for (int t = tid; t < nl; t += NT) argmax_pair(bv, bi, bp, S.nrm[t], S.lc[t], t);
+    // argmax on integer keys: the bit patterns of non-negative doubles are
+    // ordered like their values (no FP64 compares on the critical path)
+    unsigned long long bk = 0ull;
+    int bi = 0x7fffffff, bp = -1;
+    for (int t = tid; t < nl; t += NT)
+      key_max(bk, bi, bp, (unsigned long long)__double_as_longlong(S.nrm[t]), S.lc[t], t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
       const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
       const int p2 = __shfl_xor_sync(0xffffffffu, bp, o);
-      argmax_pair(bv, bi, bp, v2, i2, p2);
+      key_max(bk, bi, bp, k2, i2, p2);
     }
-    if (lane == 0) { shv[warp] = bv; shi[warp] = bi; shp[warp] = bp; }
+    if (lane == 0) { shk[warp] = bk; shi[warp] = bi; shp[warp] = bp; }
     __syncthreads();
     if (tid == 0) {
-      double v = shv[0];
+      unsigned long long kk = shk[0];
       int i = shi[0], pos = shp[0];
-      for (int w = 1; w < NW; ++w) argmax_pair(v, i, pos, shv[w], shi[w], shp[w]);
+      for (int w = 1; w < NW; ++w) key_max(kk, i, pos, shk[w], shi[w], shp[w]);
       const double twc = pos >= 0 ? S.tw[pos] : 0.0;
       if (P > 1) {
         // partials of step j in buffer j & 1: a CTA that runs ahead writes the
         // next step's into the other buffer while the group still reads these
         const int pb = (j & 1) * P + rank;
-        __stcg(jb.redv + pb, v);
-        __stcg(jb.redi + pb, i);
+        __stcg((ulonglong2*)jb.redv + pb, make_ulonglong2(kk, (unsigned long long)(unsigned)i));
         __stcg(jb.redt + pb, twc);
       }
       s_p = i;
@@ -274,23 +276,25 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
     // ---- (b) the pivot of step j over the group
     if (!group_barrier(jb.bar, P, epoch, err, &s_ok)) return;
     if (P > 1 && warp == 0) {
-      double v = -2.0, tw2 = 0.0;
+      unsigned long long kk = 0ull;
       int i = 0x7fffffff, q2 = -1;
+      double tw2 = 0.0;
       const int pb = (j & 1) * P;
       for (int q = lane; q < P; q += 32) {
-        double v2 = __ldcg(jb.redv + pb + q);
-        int i2 = __ldcg(jb.redi + pb + q);
-        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; q2 = pb + q; }
+        const ulonglong2 e = __ldcg((const ulonglong2*)jb.redv + pb + q);
+        const double t2 = __ldcg(jb.redt + pb + q);
+        const int i2 = (int)(unsigned)e.y;
+        if (e.x > kk || (e.x == kk && i2 < i)) { kk = e.x; i = i2; q2 = q; tw2 = t2; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, kk, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        const int qq = __shfl_xor_sync(0xffffffffu, q2, o);
-        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; q2 = qq; }
+        const double t2 = __shfl_xor_sync(0xffffffffu, tw2, o);
+        if (k2 > kk || (k2 == kk && i2 < i)) { kk = k2; i = i2; tw2 = t2; }
       }
+      (void)q2;
       if (lane == 0) {
-        tw2 = __ldcg(jb.redt + q2);
         if (s_p != i) s_pos = -1;   // the pivot is another CTA's column
         s_p = i;
         s_twp = tw2;
@@ -313,10 +317,13 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
       // FP64 divisions run side by side): the scaling of the reflector
       if (tid == 0 || tid == 32) {
         const double alpha = sqrt(ss);
-        double thr_a = s_tha, thr_r = s_thr;
+        double thr_a, thr_r;
         if (j == 0) {
-          s_r11 = alpha;
+          if (tid == 0) s_r11 = alpha;
           rank_thresholds(jb, d, 0, alpha, thr_a, thr_r);
+        } else {
+          thr_a = s_th[j & 1][0];
+          thr_r = s_th[j & 1][1];
         }
         const int stop = (alpha <= thr_a || alpha <= thr_r) ? 1 : 0;
         const double x0 = vc[j];
@@ -345,6 +352,11 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
           }
         }
       }
+      if (tid == 64 && j + 1 < kmax) {
+        // the thresholds of the next step, beside the two divisions above
+        const double r11 = j == 0 ? sqrt(ss) : s_r11;
+        rank_thresholds(jb, d, j + 1, r11, s_th[(j + 1) & 1][0], s_th[(j + 1) & 1][1]);
+      }
       __syncthreads();
       if (s_stop) { k = j; stopped = 1; break; }
       nl = s_nl;
@@ -362,6 +374,7 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
     // column batch are dealt to the warps round robin; the eight lanes of a
     // column add their partial dots with three shuffles.
     {
+      if (tid == 0) s_nrc = 0;   // read for the last time before the pivot step
       const int q0 = j >> 2, q1 = (d + 3) >> 2;
       const int B0 = q0 >> 3, NB = ((q1 + 7) >> 3) - B0;
       const int g = lane >> 3, i8 = lane & 7;
