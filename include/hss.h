@@ -135,6 +135,19 @@ typedef struct hss_matrix_s* hss_matrix;   /* opaque; owns device memory    */
 hss_status hss_compress(const hss_source* A, const hss_opts* opts, void* stream,
                         hss_matrix* out);
 
+/* hss_compress for a batch of independent matrices (the paper compresses
+ * one matrix per call; the batch has no counterpart there): A[count] and
+ * opts[count] (one options struct per matrix), out[count] receives the
+ * handles.  The matrices are compressed side by side on worker streams
+ * (largest n first) that start after the work already queued on `stream`;
+ * `stream` waits for all of them before the call returns.  Errors: on any
+ * status other than HSS_OK / HSS_ERR_NOT_CONVERGED every handle is freed,
+ * out[] is all NULL and the first failing matrix's status is returned (its
+ * message in hss_last_error); HSS_ERR_NOT_CONVERGED when some matrix did
+ * not converge (all handles valid, as for hss_compress). */
+hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int count, void* stream,
+                                hss_matrix* out);
+
 /* Y = H X for a compressed handle: the O(r n) product of section 2.1
  * (up-sweep x^_tau = V_tau^T [...], sibling coupling with B12/B21, down-sweep
  * with U_tau, leaves D_tau).  X, Y: device col-major n x nrhs (ldx, ldy >= n);

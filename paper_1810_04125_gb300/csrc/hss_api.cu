@@ -19,6 +19,10 @@
 
 #include "hss_internal.h"
 
+#include <atomic>
+#include <mutex>
+#include <thread>
+
 using namespace hss;
 
 namespace {
@@ -533,6 +537,11 @@ void reduce_jobs(hss_matrix_s* H, Node& t, int cs, int d, std::vector<GemmJob>& 
   }
 }
 
+std::mutex& coop_launch_mutex() {
+  static std::mutex m;
+  return m;
+}
+
 // QRCP/ID over all columns [0, d) of the listed node sides.
 struct QrcpReq { int node; int side; int rule; };
 
@@ -645,6 +654,13 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
   QrcpJob* dj;
   CKS(upload_jobs(H, jobs, &dj, st));
+  // A cooperative launch needs all of its CTAs resident at once: compressions
+  // running side by side (hss_compress_batched) take turns with them, the
+  // lock held until the launch has finished (the flag read-back below).
+  bool any_group = false;
+  for (const Batch& b : batches) any_group = any_group || b.group;
+  std::unique_lock<std::mutex> coop(coop_launch_mutex(), std::defer_lock);
+  if (any_group) coop.lock();
   int ctas_total = 0;
   for (const Batch& b : batches) {
     if (b.group) {
@@ -666,6 +682,7 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   CK(cudaFreeAsync(dj, st));
   if (H->trace) CK(cudaEventRecord(H->trace_ev[1], st));
   CKS(readback(H, H->d_flag + 2, 2 * sizeof(int), st));
+  if (coop.owns_lock()) coop.unlock();
   if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "group QRCP barrier gave up (code %d)", H->h_pinned[0]);
   if (H->h_pinned[1]) return fail(HSS_ERR_TIMEOUT, "tensor-core tile product gave up waiting (code %d)", H->h_pinned[1]);
   CKS(readback(H, outs, sizeof(int) * 3 * jobs.size(), st));
@@ -1143,6 +1160,75 @@ hss_status hss_compress(const hss_source* A, const hss_opts* o, void* stream, hs
   *out = H;
   if (!H->converged)
     return fail(HSS_ERR_NOT_CONVERGED, "root not compressed at d = d_max = %d", H->d_final);
+  return HSS_OK;
+}
+
+hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int count, void* stream,
+                                hss_matrix* out) {
+  if (count < 0) return fail(HSS_ERR_ARG, "count must be >= 0 (got %d)", count);
+  if (count == 0) return HSS_OK;
+  if (!A || !opts || !out) return fail(HSS_ERR_ARG, "NULL argument");
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ready;
+  CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  CK(cudaEventRecord(ready, st));
+  // largest problems first, handed out to the workers one at a time
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return A[a].n > A[b].n; });
+  const int T = std::min(count, 4);
+  std::atomic<int> next(0);
+  std::vector<hss_status> status(count, HSS_OK);
+  std::vector<std::string> msg(count);
+  std::vector<cudaEvent_t> done(T, nullptr);
+  std::vector<hss_status> wstat(T, HSS_OK);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  auto worker = [&](int w) {
+    cudaSetDevice(dev);
+    cudaStream_t ws;
+    if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) {
+      wstat[w] = HSS_ERR_CUDA;
+      return;
+    }
+    for (int q = next++; q < count; q = next++) {
+      const int i = order[q];
+      status[i] = hss_compress(&A[i], &opts[i], ws, &out[i]);
+      if (status[i] != HSS_OK) msg[i] = g_err;
+    }
+    if (cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(done[w], ws) != cudaSuccess)
+      wstat[w] = HSS_ERR_CUDA;
+    cudaStreamDestroy(ws);
+  };
+  std::vector<std::thread> th;
+  for (int w = 0; w < T; ++w) th.emplace_back(worker, w);
+  for (auto& t : th) t.join();
+  for (int w = 0; w < T; ++w)
+    if (done[w]) {
+      cudaStreamWaitEvent(st, done[w], 0);
+      cudaEventDestroy(done[w]);
+    }
+  cudaEventDestroy(ready);
+  hss_status first = HSS_OK;
+  int at = -1;
+  for (int w = 0; w < T; ++w)
+    if (wstat[w] != HSS_OK) { first = wstat[w]; break; }
+  for (int i = 0; i < count && first == HSS_OK; ++i)
+    if (status[i] != HSS_OK && status[i] != HSS_ERR_NOT_CONVERGED) { first = status[i]; at = i; }
+  if (first != HSS_OK) {
+    for (int i = 0; i < count; ++i) {
+      hss_free(out[i]);
+      out[i] = nullptr;
+    }
+    if (at >= 0) return fail(first, "matrix %d: %s", at, msg[at].c_str());
+    return fail(first, "worker stream setup failed");
+  }
+  for (int i = 0; i < count; ++i)
+    if (status[i] == HSS_ERR_NOT_CONVERGED)
+      return fail(HSS_ERR_NOT_CONVERGED, "matrix %d: %s", i, msg[i].c_str());
   return HSS_OK;
 }
 

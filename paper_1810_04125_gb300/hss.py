@@ -22,7 +22,7 @@ HSS_PREC_FP64, HSS_PREC_TF32X2, HSS_PREC_BF16X3 = 0, 1, 2
 HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE = 0, 1, 2, 3
 HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
 
-EXPORTS = ["hss_compress", "hss_matvec", "hss_get_stats", "hss_get_node", "hss_export_node",
+EXPORTS = ["hss_compress", "hss_compress_batched", "hss_matvec", "hss_get_stats", "hss_get_node", "hss_export_node",
            "hss_free", "hss_status_str", "hss_last_error", "hss_rcb_order",
            "hss_random_normal", "hss_sample_offdiag", "hss_sample_offdiag_noalloc"]
 
@@ -69,6 +69,7 @@ def lib():
         L = C.CDLL(LIB_PATH)
         vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.c_double
         L.hss_compress.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), vp, C.POINTER(vp)]
+        L.hss_compress_batched.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), i, vp, C.POINTER(vp)]
         L.hss_matvec.argtypes = [vp, i, vp, ll, vp, ll, vp]
         L.hss_get_stats.argtypes = [vp, C.POINTER(hss_stats)]
         L.hss_get_node.argtypes = [vp, i, C.POINTER(hss_node_info)]
@@ -180,6 +181,23 @@ def hss_sample_offdiag_noalloc(source, leaf, precision, R, Sr, Sc, stream=None):
     lds = (Sr if Sr is not None else Sc).stride(0)
     _check(lib().hss_sample_offdiag_noalloc(C.byref(source), leaf, precision, ncols, _ptr(R),
                                             R.stride(1), _ptr(Sr), _ptr(Sc), lds, _stream(stream)))
+
+
+def hss_compress_batched(sources, opts, stream=None, allow_not_converged=False):
+    """One HSSMatrix per (source, opts) pair, compressed side by side."""
+    n = len(sources)
+    if len(opts) != n:
+        raise ValueError("one opts per source")
+    src_arr = (hss_source * n)(*sources)
+    opt_arr = (hss_opts * n)(*opts)
+    hs = (C.c_void_p * n)()
+    st = lib().hss_compress_batched(src_arr, opt_arr, n, _stream(stream), hs)
+    if not (st == HSS_ERR_NOT_CONVERGED and allow_not_converged):
+        _check(st)
+    out = [HSSMatrix(h) for h in hs]
+    for m in out:
+        m.converged = bool(m.stats().converged)
+    return out
 
 
 class HSSMatrix:

@@ -73,5 +73,9 @@ def test_argument_validation_without_gpu(hss):
     assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
     assert h.value is None
     assert L.hss_matvec(None, 1, None, 1, None, 1, None) == hss.HSS_ERR_ARG
+    hs = (C.c_void_p * 1)()
+    assert L.hss_compress_batched(None, None, -1, None, hs) == hss.HSS_ERR_ARG
+    assert L.hss_compress_batched(None, C.byref(o), 1, None, hs) == hss.HSS_ERR_ARG
+    assert L.hss_compress_batched(None, None, 0, None, None) == hss.HSS_OK
     assert L.hss_rcb_order(None, 10, 2, 10, 4, None) == hss.HSS_ERR_ARG
     assert L.hss_random_normal(0, 10, 0, 1, None, 10, 0, None) == hss.HSS_ERR_ARG
