@@ -199,6 +199,7 @@ struct hss_matrix_s {
   int d_final = 0, n_adapt = 0, converged = 0;
   int qrcp_cap = -1;       // co-resident CTAs of the QRCP kernel at width qrcp_cap_d
   int qrcp_cap_d = -1;
+  int pack_decided = -1;   // mixed forms, generated A: packed tiles (1) or not (0)
   bool trace = false;      // HSS_TRACE=1: one stderr line per QRCP launch
   cudaEvent_t trace_ev[2] = {nullptr, nullptr};
   void* packA = nullptr;   // packed tensor-core tiles of a dense A (during compress)
@@ -332,12 +333,33 @@ hss_status run_gemms(hss_matrix_s* H, const std::vector<GemmJob>& jobs, cudaStre
   const int tm = tc ? 128 : 64, tn = tc ? gemm_tc_tile_n(max_n) : 64;
   std::vector<GemmTile> tiles;
   double flop = 0.0;
+  long long ntile = 0;
+  for (const GemmJob& j : jobs)
+    if (j.M > 0 && j.N > 0) ntile += (long long)((j.M + tm - 1) / tm) * ((j.N + tn - 1) / tn);
   for (size_t i = 0; i < jobs.size(); ++i) {
     const GemmJob& j = jobs[i];
     if (j.M <= 0 || j.N <= 0) continue;
     flop += 2.0 * j.M * j.N * j.K;
+    // FP64 tiles with a long K on a launch of few tiles: split K so that the
+    // launch fills the SMs (partials added atomically; C zeroed first when
+    // the job overwrites it)
+    int ks = 1;
+    const bool contiguous_c = !j.c_rows && j.c_split == 0x7fffffff &&
+                              ((j.c_rs == 1 && j.c_cs == j.M) || (j.c_cs == 1 && j.c_rs == j.N));
+    if (!tc && j.K >= 512 && j.beta == 0.0 && (j.gamma == 1.0 || (j.gamma == 0.0 && contiguous_c)) &&
+        ntile < 2 * 152) {
+      ks = (int)std::min<long long>((2 * 152 + ntile - 1) / ntile, j.K / 256);
+      ks = std::max(ks, 1);
+      if (ks > 1 && j.gamma == 0.0) CK(cudaMemsetAsync(j.C, 0, sizeof(double) * (size_t)j.M * j.N, st));
+    }
     for (int ti = 0; ti < (j.M + tm - 1) / tm; ++ti)
-      for (int tj = 0; tj < (j.N + tn - 1) / tn; ++tj) tiles.push_back({(int)i, ti, tj});
+      for (int tj = 0; tj < (j.N + tn - 1) / tn; ++tj)
+        for (int z = 0; z < ks; ++z) {
+          // K shares in multiples of the 16-wide k step
+          const int kb = (int)((long long)j.K * z / ks) / 16 * 16;
+          const int ke = z + 1 == ks ? j.K : (int)((long long)j.K * (z + 1) / ks) / 16 * 16;
+          tiles.push_back({(int)i, ti, tj, kb, ke});
+        }
   }
   if (tiles.empty()) return HSS_OK;
   if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
@@ -375,6 +397,19 @@ double tol_scale(const hss_matrix_s* H, int level) {
 }
 
 // ---------------------------------------------------------------- sampling
+// Packed operand for the mixed forms: always for a dense A; for generated
+// entries when the split tiles take at most 40 % of the free device memory
+// (decided once per compression).
+bool use_packed(hss_matrix_s* H) {
+  if (H->src.kind == HSS_SRC_DENSE) return true;
+  if (H->pack_decided < 0) {
+    size_t fr = 0, tot = 0;
+    const size_t pb = packed_a_bytes(H->n, H->o.precision);
+    H->pack_decided = (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (double)pb <= 0.4 * (double)fr) ? 1 : 0;
+  }
+  return H->pack_decided == 1;
+}
+
 hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool own_R) {
   const int n = H->n, w = c1 - c0;
   if (w <= 0) return HSS_OK;
@@ -395,13 +430,18 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
     CK(launch_sample_fp64(s, w, Rc, n, H->Sg_r + c0, H->Sg_c + c0, H->dmax, st));
     H->launches += 2;
     H->st.sample_launches += 2;
-  } else if (H->src.kind == HSS_SRC_DENSE) {
-    // dense A: split once per compression into packed tensor-core tiles
+  } else if (use_packed(H)) {
+    // dense A, or generated entries whose split tiles fit comfortably in
+    // HBM: split once per compression into packed tensor-core tiles, then
+    // every pass streams them (a generated A is evaluated once, not once per
+    // pass)
     if (!H->packA) {
       const size_t pb = packed_a_bytes(n, H->o.precision);
+      CK(H->timer.mark(PH_SAMPLE, st));
       CK(cudaMallocAsync(&H->packA, pb, st));
       CK(launch_pack_a(s, H->o.leaf, H->o.precision, H->packA, st));
       H->launches++;
+      CK(H->timer.mark(PH_RNG, st));
     }
     void* packR = nullptr;
     CK(cudaMallocAsync(&packR, packed_r_bytes(n, w, H->o.precision), st));
@@ -448,7 +488,7 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
   // (FP64: 8 B per entry; packed TF32x2: 8 B; packed BF16x3: 6 B), R read,
   // S written
   double abytes = 0.0;
-  if (H->src.kind == HSS_SRC_DENSE)
+  if (H->src.kind == HSS_SRC_DENSE || (H->o.precision != HSS_PREC_FP64 && H->pack_decided == 1))
     abytes = (H->o.precision == HSS_PREC_BF16X3 ? 6.0 : 8.0) * n * (double)n;
   H->st.bytes_sample += 2.0 * (abytes + 2.0 * 8.0 * n * (double)w);
   CK(cudaMemsetAsync(H->d_flag, 0, sizeof(int), st));

@@ -71,7 +71,10 @@ struct GemmJob {
   int M, N, K;
   double alpha, beta, gamma;
 };
-struct GemmTile { int job, ti, tj; };
+// One output tile of one job; k0..k1 is its share of K (split-K tiles add
+// alpha * partial into C atomically: the job then has beta == 0 and
+// gamma == 1, or gamma == 0 with C zeroed beforehand).
+struct GemmTile { int job, ti, tj, k0, k1; };
 
 // QR with column pivoting of W = S^T (S: m x d rows, row-major ld lds),
 // truncated by the plain rule (rule 0) or the HMT-scaled rule (rule 1),

@@ -37,15 +37,17 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmJob* __restrict__ jobs,
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-  for (int l0 = 0; l0 < jb.K; l0 += TK) {
+  const int kb = tl.k0, ke = tl.k1;
+  const bool split = kb > 0 || ke < jb.K;
+  for (int l0 = kb; l0 < ke; l0 += TK) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int il = tid % TM, kk = tid / TM + 4 * q;
       int i = i0 + il, l = l0 + kk;
-      As[kk][il] = (i < jb.M && l < jb.K) ? ld_op(jb.A, i, l) : 0.0;
+      As[kk][il] = (i < jb.M && l < ke) ? ld_op(jb.A, i, l) : 0.0;
       int jl = tid % TN;
       int j = j0 + jl;
-      Bs[kk][jl] = (j < jb.N && l < jb.K) ? ld_op(jb.B, l, j) : 0.0;
+      Bs[kk][jl] = (j < jb.N && l < ke) ? ld_op(jb.B, l, j) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -71,9 +73,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmJob* __restrict__ jobs,
     for (int y = 0; y < 4; ++y) {
       int j = j0 + tx * 4 + y;
       if (j >= jb.N) continue;
+      double* dst = base + (long long)r * jb.c_rs + (long long)j * jb.c_cs;
+      if (split) {
+        atomicAdd(dst, jb.alpha * acc[x][y]);
+        continue;
+      }
       double v = jb.alpha * acc[x][y];
       if (jb.beta != 0.0) v += jb.beta * ld_op(jb.C0, i, j);
-      double* dst = base + (long long)r * jb.c_rs + (long long)j * jb.c_cs;
       if (jb.gamma != 0.0) v += jb.gamma * *dst;
       *dst = v;
     }

@@ -32,6 +32,29 @@ namespace {
 
 constexpr int NSTAGE = 3;                  // stages of the generating kernel
 
+// Entry A(i, j) for the generating producers.  The Laplace kernel
+// 1 / (4 pi |x_i - x_j|) avoids the FP64 square root and division (long
+// sequences on the FP64 pipe, which bounds this kernel): |x_i - x_j|^-1 from
+// the FP32 reciprocal square root of r^2, refined by one Newton-Raphson step
+// for x^(-1/2), y1 = y0 (3 - r^2 y0^2) / 2, in FP64 — relative error about
+// 1.5 e0^2 for an initial error e0 ~ 1e-7, far below the split that follows.
+// r^2 outside the FP32 normal range, the diagonal and the other kinds take
+// the plain definition.
+__device__ __forceinline__ double entry_gen(const SrcDev& s, int i, int j) {
+  if (s.kind != HSS_SRC_LAPLACE || i == j) return entry(s, i, j);
+  double r2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double t = s.a[i + c * s.ld] - s.a[j + c * s.ld];
+    r2 = __fma_rn(t, t, r2);
+  }
+  const float r2f = __double2float_rn(r2);
+  if (!(r2f >= 1.1754943508222875e-38f) || !(r2f <= 1e38f)) return entry(s, i, j);
+  const double y0 = (double)rsqrtf(r2f);
+  const double y1 = y0 * __fma_rn(-0.5 * r2 * y0, y0, 1.5);
+  return y1 * (1.0 / (4.0 * 3.141592653589793));
+}
+
 // ---------------------------------------------------------------------------
 // Generating kernel (entries computed by the producer warps).
 // Warps 0-7: generate the A tile of each stage, drain chains, write the
@@ -134,7 +157,7 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
           const int gk = k0 + c * EV + x;
           double val = 0.0;
           if (gr < n && gk < n && (gk < lo || gk >= hi))
-            val = a.trans ? entry(a.src, gk, gr) : entry(a.src, gr, gk);
+            val = a.trans ? entry_gen(a.src, gk, gr) : entry_gen(a.src, gr, gk);
           v[x] = val;
         }
         uint4 chunk[T];
@@ -236,7 +259,7 @@ __global__ void __launch_bounds__(256) k_pack_a(SrcDev src, int leaf, int nrb, i
     for (int x = 0; x < EV; ++x) {
       const int gk = k0 + c * EV + x;
       double val = 0.0;
-      if (gr < n && gk < n && (gk < lo || gk >= hi)) val = o ? entry(src, gk, gr) : entry(src, gr, gk);
+      if (gr < n && gk < n && (gk < lo || gk >= hi)) val = o ? entry_gen(src, gk, gr) : entry_gen(src, gr, gk);
       v[x] = val;
     }
     uint4 chunk[T];
