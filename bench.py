@@ -357,6 +357,174 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# The other workload configurations (one JSON line each, same timing rules):
+#   c1  Toeplitz 1/(1+|i-j|), n = 1024, leaf 64, rtol 1e-6, Incrementing, FP64
+#   c3  Laplace 1/(4 pi r) on a Fibonacci sphere, n = 32768, leaf 256,
+#       rtol 1e-6, Incrementing d0 = 128, dd = 64, BF16x3 (entries generated)
+#   c4  64 dense matrices, n log-uniform in [2048, 16384]: 32 Toeplitz
+#       (1+k)^-1.5, 32 Gaussian 3-D (h = 1), leaf 128, rtol 1e-5, Doubling
+#       d0 = 64, TF32x2, hss_compress_batched
+#   c5  Toeplitz cos(0.3k)/(1+k), n = 131072, leaf 256, rtol 1e-4,
+#       Incrementing d0 = 256, dd = 128, d_max 1024, TF32x2 (generated)
+CONFIG_WORKLOADS = {
+    "c1": "toeplitz_inv_n1024_incrementing_fp64",
+    "c3": "laplace_sphere_n32768_incrementing_bf16x3",
+    "c4": "batch64_toeplitz_gauss3_n2048_16384_doubling_tf32x2",
+    "c5": "toeplitz_cos_n131072_incrementing_tf32x2",
+}
+
+
+def _entries_block(src_kind, data, n, j0, w, dev):
+    """Columns j0 .. j0+w-1 of A (n x w, column-major) built with torch on the
+    device from the source definition, for the error ||A - H||_F."""
+    import torch
+    import workloads as wl
+    J = torch.arange(j0, j0 + w, device=dev)
+    I = torch.arange(n, device=dev)
+    if src_kind == wl.SRC_TOEPLITZ:
+        col, row = data
+        dlt = I[:, None] - J[None, :]
+        return torch.where(dlt >= 0, col[dlt.clamp(min=0)], row[(-dlt).clamp(min=0)])
+    X, diag = data
+    r = torch.cdist(X, X[j0:j0 + w], compute_mode="donot_use_mm_for_euclid_dist")
+    A = 1.0 / (4.0 * 3.141592653589793 * r)
+    A[J, torch.arange(w, device=dev)] = diag
+    return A
+
+
+def run_config(args):
+    import torch
+
+    import workloads as wl
+    from paper_1810_04125_gb300 import build as B
+    B.build()
+    from paper_1810_04125_gb300 import hss
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    PREC = {"fp64": hss.HSS_PREC_FP64, "tf32x2": hss.HSS_PREC_TF32X2, "bf16x3": hss.HSS_PREC_BF16X3}
+    STRAT = {"doubling": hss.HSS_DOUBLING, "incrementing": hss.HSS_INCREMENTING}
+    stream = torch.cuda.Stream(device=dev)
+    c = args.config
+    members = []          # (device source, opts maker, error data)
+    if c == "c4":
+        sizes = wl.batch_sizes()
+        for i, n in enumerate(int(v) for v in sizes):
+            if i < 32:
+                k = torch.arange(n, device=dev, dtype=torch.float64)
+                coef = (1.0 + k) ** -1.5
+                A = coef[(torch.arange(n, device=dev)[:, None] - torch.arange(n, device=dev)[None, :]).abs()]
+            else:
+                P = wl.uniform_points(n, 3, seed=n)
+                X = torch.from_numpy(P[hss.hss_rcb_order(P, 128)]).to(dev)
+                A = torch.empty((n, n), dtype=torch.float64, device=dev)
+                for j0 in range(0, n, 2048):
+                    A[j0:j0 + 2048] = torch.exp(-torch.cdist(X[j0:j0 + 2048], X, compute_mode="donot_use_mm_for_euclid_dist") ** 2 / 2.0)
+            members.append((hss.dense_source(A.t()), n, A))    # symmetric: the buffer is A column-major
+        leaf, rtol, atol, strat, d0, dd, prec = 128, 1e-5, 1e-8, "doubling", 64, 64, "tf32x2"
+    else:
+        W = {"c1": wl.workload_toeplitz_1024, "c3": wl.workload_laplace_sphere,
+             "c5": wl.workload_toeplitz_cos}[c]()
+        src = W.source
+        if W.needs_rcb:
+            src = src.permuted(hss.hss_rcb_order(src.points, W.leaf))
+        if src.kind == wl.SRC_TOEPLITZ:
+            col = torch.from_numpy(src.col).to(dev)
+            row = torch.from_numpy(src.row).to(dev)
+            ds = hss.toeplitz_source(col, row)
+            edata = (wl.SRC_TOEPLITZ, (col, row))
+        else:
+            X = torch.from_numpy(np.ascontiguousarray(src.points)).to(dev)
+            ds = hss.points_source(src.kind, torch.from_numpy(np.ascontiguousarray(src.points.T)).to(dev).t(),
+                                   src.p0, src.p1)
+            edata = (src.kind, (X, src.p0))
+        members.append((ds, src.n, edata))
+        leaf, rtol, atol, strat, d0, dd, prec = W.leaf, W.rtol, W.atol, W.strategy, W.d0, W.dd, W.precision
+
+    def opts(p, n):
+        return hss.make_opts(leaf, rtol, atol, d0, dd, min(n, 4096 if c != "c5" else 1024), STRAT[strat],
+                             PREC[p], 10, 0)
+
+    def compress_all(p):
+        with torch.cuda.stream(stream):
+            if c == "c4":
+                return hss.hss_compress_batched([m[0] for m in members], [opts(p, m[1]) for m in members],
+                                                stream=stream)
+            return [hss.hss_compress(members[0][0], opts(p, members[0][1]), stream=stream)]
+
+    def timed(p, steps, warm):
+        for _ in range(warm):
+            del_ = compress_all(p)
+            del del_
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(stream)
+        for _ in range(steps):
+            Hs = compress_all(p)
+            stats.append([h.stats() for h in Hs])
+            del Hs
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, stats[-1]
+
+    def rel_error(Hs):
+        num = den = 0.0
+        for H, (ds, n, ed) in zip(Hs, members):
+            blk = 2048
+            Xi = torch.empty((blk, n), dtype=torch.float64, device=dev).t()
+            Y = torch.empty((blk, n), dtype=torch.float64, device=dev).t()
+            for j0 in range(0, n, blk):
+                w_ = min(blk, n - j0)
+                Xi.zero_()
+                Xi[j0:j0 + w_, :w_].copy_(torch.eye(w_, dtype=torch.float64, device=dev))
+                hss.hss_matvec(H, Xi[:, :w_], Y[:, :w_], stream=stream)
+                torch.cuda.synchronize()
+                Ab = ed[:, j0:j0 + w_] if c == "c4" else _entries_block(ed[0], ed[1], n, j0, w_, dev)
+                num += float(((Ab - Y[:, :w_]) ** 2).sum())
+                den += float((Ab ** 2).sum())
+        return (num / den) ** 0.5
+
+    clocks = Clocks(dev.index or 0)
+    with clocks:
+        ms, st = timed(prec, args.steps, args.warmup)
+    Hs = compress_all(prec)
+    err = rel_error(Hs)
+    del Hs
+    flops = sum(s.flop_sample for s in st)
+    out = {"metric": METRIC, "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == "fp64" else f"{prec} sampling, f64 QR/ID", "data": "synthetic",
+           "gpu_launches": int(sum(s.launches for s in st)),
+           "config": {"workload": CONFIG_WORKLOADS[c], "leaf": leaf, "rtol": rtol, "atol": atol,
+                      "strategy": strat, "d0": d0, "dd": dd, "precision": prec, "members": len(members)},
+           "compress_s": ms / 1e3, "rel_error": err,
+           "result": {"d_final": max(s.d_final for s in st), "n_adapt": max(s.n_adapt for s in st),
+                      "max_rank": max(max(s.max_rank_r, s.max_rank_c) for s in st),
+                      "converged": min(s.converged for s in st)},
+           "phases_ms": {"sample": sum(s.ms_sample for s in st), "id": sum(s.ms_id for s in st),
+                         "test": sum(s.ms_test for s in st), "merge_reduce": sum(s.ms_merge for s in st)},
+           "clocks": clocks.summary()}
+    if c == "c4":
+        t0 = time.perf_counter()
+        for m in members:
+            with torch.cuda.stream(stream):
+                H = hss.hss_compress(m[0], opts(prec, m[1]), stream=stream)
+            del H
+        torch.cuda.synchronize()
+        out["sum_of_single_runs_s"] = time.perf_counter() - t0
+    if prec != "fp64" and not args.no_compare:
+        ms64, st64 = timed("fp64", 1, 1)
+        out["fp64_plain"] = {"compress_s": ms64 / 1e3,
+                             "phases_ms": {"sample": sum(s.ms_sample for s in st64),
+                                           "id": sum(s.ms_id for s in st64),
+                                           "test": sum(s.ms_test for s in st64),
+                                           "merge_reduce": sum(s.ms_merge for s in st64)}}
+        out["speedup_vs_fp64_plain"] = ms64 / ms
+    print(json.dumps(out), flush=True)
+
+
 def oracle_sample(n):
     """The CPU oracle on the same family and settings at order n."""
     import workloads as w
@@ -431,9 +599,13 @@ def main():
     ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="diagnostic override of the matrix order")
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="workload configuration (c2, the default, is the one the metric is quoted on)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config != "c2":
+        run_config(args)
     else:
         run_gpu(args)
 

@@ -155,6 +155,12 @@ hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int c
 hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx,
                       double* Y, long long ldy, void* stream);
 
+/* The dense matrix H (eq. nestedUV expanded): out (device, col-major n x n,
+ * ld >= n) = H applied to identity column blocks of up to 2048 columns with
+ * hss_matvec (a temporary n x 2048 device buffer).  For tests and moderate
+ * n; returns after a sync of the stream. */
+hss_status hss_to_dense(hss_matrix H, double* out, long long ld, void* stream);
+
 hss_status hss_get_stats(hss_matrix H, hss_stats* s);                 /* host */
 hss_status hss_get_node(hss_matrix H, int node, hss_node_info* info); /* host */
 

@@ -1321,6 +1321,30 @@ hss_status hss_export_node(hss_matrix H, int node, int* Jr, int* Jc, int* Pr, in
   return HSS_OK;
 }
 
+hss_status hss_to_dense(hss_matrix H, double* out, long long ld, void* stream) {
+  if (!H || !out) return fail(HSS_ERR_ARG, "NULL argument");
+  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators (not converged)");
+  if (ld < H->n) return fail(HSS_ERR_ARG, "ld %lld < n %d", ld, H->n);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = H->n, blk = std::min(n, 2048);
+  double* X = nullptr;
+  CK(cudaMallocAsync((void**)&X, sizeof(double) * (size_t)n * blk, st));
+  for (int c0 = 0; c0 < n; c0 += blk) {
+    const int w = std::min(blk, n - c0);
+    hss_status e = HSS_OK;
+    if (launch_identity_block(X, n, c0, w, st) != cudaSuccess)
+      e = fail(HSS_ERR_CUDA, "identity block launch failed");
+    if (e == HSS_OK) e = hss_matvec(H, w, X, n, out + (long long)c0 * ld, ld, stream);
+    if (e != HSS_OK) {
+      cudaFreeAsync(X, st);
+      return e;
+    }
+  }
+  CK(cudaFreeAsync(X, st));
+  CK(cudaStreamSynchronize(st));
+  return HSS_OK;
+}
+
 hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, double* Y,
                       long long ldy, void* stream) {
   if (!H || !X || !Y) return fail(HSS_ERR_ARG, "NULL argument");

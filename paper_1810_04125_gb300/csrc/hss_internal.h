@@ -176,6 +176,7 @@ cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas,
 cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
 cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int c1,
                              int* flag, cudaStream_t st);
+cudaError_t launch_identity_block(double* X, int n, int c0, int w, cudaStream_t st);
 cudaError_t launch_gather_int(const int* src, const int* idx, int* dst, int cnt,
                               const int* src2, int split, cudaStream_t st);
 

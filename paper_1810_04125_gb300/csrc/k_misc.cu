@@ -50,7 +50,23 @@ __global__ void k_gather_int(const int* __restrict__ src, const int* __restrict_
   dst[t] = (r < split) ? src[r] : src2[r - split];
 }
 
+// X(i, j) = (i == c0 + j): columns c0 .. c0 + w - 1 of the identity (n x w,
+// column-major, ld n)
+__global__ void k_identity_block(double* X, int n, int c0, int w) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * w) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  X[e] = (i == c0 + j) ? 1.0 : 0.0;
+}
+
 }  // namespace
+
+cudaError_t launch_identity_block(double* X, int n, int c0, int w, cudaStream_t st) {
+  const long long tot = (long long)n * w;
+  if (tot <= 0) return cudaSuccess;
+  k_identity_block<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, n, c0, w);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int njobs, int max_tiles,
                            cudaStream_t st) {

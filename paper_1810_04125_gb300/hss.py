@@ -22,7 +22,7 @@ HSS_PREC_FP64, HSS_PREC_TF32X2, HSS_PREC_BF16X3 = 0, 1, 2
 HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE = 0, 1, 2, 3
 HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
 
-EXPORTS = ["hss_compress", "hss_compress_batched", "hss_matvec", "hss_get_stats", "hss_get_node", "hss_export_node",
+EXPORTS = ["hss_compress", "hss_compress_batched", "hss_matvec", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
            "hss_free", "hss_status_str", "hss_last_error", "hss_rcb_order",
            "hss_random_normal", "hss_sample_offdiag", "hss_sample_offdiag_noalloc"]
 
@@ -71,6 +71,7 @@ def lib():
         L.hss_compress.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), vp, C.POINTER(vp)]
         L.hss_compress_batched.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), i, vp, C.POINTER(vp)]
         L.hss_matvec.argtypes = [vp, i, vp, ll, vp, ll, vp]
+        L.hss_to_dense.argtypes = [vp, vp, ll, vp]
         L.hss_get_stats.argtypes = [vp, C.POINTER(hss_stats)]
         L.hss_get_node.argtypes = [vp, i, C.POINTER(hss_node_info)]
         L.hss_export_node.argtypes = [vp, i] + [vp] * 11
@@ -142,6 +143,13 @@ def hss_compress(source, opts, stream=None, allow_not_converged=False):
         return HSSMatrix(h.value, converged=False)
     _check(st)
     return HSSMatrix(h.value)
+
+
+def hss_to_dense(H, out, stream=None):
+    """out (n x n device tensor, column-major) = H."""
+    if out.stride(0) != 1:
+        raise ValueError("hss_to_dense needs a column-major out (stride(0) == 1)")
+    _check(lib().hss_to_dense(H.handle, _ptr(out), out.stride(1), _stream(stream)))
 
 
 def hss_matvec(H, X, Y, stream=None):

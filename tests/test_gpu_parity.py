@@ -182,6 +182,12 @@ def test_generators_and_matvec(hss, torch):
     hss.hss_matvec(H, Xd, Yd)
     torch.cuda.synchronize()
     np.testing.assert_allclose(Yd.cpu().numpy(), Hd @ X, rtol=0, atol=1e-11 * np.abs(Hd @ X).max())
+    # hss_to_dense, into a buffer with ld > n: the same expansion
+    D = torch.full(((n + 5) * n,), float("nan"), dtype=torch.float64, device=gu.dev())
+    Dv = torch.as_strided(D, (n, n), (1, n + 5))      # column-major, ld n + 5
+    hss.hss_to_dense(H, Dv)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(Dv.cpu().numpy(), Hd, rtol=0, atol=1e-12 * np.abs(Hd).max())
 
 
 # -------------------------------------------------------------- edge cases
