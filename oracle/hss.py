@@ -41,6 +41,10 @@ Readings (see the design notes for the full list):
      node is COMPRESSED when both sides have passed.
  P19 the loop ends after a failed pass at d = d_max (NOT_CONVERGED); the
      last growth is clipped so that d <= d_max.
+ P21 symmetric option (A = A^T): Algorithm 3 with A^T = A makes the
+     column side a copy of the row side — S^c = S^r, the same ID (J^c = J^r,
+     V = U), R^c = R^r and B21 = B12^T — so only the row side is sampled,
+     tested and factored, and the column side takes its results.
 """
 from __future__ import annotations
 
@@ -64,6 +68,7 @@ class Options:
     strategy: str = "incrementing"     # or "doubling"
     p: int = 10
     level_tol_scaling: bool = True
+    symmetric: bool = False            # A = A^T: one sample, V = U (see P21)
 
 
 @dataclass
@@ -93,9 +98,10 @@ class _Sampler:
         self.n = src.n
         self.dense = src.to_dense() if (src.dense is not None or src.n <= 8192) else None
 
-    def sample(self, Rnew):
+    def sample(self, Rnew, symmetric=False):
         if self.dense is not None:
-            return self.dense @ Rnew, self.dense.T @ Rnew
+            Sr = self.dense @ Rnew
+            return Sr, (Sr if symmetric else self.dense.T @ Rnew)
         n = self.n
         Sr = np.zeros((n, Rnew.shape[1]))
         Sc = np.zeros((n, Rnew.shape[1]))
@@ -104,8 +110,9 @@ class _Sampler:
         for i0 in range(0, n, step):
             blk = self.src.entries(idx[i0:i0 + step], idx)
             Sr[i0:i0 + step] = blk @ Rnew
-            Sc += blk.T @ Rnew[i0:i0 + step]
-        return Sr, Sc
+            if not symmetric:
+                Sc += blk.T @ Rnew[i0:i0 + step]
+        return Sr, (Sr if symmetric else Sc)
 
     def entries(self, I, J):
         if self.dense is not None:
@@ -121,7 +128,7 @@ def compress(src, R: np.ndarray, opts: Options) -> Result:
     A = _Sampler(src)
     d_max = min(opts.d_max, R.shape[1])
     d = min(opts.d0, d_max)
-    Sr, Sc = A.sample(R[:, :d])
+    Sr, Sc = A.sample(R[:, :d], opts.symmetric)
     ctx = dict(A=A, R=R, opts=opts, nodes=nodes, d_prev=0, d=d, bounds=[d])
     n_adapt = 0
     passes = []
@@ -135,9 +142,9 @@ def compress(src, R: np.ndarray, opts: Options) -> Result:
             return Result(n, nodes, d, n_adapt, False, passes)
         dd = d if opts.strategy == "doubling" else opts.dd
         dd = min(dd, d_max - d)
-        Srn, Scn = A.sample(R[:, d:d + dd])
+        Srn, Scn = A.sample(R[:, d:d + dd], opts.symmetric)
         Sr = np.hstack([Sr, Srn])
-        Sc = np.hstack([Sc, Scn])
+        Sc = Sr if opts.symmetric else np.hstack([Sc, Scn])
         ctx["d_prev"], ctx["d"] = d, d + dd
         d += dd
         ctx["bounds"].append(d)
@@ -184,17 +191,18 @@ def _local_samples(ctx, t, cols):
     """ComputeLocalSamples (Algorithm 2) for the columns ``cols``."""
     nodes, R = ctx["nodes"], ctx["R"]
     d = ctx["d"]
+    sym = ctx["opts"].symmetric
     if t.is_leaf:
         I = t.I
         sr = ctx["Sr"][I, cols] - t.D @ R[I, cols]
-        sc = ctx["Sc"][I, cols] - t.D.T @ R[I, cols]
+        sc = sr if sym else ctx["Sc"][I, cols] - t.D.T @ R[I, cols]
         m_r = m_c = t.size
     else:
         c1, c2 = nodes[t.children[0]], nodes[t.children[1]]
         sr = np.vstack([c1.Sr[c1.Jr, cols] - t.B12 @ c2.Rr[:, cols],
                         c2.Sr[c2.Jr, cols] - t.B21 @ c1.Rr[:, cols]])
-        sc = np.vstack([c1.Sc[c1.Jc, cols] - t.B21.T @ c2.Rc[:, cols],
-                        c2.Sc[c2.Jc, cols] - t.B12.T @ c1.Rc[:, cols]])
+        sc = sr if sym else np.vstack([c1.Sc[c1.Jc, cols] - t.B21.T @ c2.Rc[:, cols],
+                                       c2.Sc[c2.Jc, cols] - t.B12.T @ c1.Rc[:, cols]])
         m_r, m_c = len(c1.Jr) + len(c2.Jr), len(c1.Jc) + len(c2.Jc)
     if t.Sr is None:
         t.Sr, t.Sc = np.zeros((m_r, d)), np.zeros((m_c, d))
@@ -203,6 +211,8 @@ def _local_samples(ctx, t, cols):
         t.Sc = np.hstack([t.Sc, np.zeros((m_c, d - t.Sc.shape[1]))])
     t.Sr[:, cols] = sr
     t.Sc[:, cols] = sc
+    if ctx["opts"].symmetric:
+        t.Sc = t.Sr
 
 
 def _reduce_local_samples(ctx, t, cols):
@@ -225,7 +235,10 @@ def _reduce_local_samples(ctx, t, cols):
         t.Rr = np.hstack([t.Rr, np.zeros((t.Rr.shape[0], d - t.Rr.shape[1]))])
         t.Rc = np.hstack([t.Rc, np.zeros((t.Rc.shape[0], d - t.Rc.shape[1]))])
     t.Rr[:, cols] = t.V.T @ xr
-    t.Rc[:, cols] = t.U.T @ xc
+    if ctx["opts"].symmetric:
+        t.Rc = t.Rr
+    else:
+        t.Rc[:, cols] = t.U.T @ xc
     t.Ir = Ibase_r[t.Jr]
     t.Ic = Ibase_c[t.Jc]
 
@@ -240,10 +253,11 @@ def _node_sufficient(ctx, t) -> bool:
     opts = ctx["opts"]
     er, ea = _tols(opts, t.level)
     d = ctx["d"]
+    sides = (t.Sr,) if opts.symmetric else (t.Sr, t.Sc)
     if opts.strategy == "doubling":
         mh, nh = _hankel_sizes(ctx, t)
         out = []
-        for S in (t.Sr, t.Sc):
+        for S in sides:
             m = S.shape[0]
             piv, Rf, k, stopped = qrcp(S[:, :d].T, hmt_rule(er, ea, d, mh, nh))
             if stopped:
@@ -253,11 +267,11 @@ def _node_sufficient(ctx, t) -> bool:
             if not ok:
                 return False
             out.append((piv, Rf, k))
-        _set_id(t, out, d)
+        _set_id(t, out * 2 if opts.symmetric else out, d)
         return True
     # Incrementing (Algorithm 5 applied to the node's samples, block by
     # block as they were drawn, P18)
-    for side, S in (("r", t.Sr), ("c", t.Sc)):
+    for side, S in ((("r", t.Sr),) if opts.symmetric else (("r", t.Sr), ("c", t.Sc))):
         st = t.inc.setdefault(side, dict(Q=np.zeros((S.shape[0], 0)), rho=None,
                                          tested=0, done=False))
         while not st["done"] and st["tested"] < d:
@@ -267,13 +281,15 @@ def _node_sufficient(ctx, t) -> bool:
             st["done"] = incrementing_block_test(blk, st, er, ea)
         if st["done"]:
             st["tested"] = d
+    if opts.symmetric:
+        t.inc["c"] = t.inc["r"]
     if not (t.inc["r"]["done"] and t.inc["c"]["done"]):
         return False
     out = []
-    for S in (t.Sr, t.Sc):
+    for S in sides:
         piv, Rf, k, _ = qrcp(S[:, :d].T, plain_rule(er, ea))
         out.append((piv, Rf, k))
-    _set_id(t, out, d)
+    _set_id(t, out * 2 if opts.symmetric else out, d)
     return True
 
 

@@ -192,6 +192,44 @@ def test_synthetic_hss_exact_ranks(strategy, d0, dd):
         assert res.n_adapt >= 1
 
 
+@pytest.mark.parametrize("strategy", ["incrementing", "doubling"])
+def test_symmetric_option_exact_ranks(strategy):
+    """Symmetric option (P21) on an exactly symmetric HSS matrix: the known
+    ranks, V = U, B21 = B12^T, and the reconstruction exact to rounding."""
+    n, leaf = 1024, 64
+    ranks = {4: 8, 3: 12, 2: 16, 1: 20}
+    A = w.synthetic_hss(n, leaf, ranks, seed=4, symmetric=True)
+    assert np.array_equal(A, A.T)
+    R = w.gaussian_matrix(6, n, 0, 512)
+    res = compress(w.dense_source(A), R, Options(leaf=leaf, rtol=1e-10, atol=1e-14, d0=16, dd=16,
+                                                 d_max=512, strategy=strategy, symmetric=True))
+    assert res.converged
+    for t in res.nodes[1:]:
+        assert len(t.Jr) == ranks[t.level], (t.idx, t.level)
+        assert np.array_equal(t.Jr, t.Jc) and np.array_equal(t.U, t.V)
+    for t in res.nodes:
+        if not t.is_leaf:
+            assert np.array_equal(t.B21, t.B12.T)
+    assert apply.rel_error(res, A) < 1e-12
+
+
+def test_symmetric_option_matches_general_on_symmetric_matrix():
+    """On a symmetric kernel matrix the symmetric option reproduces the
+    general algorithm: same d_final, ranks and the same error to rounding."""
+    n, leaf = 768, 64
+    pts = w.uniform_points(n, 3, seed=2)
+    src = w.gaussian_kernel(pts[tree.rcb_order(pts, leaf)], 0.4, 0.0)
+    R = w.gaussian_matrix(8, n, 0, 512)
+    o = dict(leaf=leaf, rtol=1e-6, atol=1e-12, d0=32, dd=32, d_max=512)
+    gen = compress(src, R, Options(**o))
+    sym = compress(src, R, Options(**o, symmetric=True))
+    assert gen.converged and sym.converged and gen.d_final == sym.d_final
+    assert gen.ranks() == sym.ranks()
+    A = src.to_dense()
+    e_g, e_s = apply.rel_error(gen, A), apply.rel_error(sym, A)
+    assert abs(e_g - e_s) <= 1e-3 * e_g, (e_g, e_s)
+
+
 def _hankel(A, t):
     I = t.I
     mask = np.ones(A.shape[0], bool)

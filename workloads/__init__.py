@@ -246,12 +246,14 @@ def halving_tree_ranges(n: int, leaf: int):
     return nodes
 
 
-def synthetic_hss(n: int, leaf: int, ranks_per_level: dict, seed: int = 0) -> np.ndarray:
+def synthetic_hss(n: int, leaf: int, ranks_per_level: dict, seed: int = 0,
+                  symmetric: bool = False) -> np.ndarray:
     """Dense matrix that is exactly HSS on the halving tree with the given
     off-diagonal rank at each level (level -> rank).  Nested bases: leaf U, V
     are orthonormal ``m x r``; a parent's basis is blockdiag(children) times
     an orthonormal ``(r1+r2) x r`` transfer matrix; sibling blocks are
-    ``U_big B V_big^T`` with a Gaussian B (full rank)."""
+    ``U_big B V_big^T`` with a Gaussian B (full rank).  ``symmetric``: V = U,
+    symmetric leaf blocks and B21 = B12^T, so that A = A^T."""
     rng = np.random.default_rng(seed)
     nodes = halving_tree_ranges(n, leaf)
     children = {i: [] for i in range(len(nodes))}
@@ -269,17 +271,20 @@ def synthetic_hss(n: int, leaf: int, ranks_per_level: dict, seed: int = 0) -> np
         lo, m, lev, _ = nodes[i]
         ch = children[i]
         if not ch:
-            A[lo:lo + m, lo:lo + m] = rng.standard_normal((m, m))
+            Dl = rng.standard_normal((m, m))
+            A[lo:lo + m, lo:lo + m] = (Dl + Dl.T) / 2 if symmetric else Dl
         if i == 0:
             pass
         else:
             r = ranks_per_level[lev]
             if not ch:
-                Ubig[i], Vbig[i] = orth(m, r), orth(m, r)
+                Ubig[i] = orth(m, r)
+                Vbig[i] = Ubig[i] if symmetric else orth(m, r)
             else:
                 a, b = ch
                 ra, rb = Ubig[a].shape[1], Ubig[b].shape[1]
-                Tu, Tv = orth(ra + rb, r), orth(ra + rb, r)
+                Tu = orth(ra + rb, r)
+                Tv = Tu if symmetric else orth(ra + rb, r)
                 Ubig[i] = np.vstack([Ubig[a] @ Tu[:ra], Ubig[b] @ Tu[ra:]])
                 Vbig[i] = np.vstack([Vbig[a] @ Tv[:ra], Vbig[b] @ Tv[ra:]])
         if ch:
@@ -287,9 +292,12 @@ def synthetic_hss(n: int, leaf: int, ranks_per_level: dict, seed: int = 0) -> np
             la, ma = nodes[a][0], nodes[a][1]
             lb, mb = nodes[b][0], nodes[b][1]
             B12 = rng.standard_normal((Ubig[a].shape[1], Vbig[b].shape[1]))
-            B21 = rng.standard_normal((Ubig[b].shape[1], Vbig[a].shape[1]))
+            B21 = B12.T if symmetric else rng.standard_normal((Ubig[b].shape[1], Vbig[a].shape[1]))
             A[la:la + ma, lb:lb + mb] = Ubig[a] @ B12 @ Vbig[b].T
-            A[lb:lb + mb, la:la + ma] = Ubig[b] @ B21 @ Vbig[a].T
+            if symmetric:
+                A[lb:lb + mb, la:la + ma] = A[la:la + ma, lb:lb + mb].T
+            else:
+                A[lb:lb + mb, la:la + ma] = Ubig[b] @ B21 @ Vbig[a].T
     return np.asfortranarray(A)
 
 
