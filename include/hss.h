@@ -93,6 +93,10 @@ typedef struct hss_opts {
   const double* R;       /* optional device col-major n x d_max random
                             matrix (ld = n); NULL = generated on the device
                             with Philox4x32-10 (hss_random_normal)            */
+  int symmetric;         /* 1: A = A^T (not checked): Algorithm 3 with
+                            A^T = A, whose column side copies the row side
+                            (S^c = S^r, V = U, B21 = B12^T), so only the row
+                            side is sampled, tested and factored; 0: general */
 } hss_opts;
 
 typedef struct hss_stats {

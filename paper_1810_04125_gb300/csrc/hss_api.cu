@@ -200,6 +200,7 @@ struct hss_matrix_s {
   int qrcp_cap = -1;       // co-resident CTAs of the QRCP kernel at width qrcp_cap_d
   int qrcp_cap_d = -1;
   int pack_decided = -1;   // mixed forms, generated A: packed tiles (1) or not (0)
+  bool sym = false;        // symmetric option: the column side mirrors the row side
   bool trace = false;      // HSS_TRACE=1: one stderr line per QRCP launch
   cudaEvent_t trace_ev[2] = {nullptr, nullptr};
   void* packA = nullptr;   // packed tensor-core tiles of a dense A (during compress)
@@ -425,11 +426,12 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
   }
   SrcDev s = make_src(H->src, H->leaf_id);
   const double* Rc = H->R + (long long)c0 * n;
+  const int norient = H->sym ? 1 : 2;   // A^T R is A R for a symmetric A
   if (H->o.precision == HSS_PREC_FP64) {
     CK(H->timer.mark(PH_SAMPLE, st));
-    CK(launch_sample_fp64(s, w, Rc, n, H->Sg_r + c0, H->Sg_c + c0, H->dmax, st));
-    H->launches += 2;
-    H->st.sample_launches += 2;
+    CK(launch_sample_fp64(s, w, Rc, n, H->Sg_r + c0, H->sym ? nullptr : H->Sg_c + c0, H->dmax, st));
+    H->launches += norient;
+    H->st.sample_launches += norient;
   } else if (use_packed(H)) {
     // dense A, or generated entries whose split tiles fit comfortably in
     // HBM: split once per compression into packed tensor-core tiles, then
@@ -449,16 +451,17 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
     H->launches++;
     if (sample_tc_packed_ksplit(n, w, H->o.precision) > 1) {
       CK(cudaMemset2DAsync(H->Sg_r + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
-      CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
+      if (!H->sym) CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
     }
     CK(cudaMemsetAsync(H->d_flag + 1, 0, sizeof(int), st));
     CK(H->timer.mark(PH_SAMPLE, st));
     CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 0, H->Sg_r + c0, H->dmax,
                                H->d_flag + 1, st));
-    CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 1, H->Sg_c + c0, H->dmax,
-                               H->d_flag + 1, st));
-    H->launches += 2;
-    H->st.sample_launches += 2;
+    if (!H->sym)
+      CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 1, H->Sg_c + c0, H->dmax,
+                                 H->d_flag + 1, st));
+    H->launches += norient;
+    H->st.sample_launches += norient;
     CK(H->timer.mark(PH_RNG, st));
     CK(cudaFreeAsync(packR, st));
   } else {
@@ -468,33 +471,34 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
     H->launches++;
     if (sample_tc_ksplit(n, w, H->o.precision) > 1) {
       CK(cudaMemset2DAsync(H->Sg_r + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
-      CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
+      if (!H->sym) CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
     }
     CK(cudaMemsetAsync(H->d_flag + 1, 0, sizeof(int), st));
     CK(H->timer.mark(PH_SAMPLE, st));
     int at = 0;
     CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 0, w, packR, H->Sg_r + c0, H->dmax,
                         H->d_flag + 1, &at, st));
-    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 1, w, packR, H->Sg_c + c0, H->dmax,
-                        H->d_flag + 1, &at, st));
-    H->launches += 2;
-    H->st.sample_launches += 2;
+    if (!H->sym)
+      CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 1, w, packR, H->Sg_c + c0, H->dmax,
+                          H->d_flag + 1, &at, st));
+    H->launches += norient;
+    H->st.sample_launches += norient;
     CK(H->timer.mark(PH_RNG, st));
     CK(cudaFreeAsync(packR, st));
   }
   CK(H->timer.mark(PH_RNG, st));
-  H->st.flop_sample += 4.0 * (double)n * (double)n * (double)w;
+  H->st.flop_sample += 2.0 * norient * (double)n * (double)n * (double)w;
   // algorithmic bytes of the sampling kernels: A read once per orientation
   // (FP64: 8 B per entry; packed TF32x2: 8 B; packed BF16x3: 6 B), R read,
   // S written
   double abytes = 0.0;
   if (H->src.kind == HSS_SRC_DENSE || (H->o.precision != HSS_PREC_FP64 && H->pack_decided == 1))
     abytes = (H->o.precision == HSS_PREC_BF16X3 ? 6.0 : 8.0) * n * (double)n;
-  H->st.bytes_sample += 2.0 * (abytes + 2.0 * 8.0 * n * (double)w);
+  H->st.bytes_sample += norient * (abytes + 2.0 * 8.0 * n * (double)w);
   CK(cudaMemsetAsync(H->d_flag, 0, sizeof(int), st));
   CK(launch_nonfinite(H->Sg_r, H->dmax, n, c0, c1, H->d_flag, st));
-  CK(launch_nonfinite(H->Sg_c, H->dmax, n, c0, c1, H->d_flag, st));
-  H->launches += 2;
+  if (!H->sym) CK(launch_nonfinite(H->Sg_c, H->dmax, n, c0, c1, H->d_flag, st));
+  H->launches += norient;
   CKS(readback(H, H->d_flag, 2 * sizeof(int), st));
   if (H->o.precision != HSS_PREC_FP64 && H->h_pinned[1])
     return fail(HSS_ERR_TIMEOUT, "tensor-core sampling gave up waiting (code %d)", H->h_pinned[1]);
@@ -541,6 +545,7 @@ void merge_jobs(hss_matrix_s* H, Node& t, int cs, int d, std::vector<GemmJob>& j
   // tau.S^r = [nu1.S^r(J) - B12 nu2.R^r ; nu2.S^r(J) - B21 nu1.R^r]
   blk(t.r.S, a.r, t.B12, 1, std::max(k1r, 1), b.Rr, k2c);
   blk(t.r.S + (long long)k1r * dm, b.r, t.B21, 1, std::max(k2r, 1), a.Rr, k1c);
+  if (H->sym) return;   // symmetric option: tau.S^c is tau.S^r
   // tau.S^c = [nu1.S^c(J) - B21^T nu2.R^c ; nu2.S^c(J) - B12^T nu1.R^c]
   blk(t.c.S, a.c, t.B21, std::max(k2r, 1), 1, b.Rc, k2r);
   blk(t.c.S + (long long)k1c * dm, b.c, t.B12, std::max(k1r, 1), 1, a.Rc, k1r);
@@ -568,12 +573,12 @@ void reduce_jobs(hss_matrix_s* H, Node& t, int cs, int d, std::vector<GemmJob>& 
   if (t.leaf) {
     Opnd x = opnd(H->R + t.lo + (long long)cs * H->n, 1, H->n);
     one(t.Rr, t.c, x);
-    one(t.Rc, t.r, x);
+    if (!H->sym) one(t.Rc, t.r, x);     // symmetric option: R^c is R^r
   } else {
     Node& a = H->nodes[t.ch[0]];
     Node& b = H->nodes[t.ch[1]];
     one(t.Rr, t.c, opnd(a.Rr + cs, dm, 1, nullptr, b.Rr + cs, a.c.k));
-    one(t.Rc, t.r, opnd(a.Rc + cs, dm, 1, nullptr, b.Rc + cs, a.r.k));
+    if (!H->sym) one(t.Rc, t.r, opnd(a.Rc + cs, dm, 1, nullptr, b.Rc + cs, a.r.k));
   }
 }
 
@@ -822,7 +827,8 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         if (!t.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
         add_ex(nullptr, t.lo, t.size, nullptr, t.lo, t.size, t.D, t.size);
         CKS(alloc_side(H, t.r, true, H->Sg_r + (long long)t.lo * H->dmax, t.size));
-        CKS(alloc_side(H, t.c, true, H->Sg_c + (long long)t.lo * H->dmax, t.size));
+        if (H->sym) t.c = t.r;
+        else CKS(alloc_side(H, t.c, true, H->Sg_c + (long long)t.lo * H->dmax, t.size));
       } else {
         Node& a = H->nodes[t.ch[0]];
         Node& b = H->nodes[t.ch[1]];
@@ -832,7 +838,8 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         add_ex(a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, t.B12, std::max(a.r.k, 1));
         add_ex(b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, t.B21, std::max(b.r.k, 1));
         CKS(alloc_side(H, t.r, false, nullptr, a.r.k + b.r.k));
-        CKS(alloc_side(H, t.c, false, nullptr, a.c.k + b.c.k));
+        if (H->sym) t.c = t.r;
+        else CKS(alloc_side(H, t.c, false, nullptr, a.c.k + b.c.k));
       }
     }
     if (!ex.empty()) {
@@ -860,7 +867,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
     if (dbl) {
       for (int id : lw.cand) {
         reqs.push_back({id, 0, 1});
-        reqs.push_back({id, 1, 1});
+        if (!H->sym) reqs.push_back({id, 1, 1});
       }
     } else {
       // Incrementing: test the untested columns of every side block by block
@@ -871,11 +878,12 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         std::vector<Sd> sides;
         for (int id : lw.cand) {
           Node& t = H->nodes[id];
-          for (int sd = 0; sd < 2; ++sd) {
+          for (int sd = 0; sd < (H->sym ? 1 : 2); ++sd) {
             Side& s = sd ? t.c : t.r;
             if (s.done) s.tested = d;
             else if (d > s.tested) sides.push_back({id, sd});
           }
+          if (H->sym) t.c = t.r;
         }
         if (sides.empty()) break;
         CK(H->timer.mark(PH_TEST, st));
@@ -983,9 +991,10 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
       }
       for (int id : lw.cand) {
         Node& t = H->nodes[id];
+        if (H->sym) t.c = t.r;
         if (t.r.done && t.c.done) {
           reqs.push_back({id, 0, 0});
-          reqs.push_back({id, 1, 0});
+          if (!H->sym) reqs.push_back({id, 1, 0});
         } else {
           t.state = HSS_PARTIALLY_COMPRESSED;
         }
@@ -995,14 +1004,19 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
     CKS(run_qrcp(H, reqs, d, st, wbuf));
     CK(H->timer.mark(PH_MERGE, st));
     std::vector<GemmJob> copies, rj;
-    for (size_t i = 0; i + 1 < reqs.size(); i += 2) {
+    // the requests come as (row side, column side) pairs, or one row-side
+    // request per node with the symmetric option (the column side copies it)
+    const size_t per = H->sym ? 1 : 2;
+    for (size_t i = 0; i + per - 1 < reqs.size(); i += per) {
       Node& t = H->nodes[reqs[i].node];
+      if (H->sym) t.c = t.r;
       if (t.r.qr_acc && t.c.qr_acc) {
         CKS(finalize_id(H, reqs[i].node, 0, wbuf[i], d, copies, st));
-        CKS(finalize_id(H, reqs[i].node, 1, wbuf[i + 1], d, copies, st));
+        if (H->sym) t.c = t.r;
+        else CKS(finalize_id(H, reqs[i].node, 1, wbuf[i + 1], d, copies, st));
         t.state = HSS_COMPRESSED;
         t.Rr = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(t.c.k, 1) * H->dmax);
-        t.Rc = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(t.r.k, 1) * H->dmax);
+        t.Rc = H->sym ? t.Rr : (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(t.r.k, 1) * H->dmax);
         if (!t.Rr || !t.Rc) return fail(HSS_ERR_NOMEM, "device arena allocation failed (reduced R)");
         accepted.push_back(reqs[i].node);
       } else {
@@ -1093,7 +1107,8 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
   H->iota = (int*)H->arena.alloc(sizeof(int) * n);
   H->d_flag = (int*)H->arena.alloc(256);
   H->Sg_r = (double*)H->arena.alloc(sizeof(double) * nd);
-  H->Sg_c = (double*)H->arena.alloc(sizeof(double) * nd);
+  H->sym = o->symmetric != 0;
+  H->Sg_c = H->sym ? H->Sg_r : (double*)H->arena.alloc(sizeof(double) * nd);
   const bool mixed = o->precision != HSS_PREC_FP64;
   const bool own_R = (o->R == nullptr) || mixed;
   if (own_R) H->R = (double*)H->arena.alloc(sizeof(double) * nd);

@@ -37,7 +37,7 @@ class hss_opts(C.Structure):
     _fields_ = [("leaf", C.c_int), ("strategy", C.c_int), ("precision", C.c_int),
                 ("level_tol_scaling", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
                 ("d0", C.c_int), ("dd", C.c_int), ("d_max", C.c_int), ("oversample_p", C.c_int),
-                ("seed", C.c_ulonglong), ("R", C.c_void_p)]
+                ("seed", C.c_ulonglong), ("R", C.c_void_p), ("symmetric", C.c_int)]
 
 
 class hss_stats(C.Structure):
@@ -128,9 +128,9 @@ def make_source(kind, n, a, b=None, ld=0, dim=0, p0=0.0, p1=0.0):
 
 
 def make_opts(leaf, rtol, atol, d0, dd, d_max, strategy, precision=HSS_PREC_FP64, p=10, seed=0,
-              R=None, level_tol_scaling=1):
+              R=None, level_tol_scaling=1, symmetric=0):
     o = hss_opts(leaf, strategy, precision, level_tol_scaling, rtol, atol, d0, dd, d_max, p,
-                 seed, _ptr(R))
+                 seed, _ptr(R), int(symmetric))
     o._keep = R
     return o
 

@@ -40,7 +40,8 @@ def gpu_compress(src, R, o, precision="fp64", pass_R=True, seed=0, allow_not_con
     s = device_source(src)
     Rd = col_major(R) if pass_R else None
     opts = hss.make_opts(o.leaf, o.rtol, o.atol, o.d0, o.dd, o.d_max, STRAT[o.strategy],
-                         PREC[precision], o.p, seed, Rd, int(o.level_tol_scaling))
+                         PREC[precision], o.p, seed, Rd, int(o.level_tol_scaling),
+                         int(getattr(o, "symmetric", False)))
     return hss.hss_compress(s, opts, allow_not_converged=allow_not_converged)
 
 
