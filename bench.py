@@ -305,6 +305,31 @@ def run_gpu(args):
                  "phases_ms": {"sample": q.ms_sample, "rng_check": q.ms_rng, "id": q.ms_id,
                                "test": q.ms_test, "merge_reduce": q.ms_merge, "total": q.ms_total}}
 
+    # --- the symmetric option on the same (symmetric) matrix: A^T R = A R, the
+    # column side copies the row side; reported beside the general algorithm
+    sym = None
+    if not args.no_compare:
+        osym = hss.make_opts(cfg["leaf"], cfg["rtol"], cfg["atol"], cfg["d0"], cfg["d0"], cfg["d_max"],
+                             hss.HSS_DOUBLING, PREC[args.precision], cfg["p"], seed=cfg["seed"], symmetric=1)
+        step(osym)
+        barrier()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.steps):
+            H = step(osym)
+            del H
+        q1.record(stream)
+        barrier()
+        sms = q0.elapsed_time(q1) / args.steps
+        H = step(osym)
+        serr = rel_error(H)
+        sst = H.stats()
+        del H
+        sym = {"compress_s": sms / 1e3, "vs_general": (tmax / args.steps) / sms, "rel_error": serr,
+               "result": {"d_final": sst.d_final, "max_rank": max(sst.max_rank_r, sst.max_rank_c)},
+               "phases_ms": {"sample": sst.ms_sample, "id": sst.ms_id, "merge_reduce": sst.ms_merge}}
+
     # --- noise floor of the mixed sampling on this matrix (outside the timed
     # region): ||S_mixed - S_fp64||_F / ||S_fp64||_F over 128 columns, R
     # rounded to the tensor format as in the compression
@@ -345,6 +370,8 @@ def run_gpu(args):
     }
     if noise is not None:
         out["noise_floor"] = noise
+    if sym is not None:
+        out["symmetric_option"] = sym
     if plain is not None:
         out["fp64_plain"] = plain
         out["speedup_vs_fp64_plain"] = plain["compress_s"] / out["compress_s"]
