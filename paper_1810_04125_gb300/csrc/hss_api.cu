@@ -897,8 +897,10 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         for (auto& x : sides) {
           Side& s = x.side ? H->nodes[x.node].c : H->nodes[x.node].r;
           size_t b = block_end(s.tested) - s.tested, m = std::max(s.m, 1);
+          const size_t pg = (m + inc_group_rows((int)b) - 1) / inc_group_rows((int)b);   // group size bound
           need += Scratch::rnd(8 * m * b) + Scratch::rnd(8 * std::max<size_t>(std::max(s.q, s.m), 1) * b) +
-                  Scratch::rnd(8 * b) + Scratch::rnd(8 * 4) + Scratch::rnd(8);
+                  Scratch::rnd(8 * b) + Scratch::rnd(8 * 4) + Scratch::rnd(8) + Scratch::rnd(sizeof(unsigned)) +
+                  Scratch::rnd(8 * 2 * std::max<size_t>(pg, 1) * (b + 2));
         }
         CK(H->scratch.ensure(need, st));
         std::vector<IncJob> ij;
@@ -953,12 +955,68 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
           CKS(run_gemms(H, g2, st, "test-QtS"));
           CKS(run_gemms(H, g3, st, "test-S-QT"));
         }
+        // the rows of each side over a group of CTAs (one cooperative launch
+        // per batch of sides that fits the co-resident slots); blocks wider
+        // than the group kernel takes go to one CTA per side
+        // (only when one CTA per side would leave SMs idle and all groups fit
+        // one launch; a level with many sides keeps one CTA per side)
+        int nsm = 0, cur = 0;
+        CK(cudaGetDevice(&cur));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, cur));
+        bool grouped = bmax <= inc_group_bmax() && (int)ij.size() < nsm;
+        const int gcap = grouped ? inc_group_capacity(bmax) : 0;
+        long long gsum = 0;
+        for (const IncJob& j : ij) {   // the groups at their row widths fit the resident slots
+          const int rows = inc_group_rows(j.b);
+          gsum += (j.m + rows - 1) / rows;
+        }
+        if (gsum > gcap) grouped = false;
+        std::vector<int> P(ij.size(), 1);
+        std::vector<std::pair<size_t, size_t>> gbatches;
+        if (grouped) {
+          const int cap = gcap;
+          for (size_t i = 0; i < ij.size(); ++i) {
+            const int rows = inc_group_rows(ij[i].b);
+            P[i] = std::max(1, (ij[i].m + rows - 1) / rows);
+            ij[i].P = P[i];
+            ij[i].bar = (unsigned*)H->scratch.take(sizeof(unsigned));
+            ij[i].part = (double*)H->scratch.take(sizeof(double) * 2 * (size_t)P[i] * (ij[i].b + 2));
+          }
+          for (size_t b0 = 0; b0 < ij.size();) {
+            size_t b1 = b0;
+            int used = 0;
+            while (b1 < ij.size() && (b1 == b0 || used + P[b1] <= cap)) used += P[b1++];
+            gbatches.push_back({b0, b1});
+            b0 = b1;
+          }
+        }
         IncJob* dj;
         CKS(upload_jobs(H, ij, &dj, st));
         if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "test scratch sized too small");
         if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
-        CK(launch_inc_qr(dj, (int)ij.size(), st));
-        H->launches++;
+        if (grouped) {
+          CK(cudaMemsetAsync(H->d_flag + 4, 0, sizeof(int), st));
+          std::unique_lock<std::mutex> coop(coop_launch_mutex());
+          for (auto& gb : gbatches) {
+            std::vector<int2> map;
+            for (size_t i = gb.first; i < gb.second; ++i) {
+              CK(cudaMemsetAsync(ij[i].bar, 0, sizeof(unsigned), st));
+              for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
+            }
+            int2* dm;
+            CKS(upload_jobs(H, map, &dm, st));
+            CK(launch_inc_group(dj, dm, (int)map.size(), bmax, H->d_flag + 4, st));
+            CK(cudaFreeAsync(dm, st));
+            H->launches++;
+          }
+          CKS(readback(H, H->d_flag + 4, sizeof(int), st));
+          coop.unlock();
+          if (H->h_pinned[0])
+            return fail(HSS_ERR_TIMEOUT, "Incrementing test group barrier gave up (code %d)", H->h_pinned[0]);
+        } else {
+          CK(launch_inc_qr(dj, (int)ij.size(), st));
+          H->launches++;
+        }
         if (H->trace) {
           CK(cudaEventRecord(H->trace_ev[1], st));
           CK(cudaEventSynchronize(H->trace_ev[1]));

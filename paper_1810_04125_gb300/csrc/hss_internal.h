@@ -119,6 +119,10 @@ struct IncJob {
   double rho;           // |(R_1)_11| of the first block, < 0 if none yet
   double* res;          // out: [0]=|S_k|_F, [1]=|Sh|_F, [2]=min|diag|, [3]=|R_11|
   int* flag;            // out: [0]=sufficient, [1]=new q
+  // group form (launch_inc_group): P CTAs split the m rows
+  int P;
+  unsigned* bar;        // group barrier counter, zero before the launch
+  double* part;         // 2 x P x (b + 2) partial sums
 };
 
 // Gather of sub-blocks of A: out(i, j) = A(I[i], J[j]) (col-major, ld ldo);
@@ -174,6 +178,14 @@ int qrcp_group_capacity(int d_max);
 cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, int* err,
                         cudaStream_t st);
 cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
+// The same test with the rows of each side split over a group of P CTAs
+// (map[cta] = (job, rank), cooperative launch); b_max: largest block, at
+// most inc_group_bmax().
+int inc_group_rows(int b);                 // rows per CTA for a block of b columns
+int inc_group_bmax();
+int inc_group_capacity(int b_max);          // co-resident CTAs
+cudaError_t launch_inc_group(const IncJob* jobs_dev, const int2* map_dev, int nctas, int b_max, int* err,
+                             cudaStream_t st);
 cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int c1,
                              int* flag, cudaStream_t st);
 cudaError_t launch_identity_block(double* X, int n, int c0, int w, cudaStream_t st);
