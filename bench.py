@@ -115,6 +115,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_over_ranks(t_ms, flops, world, device):
+    """Whole-job figures of a replicated run: the slowest rank's time and the
+    work of all ranks (replicas only: no collective on the data path, one
+    reduction of two scalars after the timed region)."""
+    if world <= 1:
+        return t_ms, flops
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    f = torch.tensor([flops], device=device, dtype=torch.float64)
+    dist.all_reduce(f)
+    return float(t.item()), float(f.item())
+
+
 def build_inputs(device, n, dim, seed, leaf):
     """Points (RCB-ordered by the library's host routine) and the dense
     Gaussian-kernel matrix, built on the device in column blocks."""
@@ -214,17 +229,7 @@ def run_gpu(args):
     err_main = rel_error(H_keep)
     del H_keep
     flops = sum(s.flop_sample for s in stats)
-    tmax = t_ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-        f = torch.tensor([flops], device=dev, dtype=torch.float64)
-        dist.all_reduce(f)
-        flops_all = float(f.item())
-    else:
-        flops_all = flops
+    tmax, flops_all = reduce_over_ranks(t_ms, flops, world, dev)
     value = flops_all / (tmax / 1e3) / 1e12
     s0 = stats[-1]
 
