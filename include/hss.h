@@ -212,8 +212,11 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
                               const double* R, long long ldr, double* Sr, double* Sc,
                               long long lds, void* stream);
 
-/* The same computation as hss_sample_offdiag (same arguments, same
- * results), for callers that cannot let a library allocate device memory:
+/* The same computation as hss_sample_offdiag in its FP64 form (same
+ * arguments, same results; precision must be HSS_PREC_FP64 — the mixed
+ * forms stage their split operands in temporary buffers, so they return
+ * HSS_ERR_UNSUPPORTED here), for callers that cannot let a library allocate
+ * device memory:
  * a serving process or framework that owns the whole device-memory budget
  * through its own pool, or a caller that cannot accept the synchronisation
  * or the possible failure of cudaMalloc / cudaMallocAsync in the middle of

@@ -1720,7 +1720,8 @@ extern "C" hss_status hss_sample_offdiag_noalloc(const hss_source* A, int leaf, 
     return fail(HSS_ERR_ARG, "n = %d exceeds the fixed table of hss_sample_offdiag_noalloc (%d)", n,
                 HSS_NOALLOC_MAX_N);
   if (precision != HSS_PREC_FP64)
-    return fail(HSS_ERR_UNSUPPORTED, "mixed-precision sampling is not built in this library");
+    return fail(HSS_ERR_UNSUPPORTED, "hss_sample_offdiag_noalloc takes HSS_PREC_FP64 only (the mixed forms "
+                                     "need temporary operand buffers)");
   int* label = nullptr;
   CKS(noalloc_table(&label));
   cudaStream_t st = (cudaStream_t)stream;
