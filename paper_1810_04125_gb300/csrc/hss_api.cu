@@ -443,6 +443,9 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
       CK(cudaMallocAsync(&H->packA, pb, st));
       CK(launch_pack_a(s, H->o.leaf, H->o.precision, H->packA, st));
       H->launches++;
+      // the split is part of the sampling work: a dense A read once, the
+      // packed tiles written once
+      H->st.bytes_sample += (H->src.kind == HSS_SRC_DENSE ? 8.0 * n * (double)n : 0.0) + (double)pb;
       CK(H->timer.mark(PH_RNG, st));
     }
     void* packR = nullptr;
