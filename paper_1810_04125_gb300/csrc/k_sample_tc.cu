@@ -320,7 +320,10 @@ __global__ void __maxnreg__(96) k_sample_tc_packed(TcPackedArgs a) {
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int rb = blockIdx.x, ct = blockIdx.y;
+  // column tiles vary fastest across the grid: the CTAs that stream one
+  // row block of A for different column tiles run together and share it
+  // through L2, so A crosses HBM once per pass
+  const int rb = blockIdx.y, ct = blockIdx.x;
   const int kt0 = (int)((long long)a.nkt * blockIdx.z / a.ksplit);
   const int kt1 = (int)((long long)a.nkt * (blockIdx.z + 1) / a.ksplit);
   const int nk = kt1 - kt0, DR = a.drain;
@@ -418,7 +421,7 @@ template <int PREC>
 cudaError_t launch_packed_t(const TcPackedArgs& a, int gx, int gy, cudaStream_t st) {
   constexpr int T = Split<PREC>::T, NS = packed_stages<PREC>();
   const size_t sm = (size_t)NS * (T * TILE_A_BYTES + (size_t)a.N * 128) + 8 * (2 * NS + 4) + 16 + 1024;
-  dim3 grid(gx, gy, a.ksplit);
+  dim3 grid(gy, gx, a.ksplit);   // x: column tiles, y: row blocks
 #define HSS_LAUNCH_PK(NHV)                                                                          \
   do {                                                                                              \
     cudaError_t e = cudaFuncSetAttribute(k_sample_tc_packed<PREC, NHV>,                             \
