@@ -616,7 +616,10 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   }
   struct Batch { size_t b0, b1; bool group; };
   std::vector<Batch> batches;
-  for (size_t b0 = 0; b0 < nj;) {
+  bool all_small = nj >= (size_t)cap;
+  for (size_t i = 0; i < nj && all_small; ++i) all_small = mj[i] <= NL;
+  if (all_small) batches.push_back({0, nj, false});   // one CTA per side fills the GPU: one plain launch
+  for (size_t b0 = all_small ? nj : 0; b0 < nj;) {
     // the largest prefix whose groups fit at width NL
     size_t b1 = b0;
     int used = 0;
