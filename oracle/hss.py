@@ -45,6 +45,13 @@ Readings (see the design notes for the full list):
      column side a copy of the row side — S^c = S^r, the same ID (J^c = J^r,
      V = U), R^c = R^r and B21 = B12^T — so only the row side is sampled,
      tested and factored, and the column side takes its results.
+ P22 HMT criterion option (Lemma 4.1, eq. HMT_IQQH): Incrementing with the
+     test of each block S_k replaced by  alpha sqrt(2/pi) max_i
+     |((I - Q Q^T)^2 S_k)(:, i)|_2 <= eps_a  on the node's local sample
+     (the only sample the construction has); on failure the block's
+     orthonormal basis joins Q, as in Algorithm 5.  The criterion has no
+     relative form, so rtol is ignored and the final RRQR keeps the pivots
+     with |R_jj| > eps_a.
 """
 from __future__ import annotations
 
@@ -68,6 +75,8 @@ class Options:
     strategy: str = "incrementing"     # or "doubling"
     p: int = 10
     level_tol_scaling: bool = True
+    criterion: str = "new"             # or "hmt" (P22; Incrementing only)
+    hmt_alpha: float = 10.0
     symmetric: bool = False            # A = A^T: one sample, V = U (see P21)
 
 
@@ -123,6 +132,10 @@ class _Sampler:
 def compress(src, R: np.ndarray, opts: Options) -> Result:
     """HSSCompressAdaptive (Algorithm 3).  ``R`` is the caller's n x d_max
     Gaussian matrix; the pass with d columns uses R[:, :d]."""
+    if opts.criterion not in ("new", "hmt"):
+        raise ValueError(f"unknown criterion {opts.criterion!r}")
+    if opts.criterion == "hmt" and (opts.strategy != "incrementing" or not opts.hmt_alpha > 1.0):
+        raise ValueError("the HMT criterion is an Incrementing test with alpha > 1")
     n = src.n
     nodes = halving_tree(n, opts.leaf)
     A = _Sampler(src)
@@ -278,7 +291,10 @@ def _node_sufficient(ctx, t) -> bool:
             end = min(b for b in ctx["bounds"] if b > st["tested"])
             blk = S[:, st["tested"]:end]
             st["tested"] = end
-            st["done"] = incrementing_block_test(blk, st, er, ea)
+            if opts.criterion == "hmt":
+                st["done"] = hmt_block_test(blk, st, ea, opts.hmt_alpha)
+            else:
+                st["done"] = incrementing_block_test(blk, st, er, ea)
         if st["done"]:
             st["tested"] = d
     if opts.symmetric:
@@ -287,7 +303,7 @@ def _node_sufficient(ctx, t) -> bool:
         return False
     out = []
     for S in sides:
-        piv, Rf, k, _ = qrcp(S[:, :d].T, plain_rule(er, ea))
+        piv, Rf, k, _ = qrcp(S[:, :d].T, plain_rule(0.0 if opts.criterion == "hmt" else er, ea))
         out.append((piv, Rf, k))
     _set_id(t, out * 2 if opts.symmetric else out, d)
     return True
@@ -316,6 +332,37 @@ def incrementing_block_test(Sk: np.ndarray, st: dict, er: float, ea: float) -> b
     mn = float(dg.min())
     if mn < ea or mn < er * st["rho"]:
         return True
+    room = m - Q.shape[1]
+    st["Q"] = np.hstack([Q, Qk[:, :min(b, room)]])
+    return st["Q"].shape[1] >= m
+
+
+def hmt_estimate(Y: np.ndarray, alpha: float) -> float:
+    """The right-hand side of Lemma 4.1 (eq. HMT_err_bound): for Y = B W with
+    W of p independent standard Gaussian columns, alpha sqrt(2/pi) times the
+    largest column 2-norm of Y bounds |B|_2 except with probability alpha^-p."""
+    if Y.shape[1] == 0:
+        return 0.0
+    return alpha * math.sqrt(2.0 / math.pi) * float(np.max(np.linalg.norm(Y, axis=0)))
+
+
+def hmt_block_test(Sk: np.ndarray, st: dict, ea: float, alpha: float) -> bool:
+    """Incrementing step with the HMT criterion (eq. HMT_IQQH, P22) on the
+    new block S_k (m x b): the part of S_k outside span(Q), by the same
+    iterated block Gram-Schmidt as Algorithm 5, gives the estimate of
+    Lemma 4.1; the block is sufficient when the estimate is <= eps_a,
+    otherwise its orthonormal basis joins Q."""
+    Q = st["Q"]
+    m, b = Sk.shape
+    if b == 0:
+        return False
+    Sh = Sk.copy()
+    if Q.shape[1]:
+        Sh = Sh - Q @ (Q.T @ Sh)
+        Sh = Sh - Q @ (Q.T @ Sh)
+    if hmt_estimate(Sh, alpha) <= ea:
+        return True
+    Qk, _ = np.linalg.qr(Sh)
     room = m - Q.shape[1]
     st["Q"] = np.hstack([Q, Qk[:, :min(b, room)]])
     return st["Q"].shape[1] >= m

@@ -337,3 +337,103 @@ def test_table3_rank_band():
         assert res.converged
         assert 0.7 * rank <= res.max_rank() <= 1.3 * rank, (rtol, res.max_rank(), rank)
         assert apply.rel_error(res, A) <= rtol
+
+
+# ------------------------------------------------------ HMT criterion (P22)
+def test_hmt_estimate_rank_one_failure_probability():
+    """Lemma 4.1 on a rank-one B = u v^T with unit u, v (|B|_2 = 1): B w =
+    u (v^T w) with v^T w standard normal, so the estimate alpha sqrt(2/pi)
+    max_i |B w_i|_2 falls below |B|_2 exactly when every |g_i| < 1 / (alpha
+    sqrt(2/pi)), which has probability erf(sqrt(pi) / (2 alpha))^p <= alpha^-p.
+    The frequency over many draws pins the constant and the max."""
+    rng = np.random.default_rng(21)
+    u = rng.standard_normal(7)
+    v = rng.standard_normal(5)
+    B = np.outer(u / np.linalg.norm(u), v / np.linalg.norm(v))
+    alpha, T = 2.0, 40000
+    for p in (1, 3):
+        W = rng.standard_normal((T, 5, p))
+        fails = sum(hss.hmt_estimate(B @ W[t], alpha) < 1.0 for t in range(T))
+        prob = math.erf(math.sqrt(math.pi) / (2.0 * alpha)) ** p
+        assert prob <= alpha ** -p
+        assert abs(fails / T - prob) < 5.0 * math.sqrt(prob * (1.0 - prob) / T), (p, fails / T, prob)
+    # a full-rank B: the bound of the lemma fails with frequency <= alpha^-p
+    B = rng.standard_normal((6, 9))
+    nB = np.linalg.norm(B, 2)
+    p, T = 3, 20000
+    W = rng.standard_normal((T, 9, p))
+    fails = sum(hss.hmt_estimate(B @ W[t], alpha) < nB for t in range(T)) / T
+    assert fails <= alpha ** -p + 5.0 * math.sqrt(alpha ** -p / T)
+
+
+def test_hmt_criterion_leaves_meet_lemma():
+    """At a leaf the local sample is exactly F R(outside) with F the Hankel
+    block A(I, complement) (eq. sample_off_diag), so Lemma 4.1 holds with
+    B = (I - Q Q^T) F: when the HMT test accepts a block,
+    |(I - Q Q^T) F|_2 <= eps_a / level except with probability alpha^-b."""
+    n, leaf, atol = 1024, 128, 1e-6
+    A = w.udv_matrix(n, 120, seed=4)
+    o = Options(leaf=leaf, rtol=0.0, atol=atol, d0=16, dd=16, d_max=512, criterion="hmt")
+    res = compress(w.dense_source(A), w.gaussian_matrix(2, n, 0, 512), o)
+    assert res.converged
+    grew = 0
+    for t in res.nodes:
+        if not t.is_leaf:
+            continue
+        out = np.setdiff1d(np.arange(n), t.I)
+        ea = atol / t.level
+        for side, F in (("r", A[np.ix_(t.I, out)]), ("c", A[np.ix_(out, t.I)].T)):
+            Q = t.inc[side]["Q"]
+            resid = np.linalg.norm(F - Q @ (Q.T @ F), 2)
+            assert resid <= ea, (t.idx, side, resid, ea)
+            if 0 < Q.shape[1] < t.size and np.linalg.norm(F, 2) > ea:
+                grew += 1
+    assert grew > 0      # the test had to grow bases: it was not vacuous
+
+
+def test_hmt_criterion_table3_shape():
+    """Table 3: at the same absolute tolerance the HMT criterion (rtol
+    ignored) takes at least as many samples as the new criterion with
+    rtol = atol, and gives ranks at least as large and errors no larger."""
+    n = 1024
+    A = w.udv_matrix(n, 200, seed=1)
+    R = w.gaussian_matrix(1, n, 0, n)
+    for tol in (1e-6, 1e-10):
+        new = compress(w.dense_source(A), R, Options(leaf=128, rtol=tol, atol=tol, d0=128, dd=64,
+                                                     d_max=1024))
+        hmt = compress(w.dense_source(A), R, Options(leaf=128, rtol=tol, atol=tol, d0=128, dd=64,
+                                                     d_max=1024, criterion="hmt"))
+        assert new.converged and hmt.converged
+        e_new, e_hmt = apply.rel_error(new, A), apply.rel_error(hmt, A)
+        assert hmt.d_final >= new.d_final and hmt.max_rank() >= new.max_rank(), tol
+        assert e_hmt <= e_new * 1.01 and e_hmt <= tol, (tol, e_new, e_hmt)
+
+
+def test_hmt_criterion_options_checked():
+    A = w.udv_matrix(64, 8, seed=0)
+    for o in (Options(leaf=16, strategy="doubling", criterion="hmt"),
+              Options(leaf=16, criterion="hmt", hmt_alpha=1.0), Options(leaf=16, criterion="x")):
+        with pytest.raises(ValueError):
+            compress(w.dense_source(A), w.gaussian_matrix(0, 64, 0, 64), o)
+
+
+def test_hmt_block_test_cases():
+    """The HMT block test on blocks whose projected columns are known: a block
+    inside span(Q) is sufficient; orthogonal columns of norms 1, 2, 1/2
+    outside span(Q) have the estimate alpha sqrt(2/pi) 2, and a failed block
+    extends Q by its width with orthonormal columns."""
+    rng = np.random.default_rng(9)
+    m = 40
+    full, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    Q, P = full[:, :6], full[:, 6:]
+    st = dict(Q=Q.copy())
+    assert hss.hmt_block_test(Q @ rng.standard_normal((6, 8)), st, 1e-12, 10.0)
+    Sk = P[:, :3] * np.array([1.0, 2.0, 0.5]) + Q @ rng.standard_normal((6, 3))
+    for alpha in (2.0, 10.0):
+        thr = alpha * math.sqrt(2.0 / math.pi) * 2.0
+        st = dict(Q=Q.copy())
+        assert hss.hmt_block_test(Sk, st, 1.001 * thr, alpha) and st["Q"].shape[1] == 6
+        st = dict(Q=Q.copy())
+        assert not hss.hmt_block_test(Sk, st, 0.999 * thr, alpha)
+        assert st["Q"].shape[1] == 9
+        np.testing.assert_allclose(st["Q"].T @ st["Q"], np.eye(9), atol=1e-13)
