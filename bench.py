@@ -17,6 +17,8 @@ FP64 QR/ID); the FP64 plain form of the same compression is timed after it
 ("fp64_plain", "speedup_vs_fp64_plain"), and both report the reconstruction
 error ||A - H||_F / ||A||_F.
   python bench.py --impl reference     # the CPU oracle on a bounded sample
+  python bench.py --config c1|c3|c4|c5 # the other workload configurations
+  python bench.py --config table3      # new criterion vs HMT criterion grid
 
 Multi-GPU (torchrun): every rank compresses its own replica of the matrix
 (the path does not shard in this build), value = all ranks' flops / the
@@ -557,6 +559,73 @@ def run_config(args):
     print(json.dumps(out), flush=True)
 
 
+def run_table3(args):
+    """The comparison of stopping criteria of the paper's Table 3 on
+    alpha I + beta U D V^T (alpha = beta = 1, N = 20000, r = 200,
+    D_kk = 2^(-53 (k-1)/r), U and V orthonormal from QR of seeded Gaussian
+    matrices): the new criterion over the rtol x atol grid and the HMT
+    criterion per atol, each cell the relative error ||A - H||_F / ||A||_F,
+    the HSS rank (largest node rank), the final number of samples and the
+    compression time.  FP64 sampling (the grid reaches 1e-14), Incrementing
+    from d0 = 128 by 64, leaf 128, d_max = 5000 (the paper's rank cap)."""
+    import torch
+
+    from paper_1810_04125_gb300 import build as B
+    B.build()
+    from paper_1810_04125_gb300 import hss
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    n, r = (args.n or 20000), 200
+    rng = np.random.default_rng(0)
+    U = torch.from_numpy(np.linalg.qr(rng.standard_normal((n, r)))[0]).to(dev)
+    V = torch.from_numpy(np.linalg.qr(rng.standard_normal((n, r)))[0]).to(dev)
+    D = 2.0 ** (-53.0 * torch.arange(r, dtype=torch.float64, device=dev) / r)
+    A = (U * D) @ V.t()                          # row-major storage of A = column-major A^T
+    A.diagonal().add_(1.0)
+    At = A.t()                                   # column-major view of A
+    del U, V
+    src = hss.dense_source(At)
+    nA = float(torch.linalg.norm(A))
+    H_dense = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    stream = torch.cuda.Stream(device=dev)
+    tols = [1e-2, 1e-6, 1e-10, 1e-14]
+    cells = []
+
+    def run(crit, rtol, atol):
+        o = hss.make_opts(128, rtol, atol, 128, 64, min(n, 5000), hss.HSS_INCREMENTING, hss.HSS_PREC_FP64,
+                          10, 0, criterion=crit)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            H = hss.hss_compress(src, o, stream=stream, allow_not_converged=True)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        st = H.stats()
+        cell = {"criterion": "hmt" if crit == hss.HSS_CRIT_HMT else "new",
+                "rtol": None if crit == hss.HSS_CRIT_HMT else rtol, "atol": atol,
+                "converged": int(st.converged), "rank": max(st.max_rank_r, st.max_rank_c),
+                "d_final": st.d_final, "compress_s": e0.elapsed_time(e1) / 1e3, "rel_error": None}
+        if st.converged:
+            hss.hss_to_dense(H, H_dense, stream=stream)
+            torch.cuda.synchronize()
+            cell["rel_error"] = float(torch.linalg.norm(H_dense - At)) / nA
+        del H
+        cells.append(cell)
+        print(json.dumps(cell), file=sys.stderr, flush=True)
+
+    for rtol in tols:
+        for atol in tols:
+            run(hss.HSS_CRIT_NEW, rtol, atol)
+    for atol in tols:
+        run(hss.HSS_CRIT_HMT, 0.0, atol)
+    out = {"metric": "HSS rank and relative error per stopping criterion (Table 3 grid)",
+           "unit": "rel_error/rank", "data": "synthetic", "dtype": "f64",
+           "config": {"workload": f"udv_n{n}_r{r}", "leaf": 128, "strategy": "incrementing", "d0": 128,
+                      "dd": 64, "d_max": min(n, 5000), "hmt_alpha": 10.0},
+           "cells": cells}
+    print(json.dumps(out), flush=True)
+
+
 def oracle_sample(n):
     """The CPU oracle on the same family and settings at order n."""
     import workloads as w
@@ -631,11 +700,13 @@ def main():
     ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="diagnostic override of the matrix order")
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table3"],
                     help="workload configuration (c2, the default, is the one the metric is quoted on)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "table3":
+        run_table3(args)
     elif args.config != "c2":
         run_config(args)
     else:

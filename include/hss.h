@@ -42,6 +42,21 @@ typedef enum {
  * with the four tests of eq. stopping_criteria. */
 enum { HSS_DOUBLING = 0, HSS_INCREMENTING = 1 };
 
+/* Stopping test of the Incrementing strategy (section 2.4).
+ *  NEW : the relative and absolute tests of eq. stopping_criteria (the
+ *        paper's criterion).
+ *  HMT : the probabilistic bound of Lemma 4.1 (eq. HMT_err_bound) in the form
+ *        of eq. HMT_IQQH, applied to the node's local sample: a block S_k of
+ *        b new columns is sufficient when
+ *          alpha sqrt(2/pi) max_i |((I - Q Q^T)^2 S_k)(:, i)|_2 <= eps_a,
+ *        which bounds the 2-norm of the part of the sampled operator outside
+ *        span(Q) by eps_a except with probability alpha^-b; otherwise the
+ *        block's orthonormal basis joins Q.  It knows no relative tolerance:
+ *        rtol is ignored, and the final RRQR keeps the pivots with
+ *        |R_jj| > eps_a (the paper's Table 3 compares the two criteria).
+ *        Incrementing only (HSS_ERR_ARG with Doubling). */
+enum { HSS_CRIT_NEW = 0, HSS_CRIT_HMT = 1 };
+
 /* Arithmetic of the sampling product S = A R (the only step that is not
  * FP64 in the mixed forms; the QR, ID, tests and merges are always FP64).
  *  FP64   : plain FP64 products.
@@ -97,6 +112,9 @@ typedef struct hss_opts {
                             A^T = A, whose column side copies the row side
                             (S^c = S^r, V = U, B21 = B12^T), so only the row
                             side is sampled, tested and factored; 0: general */
+  int criterion;         /* HSS_CRIT_NEW (0, default) or HSS_CRIT_HMT        */
+  double hmt_alpha;      /* alpha > 1 of the HMT criterion (Lemma 4.1; the
+                            paper's example takes 10); ignored with NEW       */
 } hss_opts;
 
 typedef struct hss_stats {

@@ -689,7 +689,9 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     j.mh = t.size; j.nh = H->n - t.size; j.p = H->o.oversample_p;
     j.do_id = 1;
     double sc = tol_scale(H, t.level);
-    j.er = H->o.rtol * sc; j.ea = H->o.atol * sc;
+    // the HMT criterion knows the absolute tolerance only: its final RRQR
+    // keeps the pivots above eps_a
+    j.er = (H->o.criterion == HSS_CRIT_HMT ? 0.0 : H->o.rtol) * sc; j.ea = H->o.atol * sc;
     j.out = outs + 3 * i;
     j.P = P[i];
     j.bar = bars + i;
@@ -929,6 +931,8 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
           double sc = tol_scale(H, t.level);
           j.er = H->o.rtol * sc; j.ea = H->o.atol * sc;
           j.rho = s.rho;
+          j.hmt = H->o.criterion == HSS_CRIT_HMT;
+          j.hmt_c = j.hmt ? H->o.hmt_alpha * std::sqrt(2.0 / std::acos(-1.0)) : 0.0;
           ij.push_back(j);
           // Sh = S(:, tested:tested+b)
           GemmJob c = gemm_job();
@@ -1256,6 +1260,14 @@ hss_status hss_compress(const hss_source* A, const hss_opts* o, void* stream, hs
     return fail(HSS_ERR_ARG, "unknown precision %d", o->precision);
   if (!(o->rtol >= 0.0) || !(o->atol >= 0.0)) return fail(HSS_ERR_ARG, "tolerances must be >= 0");
   if (o->oversample_p < 0) return fail(HSS_ERR_ARG, "oversample_p must be >= 0");
+  if (o->criterion != HSS_CRIT_NEW && o->criterion != HSS_CRIT_HMT)
+    return fail(HSS_ERR_ARG, "unknown criterion %d", o->criterion);
+  if (o->criterion == HSS_CRIT_HMT) {
+    if (o->strategy != HSS_INCREMENTING)
+      return fail(HSS_ERR_ARG, "the HMT criterion is a test of the Incrementing strategy");
+    if (!(o->hmt_alpha > 1.0) || !std::isfinite(o->hmt_alpha))
+      return fail(HSS_ERR_ARG, "hmt_alpha must be finite and > 1 (got %g)", o->hmt_alpha);
+  }
   cudaStream_t st = (cudaStream_t)stream;
   hss_matrix_s* H = new (std::nothrow) hss_matrix_s();
   if (!H) return fail(HSS_ERR_NOMEM, "host allocation failed");

@@ -117,7 +117,10 @@ struct IncJob {
   double* tau;          // workspace b
   double er, ea;
   double rho;           // |(R_1)_11| of the first block, < 0 if none yet
-  double* res;          // out: [0]=|S_k|_F, [1]=|Sh|_F, [2]=min|diag|, [3]=|R_11|
+  int hmt;              // 1: the HMT criterion (Lemma 4.1) instead of eq. stopping_criteria
+  double hmt_c;         // alpha sqrt(2/pi) of the HMT criterion
+  double* res;          // out: [0]=|S_k|_F, [1]=|Sh|_F, [2]=min|diag| (the HMT estimate
+                        // with hmt), [3]=|R_11|
   int* flag;            // out: [0]=sufficient, [1]=new q
   // group form (launch_inc_group): P CTAs split the m rows
   int P;

@@ -9,6 +9,11 @@
 // Q_k is formed explicitly (backward accumulation of the reflectors) and
 // appended to the side's basis Q; a basis that reaches m columns spans the
 // whole sample space and is sufficient.
+//
+// With the HMT criterion (Lemma 4.1, eq. HMT_IQQH) the only test is
+//   alpha sqrt(2/pi) max_i |Sh(:, i)|_2 <= eps_a
+// (hmt_c = alpha sqrt(2/pi)); on failure the block's Q_k joins Q as above,
+// with no test on diag R_k.
 #include "hss_internal.h"
 
 namespace hss {
@@ -32,6 +37,17 @@ __device__ double block_sum(double v, double* sh) {
   return t;
 }
 
+__device__ double block_max(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x / 32] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < NW; ++w) t = fmax(t, sh[w]);
+  return t;
+}
+
 __global__ void __launch_bounds__(NT) k_inc_qr(const IncJob* __restrict__ jobs) {
   const IncJob jb = jobs[blockIdx.x];
   const int m = jb.m, b = jb.b, tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -50,7 +66,22 @@ __global__ void __launch_bounds__(NT) k_inc_qr(const IncJob* __restrict__ jobs) 
   for (long long e = tid; e < (long long)m * b; e += NT) s = __fma_rn(A[e], A[e], s);
   const double nSh = sqrt(block_sum(s, sh));
   if (tid == 0) { jb.res[0] = nS; jb.res[1] = nSh; jb.res[2] = -1.0; jb.res[3] = -1.0; }
-  if (b == 0 || nS == 0.0 || nSh < jb.er * nS || nSh / sqrt((double)b) < jb.ea) {
+  if (jb.hmt) {
+    // the largest squared column norm of Sh, a warp per column
+    double cm = 0.0;
+    for (int c = warp; c < b; c += NW) {
+      const double* col = A + (long long)c * m;
+      double w = 0.0;
+      for (int r = lane; r < m; r += 32) w = __fma_rn(col[r], col[r], w);
+      cm = fmax(cm, warp_sum(w));
+    }
+    const double est = jb.hmt_c * sqrt(block_max(cm, sh));
+    if (tid == 0) jb.res[2] = est;
+    if (b == 0 || est <= jb.ea) {
+      if (tid == 0) { jb.flag[0] = 1; jb.flag[1] = jb.q; }
+      return;
+    }
+  } else if (b == 0 || nS == 0.0 || nSh < jb.er * nS || nSh / sqrt((double)b) < jb.ea) {
     if (tid == 0) { jb.flag[0] = 1; jb.flag[1] = jb.q; }
     return;
   }
@@ -92,8 +123,8 @@ __global__ void __launch_bounds__(NT) k_inc_qr(const IncJob* __restrict__ jobs) 
     __syncthreads();
   }
   const double rho = jb.rho < 0.0 ? r11 : jb.rho;
-  if (tid == 0) { jb.res[2] = mn; jb.res[3] = r11; }
-  if (mn < jb.ea || mn < jb.er * rho) {
+  if (tid == 0) { if (!jb.hmt) jb.res[2] = mn; jb.res[3] = r11; }
+  if (!jb.hmt && (mn < jb.ea || mn < jb.er * rho)) {
     if (tid == 0) { jb.flag[0] = 1; jb.flag[1] = jb.q; }
     return;
   }
@@ -228,15 +259,34 @@ __global__ void __launch_bounds__(NT, 2) k_inc_group(const IncJob* __restrict__ 
   s1 = bsum(s1, sh);
   s2 = bsum(s2, sh);
   if (tid == 0) { __stcg(slot(parity, rank), s1); __stcg(slot(parity, rank) + 1, s2); }
+  if (jb.hmt) {   // partial squared column norms of the projected block
+    for (int c = tid / 32; c < b; c += NW) {
+      double w = 0.0;
+      for (int i = tid % 32; i < nr; i += 32) { const double h = V[i + (size_t)c * RB]; w = __fma_rn(h, h, w); }
+      w = warp_sum(w);
+      if ((tid & 31) == 0) __stcg(slot(parity, rank) + 2 + c, w);
+    }
+  }
   if (!gbar(jb.bar, P, epoch, err, &s_ok)) return;
   double nS = 0.0, nSh = 0.0;
   for (int q = 0; q < P; ++q) { nS += __ldcg(slot(parity, q)); nSh += __ldcg(slot(parity, q) + 1); }
+  double est = 0.0;
+  if (jb.hmt) {   // column totals in rank order, then the largest
+    double cm = 0.0;
+    for (int c = tid; c < b; c += NT) {
+      double w = 0.0;
+      for (int q = 0; q < P; ++q) w += __ldcg(slot(parity, q) + 2 + c);
+      cm = fmax(cm, w);
+    }
+    est = jb.hmt_c * sqrt(block_max(cm, sh));
+  }
   parity ^= 1;
   nS = sqrt(nS);
   nSh = sqrt(nSh);
   const bool lead = rank == 0 && tid == 0;
-  if (lead) { jb.res[0] = nS; jb.res[1] = nSh; jb.res[2] = -1.0; jb.res[3] = -1.0; }
-  if (b == 0 || nS == 0.0 || nSh < jb.er * nS || nSh / sqrt((double)b) < jb.ea) {
+  if (lead) { jb.res[0] = nS; jb.res[1] = nSh; jb.res[2] = jb.hmt ? est : -1.0; jb.res[3] = -1.0; }
+  if (jb.hmt ? (b == 0 || est <= jb.ea)
+             : (b == 0 || nS == 0.0 || nSh < jb.er * nS || nSh / sqrt((double)b) < jb.ea)) {
     if (lead) { jb.flag[0] = 1; jb.flag[1] = jb.q; }
     return;
   }
@@ -311,8 +361,8 @@ __global__ void __launch_bounds__(NT, 2) k_inc_group(const IncJob* __restrict__ 
     }
   }
   const double rho = jb.rho < 0.0 ? r11 : jb.rho;
-  if (lead) { jb.res[2] = mn; jb.res[3] = r11; }
-  if (mn < jb.ea || mn < jb.er * rho) {
+  if (lead) { if (!jb.hmt) jb.res[2] = mn; jb.res[3] = r11; }
+  if (!jb.hmt && (mn < jb.ea || mn < jb.er * rho)) {
     if (lead) { jb.flag[0] = 1; jb.flag[1] = jb.q; }
     return;
   }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhss.so")
 HSS_OK, HSS_ERR_ARG, HSS_ERR_NOMEM, HSS_ERR_CUDA = 0, 1, 2, 3
 HSS_ERR_NOT_CONVERGED, HSS_ERR_NONFINITE, HSS_ERR_TIMEOUT, HSS_ERR_UNSUPPORTED = 4, 5, 6, 7
 HSS_DOUBLING, HSS_INCREMENTING = 0, 1
+HSS_CRIT_NEW, HSS_CRIT_HMT = 0, 1
 HSS_PREC_FP64, HSS_PREC_TF32X2, HSS_PREC_BF16X3 = 0, 1, 2
 HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE = 0, 1, 2, 3
 HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
@@ -37,7 +38,8 @@ class hss_opts(C.Structure):
     _fields_ = [("leaf", C.c_int), ("strategy", C.c_int), ("precision", C.c_int),
                 ("level_tol_scaling", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
                 ("d0", C.c_int), ("dd", C.c_int), ("d_max", C.c_int), ("oversample_p", C.c_int),
-                ("seed", C.c_ulonglong), ("R", C.c_void_p), ("symmetric", C.c_int)]
+                ("seed", C.c_ulonglong), ("R", C.c_void_p), ("symmetric", C.c_int),
+                ("criterion", C.c_int), ("hmt_alpha", C.c_double)]
 
 
 class hss_stats(C.Structure):
@@ -128,9 +130,9 @@ def make_source(kind, n, a, b=None, ld=0, dim=0, p0=0.0, p1=0.0):
 
 
 def make_opts(leaf, rtol, atol, d0, dd, d_max, strategy, precision=HSS_PREC_FP64, p=10, seed=0,
-              R=None, level_tol_scaling=1, symmetric=0):
+              R=None, level_tol_scaling=1, symmetric=0, criterion=0, hmt_alpha=10.0):
     o = hss_opts(leaf, strategy, precision, level_tol_scaling, rtol, atol, d0, dd, d_max, p,
-                 seed, _ptr(R), int(symmetric))
+                 seed, _ptr(R), int(symmetric), int(criterion), float(hmt_alpha))
     o._keep = R
     return o
 

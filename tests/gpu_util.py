@@ -41,7 +41,8 @@ def gpu_compress(src, R, o, precision="fp64", pass_R=True, seed=0, allow_not_con
     Rd = col_major(R) if pass_R else None
     opts = hss.make_opts(o.leaf, o.rtol, o.atol, o.d0, o.dd, o.d_max, STRAT[o.strategy],
                          PREC[precision], o.p, seed, Rd, int(o.level_tol_scaling),
-                         int(getattr(o, "symmetric", False)))
+                         int(getattr(o, "symmetric", False)),
+                         1 if getattr(o, "criterion", "new") == "hmt" else 0, getattr(o, "hmt_alpha", 10.0))
     return hss.hss_compress(s, opts, allow_not_converged=allow_not_converged)
 
 
@@ -108,6 +109,8 @@ def rank_mismatch_allowed(t, side, o, d, k_lo, k_hi, n, band=0.1):
     sv = np.linalg.svd(S, compute_uv=False)
     scale = 1.0 / t.level if o.level_tol_scaling else 1.0
     er, ea = o.rtol * scale, o.atol * scale
+    if getattr(o, "criterion", "new") == "hmt":
+        er = 0.0          # the HMT criterion's final RRQR knows eps_a only
     rule = "hmt" if o.strategy == "doubling" else "plain"
     thr = _thresholds(diag, er, ea, rule, d, t.size, n - t.size)
     for j in range(max(0, k_lo - 1), min(diag.size, k_hi + 1)):

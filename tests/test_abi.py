@@ -71,6 +71,13 @@ def test_argument_validation_without_gpu(hss):
     assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
     bad = hss.make_opts(64, 1e-6, 1e-12, 64, 32, 256, 7)
     assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
+    # the HMT criterion: Incrementing only, alpha > 1 and finite, known criterion codes
+    for kw in (dict(strategy=hss.HSS_DOUBLING, criterion=hss.HSS_CRIT_HMT),
+               dict(strategy=hss.HSS_INCREMENTING, criterion=hss.HSS_CRIT_HMT, hmt_alpha=1.0),
+               dict(strategy=hss.HSS_INCREMENTING, criterion=hss.HSS_CRIT_HMT, hmt_alpha=float("inf")),
+               dict(strategy=hss.HSS_INCREMENTING, criterion=2)):
+        bad = hss.make_opts(64, 1e-6, 1e-12, 64, 32, 256, **kw)
+        assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG, kw
     assert h.value is None
     assert L.hss_matvec(None, 1, None, 1, None, 1, None) == hss.HSS_ERR_ARG
     hs = (C.c_void_p * 1)()
