@@ -45,6 +45,11 @@ Readings (see the design notes for the full list):
      column side a copy of the row side — S^c = S^r, the same ID (J^c = J^r,
      V = U), R^c = R^r and B21 = B12^T — so only the row side is sampled,
      tested and factored, and the column side takes its results.
+ P23 hard restart (section 4.3.2, Table 4): attempts with d = d0, 2 d0,
+     4 d0, ... (the last clipped to d_max), each Algorithm 3 with no growth
+     (d_max = d) on the first d columns of R and nothing carried over; the
+     strategy's own test is the failure check; the first converged attempt
+     is the result.  The known-rank mode is one attempt with d0 = d_max.
  P22 HMT criterion option (Lemma 4.1, eq. HMT_IQQH): Incrementing with the
      test of each block S_k replaced by  alpha sqrt(2/pi) max_i
      |((I - Q Q^T)^2 S_k)(:, i)|_2 <= eps_a  on the node's local sample
@@ -56,7 +61,7 @@ Readings (see the design notes for the full list):
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -162,6 +167,23 @@ def compress(src, R: np.ndarray, opts: Options) -> Result:
         d += dd
         ctx["bounds"].append(d)
         n_adapt += 1
+
+
+def compress_hard_restart(src, R: np.ndarray, opts: Options):
+    """The "hard-restart" mode the paper compares against (section 4.3.2,
+    Table 4, P23): without adaptivity a user restarts the compression from
+    scratch with more random vectors when it fails.  Returns the first
+    converged attempt (or the last one, at d_max) and the number of
+    restarts."""
+    d_cap = min(opts.d_max, R.shape[1])
+    d = min(opts.d0, d_cap)
+    restarts = 0
+    while True:
+        res = compress(src, R, replace(opts, d0=d, d_max=d))
+        if res.converged or d >= d_cap:
+            return res, restarts
+        d = min(2 * d, d_cap)
+        restarts += 1
 
 
 def _tols(opts: Options, level: int):

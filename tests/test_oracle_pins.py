@@ -437,3 +437,38 @@ def test_hmt_block_test_cases():
         assert not hss.hmt_block_test(Sk, st, 0.999 * thr, alpha)
         assert st["Q"].shape[1] == 9
         np.testing.assert_allclose(st["Q"].T @ st["Q"], np.eye(9), atol=1e-13)
+
+
+# ----------------------------------------- known-rank and hard restart (P23)
+@pytest.mark.parametrize("d0", [3, 5, 8, 20, 21])
+def test_hard_restart_on_exact_ranks(d0):
+    """A synthetic HSS matrix with per-level ranks 8/12/16/20 (level 4 ... 1):
+    one pass with d vectors converges exactly when d >= 21 — every local
+    sample then has more columns than its rank, while at d <= 20 the level-1
+    sides (32 rows, rank 20) fail the Incrementing test.  So the hard restart
+    doubles d0 until it reaches 21: the number of restarts and the final d
+    follow in closed form, and the ranks are the exact ones."""
+    n, leaf = 1024, 64
+    ranks = {4: 8, 3: 12, 2: 16, 1: 20}
+    A = w.synthetic_hss(n, leaf, ranks, seed=3)
+    R = w.gaussian_matrix(5, n, 0, 512)
+    o = Options(leaf=leaf, rtol=1e-10, atol=1e-14, d0=d0, dd=8, d_max=512)
+    res, k = hss.compress_hard_restart(w.dense_source(A), R, o)
+    want = 0
+    while d0 * 2 ** want < 21:
+        want += 1
+    assert res.converged and k == want and res.d_final == d0 * 2 ** want and res.n_adapt == 0
+    for t in res.nodes[1:]:
+        assert len(t.Jr) == len(t.Jc) == ranks[t.level], t.idx
+    assert apply.rel_error(res, A) < 1e-12
+
+
+def test_known_rank_single_pass():
+    """Known-rank mode (d0 = d_max): one pass, no growth; it converges at
+    d = 21 and reports NOT_CONVERGED at d = 20 on the matrix above."""
+    n, leaf = 1024, 64
+    A = w.synthetic_hss(n, leaf, {4: 8, 3: 12, 2: 16, 1: 20}, seed=3)
+    R = w.gaussian_matrix(5, n, 0, 512)
+    for d, ok in ((20, False), (21, True)):
+        res = compress(w.dense_source(A), R, Options(leaf=leaf, rtol=1e-10, atol=1e-14, d0=d, dd=8, d_max=d))
+        assert res.converged == ok and res.n_adapt == 0 and res.d_final == d
