@@ -19,6 +19,7 @@ error ||A - H||_F / ||A||_F.
   python bench.py --impl reference     # the CPU oracle on a bounded sample
   python bench.py --config c1|c3|c4|c5 # the other workload configurations
   python bench.py --config table3      # new criterion vs HMT criterion grid
+  python bench.py --config table4      # known-rank vs Incrementing vs hard restart
 
 Multi-GPU (torchrun): every rank compresses its own replica of the matrix
 (the path does not shard in this build), value = all ranks' flops / the
@@ -626,6 +627,88 @@ def run_table3(args):
     print(json.dumps(out), flush=True)
 
 
+def run_table4(args):
+    """The adaptivity-cost comparison of the paper's Table 4 on I + U D V^T
+    (N = 60000, r = 1200, D_kk = 2^(-53 (k-1)/r), U and V orthonormal from QR
+    of seeded Gaussian matrices; dense FP64 A, 28.8 GB), rtol = atol = 1e-14,
+    FP64, leaf 128, d_max = 2048.  Modes: known-rank (one pass with
+    d = r + 64 vectors), Incrementing from (d0, dd) = (128, 64) and (512,
+    128), hard restart from d0 = 128 and 512 (attempts d0, 2 d0, ... from
+    scratch).  Per mode: compression time (CUDA events around the call, all
+    attempts of a hard restart included), HSS rank, adaptations or restarts,
+    and ||A - H||_F / ||A||_F from H applied to identity blocks."""
+    import torch
+
+    from paper_1810_04125_gb300 import build as B
+    B.build()
+    from paper_1810_04125_gb300 import hss
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    n, r = (args.n or 60000), 1200
+    rng = np.random.default_rng(0)
+    U = torch.from_numpy(np.linalg.qr(rng.standard_normal((n, r)))[0]).to(dev)
+    V = torch.from_numpy(np.linalg.qr(rng.standard_normal((n, r)))[0]).to(dev)
+    D = 2.0 ** (-53.0 * torch.arange(r, dtype=torch.float64, device=dev) / r)
+    G = (V * D) @ U.t()                # G = V D U^T row-major: G.t() is A = I + U D V^T column-major
+    G.diagonal().add_(1.0)
+    del U, V
+    torch.cuda.synchronize()
+    src = hss.dense_source(G.t())
+    nA = float(torch.linalg.norm(G))
+    stream = torch.cuda.Stream(device=dev)
+    d_max = min(n, 2048)
+
+    def rel_error(H):
+        num = 0.0
+        blk = 4096
+        E = torch.zeros((blk, n), dtype=torch.float64, device=dev).t()
+        Y = torch.empty((blk, n), dtype=torch.float64, device=dev).t()
+        for j0 in range(0, n, blk):
+            wdt = min(blk, n - j0)
+            E.zero_()
+            E[j0:j0 + wdt, :wdt].copy_(torch.eye(wdt, dtype=torch.float64, device=dev))
+            hss.hss_matvec(H, E[:, :wdt], Y[:, :wdt], stream=stream)
+            torch.cuda.synchronize()
+            num += float(((Y[:, :wdt] - G[j0:j0 + wdt].t()) ** 2).sum())
+        return (num ** 0.5) / nA
+
+    rows = []
+
+    def run(mode, d0, dd):
+        dmx = d0 if mode == "known-rank" else d_max
+        o = hss.make_opts(128, 1e-14, 1e-14, d0, dd, dmx, hss.HSS_INCREMENTING, hss.HSS_PREC_FP64, 10, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            if mode == "hard-restart":
+                H, k = hss.hss_compress_restart(src, o, stream=stream, allow_not_converged=True)
+            else:
+                H = hss.hss_compress(src, o, stream=stream, allow_not_converged=True)
+                k = None
+            e1.record(stream)
+        torch.cuda.synchronize()
+        st = H.stats()
+        row = {"mode": mode, "d0": d0, "dd": dd if mode == "incrementing" else None,
+               "compress_s": e0.elapsed_time(e1) / 1e3, "converged": int(st.converged),
+               "rank": max(st.max_rank_r, st.max_rank_c), "d_final": st.d_final,
+               "adaptations": st.n_adapt if k is None else k,
+               "rel_error": rel_error(H) if st.converged else None}
+        del H
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+
+    run("known-rank", min(n, r + 64), 64)
+    for d0, dd in ((128, 64), (512, 128)):
+        run("incrementing", d0, dd)
+        run("hard-restart", d0, dd)
+    out = {"metric": "HSS compression s per adaptivity mode (Table 4)", "unit": "s", "data": "synthetic",
+           "dtype": "f64", "higher_is_better": False,
+           "config": {"workload": f"udv_n{n}_r{r}", "leaf": 128, "rtol": 1e-14, "atol": 1e-14,
+                      "strategy": "incrementing", "d_max": d_max},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def oracle_sample(n):
     """The CPU oracle on the same family and settings at order n."""
     import workloads as w
@@ -700,13 +783,15 @@ def main():
     ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="diagnostic override of the matrix order")
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table3"],
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table3", "table4"],
                     help="workload configuration (c2, the default, is the one the metric is quoted on)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "table3":
         run_table3(args)
+    elif args.config == "table4":
+        run_table4(args)
     elif args.config != "c2":
         run_config(args)
     else:

@@ -157,6 +157,22 @@ typedef struct hss_matrix_s* hss_matrix;   /* opaque; owns device memory    */
 hss_status hss_compress(const hss_source* A, const hss_opts* opts, void* stream,
                         hss_matrix* out);
 
+/* The two non-adaptive modes the paper measures its adaptivity against
+ * (section 4.3.2, Table 4).  "Known-rank" is hss_compress with
+ * opts->d0 == opts->d_max: one pass with a fixed number of random vectors,
+ * no growth (HSS_ERR_NOT_CONVERGED if that number is too small).
+ * "Hard-restart", this call: without adaptivity a user restarts from scratch
+ * with more random vectors when a compression fails.  Attempts with
+ * d = d0, 2 d0, 4 d0, ... (the last clipped to d_max), each an hss_compress
+ * with d0 = d_max = d on the first d columns of R (opts->R, or the generated
+ * R of opts->seed, whose leading columns are the same for every d), nothing
+ * carried over between attempts; the strategy's own test decides failure.
+ * *out receives the first converged attempt (or the attempt at d_max with
+ * HSS_ERR_NOT_CONVERGED, as hss_compress); *restarts (host, may be NULL) the
+ * number of failed attempts.  Its stats cover the last attempt only. */
+hss_status hss_compress_restart(const hss_source* A, const hss_opts* opts, void* stream,
+                                hss_matrix* out, int* restarts);
+
 /* hss_compress for a batch of independent matrices (the paper compresses
  * one matrix per call; the batch has no counterpart there): A[count] and
  * opts[count] (one options struct per matrix), out[count] receives the

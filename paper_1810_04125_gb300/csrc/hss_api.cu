@@ -1294,6 +1294,29 @@ hss_status hss_compress(const hss_source* A, const hss_opts* o, void* stream, hs
   return HSS_OK;
 }
 
+hss_status hss_compress_restart(const hss_source* A, const hss_opts* o, void* stream, hss_matrix* out,
+                                int* restarts) {
+  if (restarts) *restarts = 0;
+  if (!A || !o || !out) return fail(HSS_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  const int cap = std::min(o->d_max, A->n);
+  hss_opts a = *o;
+  int d = std::min(o->d0, cap), k = 0;
+  for (;;) {
+    a.d0 = a.d_max = d;
+    hss_matrix H = nullptr;
+    const hss_status s = hss_compress(A, &a, stream, &H);
+    if (s != HSS_ERR_NOT_CONVERGED || d >= cap) {   // converged, failed, or the last attempt
+      *out = H;
+      if (restarts) *restarts = k;
+      return s;
+    }
+    hss_free(H);
+    d = (int)std::min<long long>(2LL * d, cap);
+    ++k;
+  }
+}
+
 hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int count, void* stream,
                                 hss_matrix* out) {
   if (count < 0) return fail(HSS_ERR_ARG, "count must be >= 0 (got %d)", count);

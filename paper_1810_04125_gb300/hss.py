@@ -23,7 +23,7 @@ HSS_PREC_FP64, HSS_PREC_TF32X2, HSS_PREC_BF16X3 = 0, 1, 2
 HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE = 0, 1, 2, 3
 HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
 
-EXPORTS = ["hss_compress", "hss_compress_batched", "hss_matvec", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
+EXPORTS = ["hss_compress", "hss_compress_restart", "hss_compress_batched", "hss_matvec", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
            "hss_free", "hss_status_str", "hss_last_error", "hss_rcb_order",
            "hss_random_normal", "hss_sample_offdiag", "hss_sample_offdiag_noalloc"]
 
@@ -72,6 +72,8 @@ def lib():
         vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.c_double
         L.hss_compress.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), vp, C.POINTER(vp)]
         L.hss_compress_batched.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), i, vp, C.POINTER(vp)]
+        L.hss_compress_restart.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), vp, C.POINTER(vp),
+                                           C.POINTER(i)]
         L.hss_matvec.argtypes = [vp, i, vp, ll, vp, ll, vp]
         L.hss_to_dense.argtypes = [vp, vp, ll, vp]
         L.hss_get_stats.argtypes = [vp, C.POINTER(hss_stats)]
@@ -145,6 +147,17 @@ def hss_compress(source, opts, stream=None, allow_not_converged=False):
         return HSSMatrix(h.value, converged=False)
     _check(st)
     return HSSMatrix(h.value)
+
+
+def hss_compress_restart(source, opts, stream=None, allow_not_converged=False):
+    """The hard-restart mode; returns (HSSMatrix, number of restarts)."""
+    h = C.c_void_p()
+    k = C.c_int(0)
+    st = lib().hss_compress_restart(C.byref(source), C.byref(opts), _stream(stream), C.byref(h), C.byref(k))
+    if st == HSS_ERR_NOT_CONVERGED and h.value and allow_not_converged:
+        return HSSMatrix(h.value, converged=False), k.value
+    _check(st)
+    return HSSMatrix(h.value), k.value
 
 
 def hss_to_dense(H, out, stream=None):

@@ -46,6 +46,18 @@ def gpu_compress(src, R, o, precision="fp64", pass_R=True, seed=0, allow_not_con
     return hss.hss_compress(s, opts, allow_not_converged=allow_not_converged)
 
 
+def gpu_compress_restart(src, R, o, precision="fp64", pass_R=True, seed=0):
+    """The hard-restart mode through the C ABI: (handle, restarts)."""
+    from paper_1810_04125_gb300 import hss
+    s = device_source(src)
+    Rd = col_major(R) if pass_R else None
+    opts = hss.make_opts(o.leaf, o.rtol, o.atol, o.d0, o.dd, o.d_max, STRAT[o.strategy],
+                         PREC[precision], o.p, seed, Rd, int(o.level_tol_scaling),
+                         int(getattr(o, "symmetric", False)),
+                         1 if getattr(o, "criterion", "new") == "hmt" else 0, getattr(o, "hmt_alpha", 10.0))
+    return hss.hss_compress_restart(s, opts, allow_not_converged=True)
+
+
 def gpu_dense(H, n):
     import torch
     from paper_1810_04125_gb300 import hss

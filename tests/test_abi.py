@@ -84,5 +84,10 @@ def test_argument_validation_without_gpu(hss):
     assert L.hss_compress_batched(None, None, -1, None, hs) == hss.HSS_ERR_ARG
     assert L.hss_compress_batched(None, C.byref(o), 1, None, hs) == hss.HSS_ERR_ARG
     assert L.hss_compress_batched(None, None, 0, None, None) == hss.HSS_OK
+    k = C.c_int(5)
+    assert L.hss_compress_restart(None, C.byref(o), None, C.byref(h), C.byref(k)) == hss.HSS_ERR_ARG
+    assert k.value == 0
+    bad = hss.make_opts(0, 1e-6, 1e-12, 64, 32, 256, hss.HSS_INCREMENTING)
+    assert L.hss_compress_restart(C.byref(s), C.byref(bad), None, C.byref(h), None) == hss.HSS_ERR_ARG
     assert L.hss_rcb_order(None, 10, 2, 10, 4, None) == hss.HSS_ERR_ARG
     assert L.hss_random_normal(0, 10, 0, 1, None, 10, 0, None) == hss.HSS_ERR_ARG
