@@ -198,7 +198,8 @@ struct hss_matrix_s {
   size_t h_pinned_cap = 0;
   int d_final = 0, n_adapt = 0, converged = 0;
   int qrcp_cap = -1;       // co-resident CTAs of the QRCP kernel at width qrcp_cap_d
-  int qrcp_cap_d = -1;
+  int qrcp_cap_d = -1;     // and shape qrcp_cap_w
+  int qrcp_cap_w = -1;
   int pack_decided = -1;   // mixed forms, generated A: packed tiles (1) or not (0)
   bool sym = false;        // symmetric option: the column side mirrors the row side
   bool trace = false;      // HSS_TRACE=1: one stderr line per QRCP launch
@@ -603,9 +604,13 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   // its m columns (g a multiple of 32, at most qrcp_cols_per_cta()), with g
   // the smallest width for which the groups of a batch fit the co-resident
   // CTAs; one cooperative launch per batch (plain launch when every P is 1).
-  if (H->qrcp_cap_d != d) {
-    H->qrcp_cap = qrcp_group_capacity(d);
+  // few node sides (the top levels): the wide shape, whose groups have half
+  // as many CTAs; otherwise the narrow one
+  const int wide = nj <= 8 ? 1 : 0;
+  if (H->qrcp_cap_d != d || H->qrcp_cap_w != wide) {
+    H->qrcp_cap = qrcp_group_capacity(d, wide);
     H->qrcp_cap_d = d;
+    H->qrcp_cap_w = wide;
   }
   const int cap = H->qrcp_cap, NL = qrcp_cols_per_cta();
   if (cap <= 0) return fail(HSS_ERR_CUDA, "QRCP kernel cannot be resident (d = %d)", d);
@@ -722,11 +727,11 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
         for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
       int2* dm;
       CKS(upload_jobs(H, map, &dm, st));
-      CK(launch_qrcp(dj, dm, (int)map.size(), d, H->d_flag + 2, st));
+      CK(launch_qrcp(dj, dm, (int)map.size(), d, wide, H->d_flag + 2, st));
       CK(cudaFreeAsync(dm, st));
       ctas_total += (int)map.size();
     } else {
-      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), d, H->d_flag + 2, st));
+      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), d, wide, H->d_flag + 2, st));
       ctas_total += (int)(b.b1 - b.b0);
     }
     H->launches++;

@@ -176,9 +176,10 @@ cudaError_t launch_gemm_tc(const GemmJob* jobs_dev, const GemmTile* tiles_dev, i
 // the job's group) and the launch is cooperative.  d_max: largest d.  A CTA
 // owns at most qrcp_cols_per_cta() columns (m / P); W is col-major with
 // ldw a multiple of 4; nrm holds m doubles.
+// wide: 256 threads and two CTAs per SM (else 128 threads, four per SM).
 int qrcp_cols_per_cta();
-int qrcp_group_capacity(int d_max);
-cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, int* err,
+int qrcp_group_capacity(int d_max, int wide);
+cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, int wide, int* err,
                         cudaStream_t st);
 cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
 // The same test with the rows of each side split over a group of P CTAs

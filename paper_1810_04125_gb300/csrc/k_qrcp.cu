@@ -1,7 +1,7 @@
 // Batched interpolative decomposition by QR with column pivoting (eq. ID):
 // for every job, W = S^T (d x m, the sample's rows as columns) is factored
 // as W Pi = Q [R1 R2], truncated at the first pivot that fails the rank
-// rule, and X = R1^{-1} R2 (= E^T) is formed by back substitution.
+// rule, and X = R1^{-1} R2 (= E^T) is formed by blocked back substitution.
 //
 // Rank rules (tolerances already divided by level(tau)):
 //   rule 0 (plain):  stop at pivot j when |R_jj| <= eps_a or
@@ -25,12 +25,13 @@
 // One pass over the trailing matrix per pivot step.  Applying reflector
 // H_{j-1} to a column and forming the dot product with the next reflector
 // v_j are fused: the pass of step j reads W(r, c) (r >= j), subtracts
-// tw_{j-1}(c) v_{j-1}(r), stores it and accumulates v_j(r) times it.  Row
+// tw_{j-1}(c) v_{j-1}(r), stores it and accumulates v_j(r) times it (both
+// reflectors kept unscaled, their scale folded into the coefficients).  Row
 // j-1 and the norm down-date only need tw_{j-1}(c) and the old W(j-1, c),
 // so the next pivot is known before the pass; the pivot column is brought
 // up to date on the fly when it is read.  Inside a CTA eight lanes share a
-// live column (a quad of 4 rows each, 16-byte loads) and the eight warps
-// split the rows; the partial dot products meet in shared memory.
+// live column (a quad of 4 rows each, 16-byte loads) and the warps split
+// the rows; the partial dot products meet in shared memory.
 //
 // Pivot = largest down-dated squared column norm (lowest index on ties),
 // recomputed from the column when cancellation has left less than
@@ -44,8 +45,21 @@
 namespace hss {
 namespace {
 
-constexpr int NT = 256, NW = NT / 32;
+// Two launch shapes: 256 threads and two CTAs per SM for levels with few
+// node sides, 128 threads and four CTAs per SM otherwise (more co-resident
+// groups, so that one group's serial phases overlap others' passes).  The
+// registers are budgeted for 512 threads per SM either way.
+constexpr int NT_WIDE = 256, NT_NARROW = 128;
 constexpr int NLMAX = 256;   // own columns per CTA (host sizes the groups)
+constexpr int PCU = 8;       // loads in flight per thread when the pivot column is read
+constexpr int EB = 16;       // rows per block of the back substitution X = R1^{-1} R2
+
+// sum of N partials spaced NLMAX apart, as a balanced tree (fixed order)
+template <int N>
+__device__ __forceinline__ double tree_sum(const double* p) {
+  if constexpr (N == 1) return p[0];
+  else return tree_sum<N / 2>(p) + tree_sum<N - N / 2>(p + (N / 2) * NLMAX);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -97,6 +111,7 @@ __device__ bool group_barrier(unsigned* bar, int P, unsigned& epoch, int* err, i
 }
 
 // block-wide sum; every thread gets the same value (fixed order)
+template <int NW>
 __device__ double block_sum(double v, double* sh) {
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x / 32] = v;
@@ -126,7 +141,7 @@ __device__ __forceinline__ void rank_thresholds(const QrcpJob& jb, int d, int j,
 }
 
 // shared-memory carve-up (dynamic part): two reflectors of d_max entries,
-// then per own live column: partial dots of the eight warps, tw, top, norm^2,
+// then per own live column: partial dots of the warps, tw, top, norm^2,
 // norm^2 at the last exact computation, column index
 struct Carve {
   double *v0, *v1, *part, *tw, *top, *nrm, *orig;
@@ -134,6 +149,7 @@ struct Carve {
   int* rc;   // columns whose norm is recomputed this step
 };
 
+template <int NW>
 __device__ __forceinline__ Carve carve(double* base, int dmax) {
   const int dp = (dmax + 3) & ~3;   // 32-byte aligned reflectors, whole quads
   Carve c;
@@ -149,8 +165,10 @@ __device__ __forceinline__ Carve carve(double* base, int dmax) {
   return c;
 }
 
-__global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs,
-                                             const int2* __restrict__ map, int* err, int dmax) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict__ jobs,
+                                                   const int2* __restrict__ map, int* err, int dmax) {
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) double smem_d[];
   const int2 me = map ? map[blockIdx.x] : make_int2(blockIdx.x, 0);
   const QrcpJob jb = jobs[me.x];
@@ -160,14 +178,14 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
   double* W = jb.W;
   double* diag = jb.diag;
   double* liveg = jb.nrm;   // global: +1 live, -1 retired (read by rank 0 at the end)
-  Carve S = carve(smem_d, dmax);
+  Carve S = carve<NW>(smem_d, dmax);
   double* vp = S.v0;        // v_{j-1}
   double* vc = S.v1;        // v_j
   __shared__ double sh[NW];
   __shared__ unsigned long long shk[NW];
   __shared__ int shi[NW], shp[NW];
   __shared__ int s_ok, s_p, s_pos, s_stop, s_nl, s_nrc;
-  __shared__ double s_twp, s_tau, s_scal, s_r11;
+  __shared__ double s_twp, s_tau, s_scal, s_r11, s_uj;
   __shared__ double s_th[2][2];   // stop thresholds (eps_a, eps_r |R_11|) by step parity
   unsigned epoch = 0;
 
@@ -206,18 +224,20 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
   if (tid == 0) s_nrc = 0;
   __syncthreads();
   const double tol3z = 1.4901161193847656e-08;   // sqrt(2^-52)
-  double tau = 0.0;
+  // the reflector of step j is kept unscaled, u_j = x - beta e_j (rows >= j,
+  // x the pivot column), H_j = I - tau_j v v^T with v = scal_j u_j; with
+  // dot = u_j^T x over a column, row j of R is top - c1 dot and the column
+  // update of the next pass is x -= (c2 dot) u_j: c1 = tau scal,
+  // c2 = tau scal^2 (no scaling pass over the reflector)
+  double c1 = 0.0, c2 = 0.0, uj = 0.0;
   for (int j = 0; j <= kmax; ++j) {
     // ---- (a) finish step j-1 on the own live columns: tw_{j-1} from the
     // partial dots, row j-1 of R, norm down-date; local argmax
     for (int t = tid; t < nl; t += NT) {
       if (j >= 1) {
-        const double* pt = S.part + t;
-        const double dot = ((pt[0] + pt[NLMAX]) + (pt[2 * NLMAX] + pt[3 * NLMAX])) +
-                           ((pt[4 * NLMAX] + pt[5 * NLMAX]) + (pt[6 * NLMAX] + pt[7 * NLMAX]));
-        const double twv = tau * dot;
-        S.tw[t] = twv;
-        const double rjc = S.top[t] - twv;
+        const double dot = tree_sum<NW>(S.part + t);
+        S.tw[t] = c2 * dot;
+        const double rjc = S.top[t] - c1 * dot;
         W[(long long)S.lc[t] * ldw + (j - 1)] = rjc;
         const double v = __fma_rn(-rjc, rjc, S.nrm[t]);
         if (v <= tol3z * S.orig[t]) S.rc[atomicAdd(&s_nrc, 1)] = t;
@@ -307,12 +327,24 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
       const double* pc = W + (long long)p * ldw;
       const double twp = s_twp;
       double s = 0.0;
-      for (int r = j + tid; r < d; r += NT) {
-        const double x = __fma_rn(-twp, vp[r], P > 1 ? __ldcg(pc + r) : pc[r]);
-        vc[r] = x;
-        s = __fma_rn(x, x, s);
+      for (int r0 = j + tid; r0 < d; r0 += PCU * NT) {   // PCU loads in flight per thread
+        double xv[PCU];
+#pragma unroll
+        for (int u = 0; u < PCU; ++u) {
+          const int r = r0 + u * NT;
+          xv[u] = r < d ? (P > 1 ? __ldcg(pc + r) : pc[r]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < PCU; ++u) {
+          const int r = r0 + u * NT;
+          if (r < d) {
+            const double x = __fma_rn(-twp, vp[r], xv[u]);
+            vc[r] = x;
+            s = __fma_rn(x, x, s);
+          }
+        }
       }
-      const double ss = block_sum(s, sh);
+      const double ss = block_sum<NW>(s, sh);
       // thread 0: norm, stop test, tau; thread 32 (another warp, so the two
       // FP64 divisions run side by side): the scaling of the reflector
       if (tid == 0 || tid == 32) {
@@ -334,6 +366,7 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
           s_stop = stop;
           if (!stop) {
             s_tau = (beta - x0) / beta;
+            s_uj = x0 - beta;
             const int pos = s_pos;
             if (pos >= 0) {
               // the own pivot column leaves the live list
@@ -360,82 +393,118 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
       __syncthreads();
       if (s_stop) { k = j; stopped = 1; break; }
       nl = s_nl;
-      tau = s_tau;
-      const double scal = s_scal;
-      for (int r = j + 1 + tid; r < d; r += NT) vc[r] *= scal;
-      if (tid == 0) vc[j] = 1.0;
-      __syncthreads();
+      c1 = s_tau * s_scal;
+      c2 = c1 * s_scal;
+      uj = s_uj;   // u_j(j); vc[j] keeps x(j), which the pass replaces by uj
     }
     // ---- (d) the fused pass: rows r >= j of the own live columns,
-    //   x = W(r,c) - tw_{j-1}(c) v_{j-1}(r);  W(r,c) = x;  dot += v_j(r) x
-    // A warp takes four live columns at a time, eight lanes per column, lane
-    // i of a group one quad (4 rows) of each block of 8 quads, so that every
-    // 16-byte load of the warp touches four 128-byte lines.  Blocks of a
-    // column batch are dealt to the warps round robin; the eight lanes of a
-    // column add their partial dots with three shuffles.
+    //   x = W(r,c) - tw_{j-1}(c) u_{j-1}(r);  W(r,c) = x;  dot += u_j(r) x
+    // A warp takes four live columns at a time (a batch), eight lanes per
+    // column, lane i of a group one quad (4 rows) of each block of 8 quads,
+    // so that every 16-byte load of the warp touches four 128-byte lines.
+    // The blocks of a batch are dealt to the warps round robin, two at a
+    // time (a unit); a warp walks its units across the batches in order and
+    // loads the next unit while it computes the current one, so the loads
+    // of one batch overlap the arithmetic of the previous.  At the end of a
+    // batch the eight lanes of a column add their partial dots with three
+    // shuffles; a batch in which a warp has no block leaves its zero.
     {
       if (tid == 0) s_nrc = 0;   // read for the last time before the pivot step
       const int q0 = j >> 2, q1 = (d + 3) >> 2;
       const int B0 = q0 >> 3, NB = ((q1 + 7) >> 3) - B0;
       const int g = lane >> 3, i8 = lane & 7;
-      for (int b = 0; 4 * b < nl; ++b) {
+      const int nbat = (nl + 3) >> 2;
+      for (int t = lane; t < nl; t += 32) S.part[warp * NLMAX + t] = 0.0;
+      __syncwarp();
+      // the warp's first block of batch b; units step by two blocks per warp
+      auto first_blk = [&](int bb) { return (warp - (bb * NB) % NW + NW) % NW; };
+      auto advance = [&](int& bb, int& bk) {
+        while (bb < nbat && bk >= NB) {
+          ++bb;
+          if (bb < nbat) bk = first_blk(bb);
+        }
+      };
+      auto load = [&](int bb, int bk, double2& a01, double2& a23, double2& b01, double2& b23, bool& va,
+                      bool& vb) {
+        const int t = 4 * bb + g;
+        const bool act = t < nl;
+        const double* col = W + (long long)(act ? S.lc[t] : 0) * ldw;
+        const int qa = 8 * (B0 + bk) + i8, qb = qa + 8 * NW;
+        va = act && qa >= q0 && qa < q1;
+        vb = act && bk + NW < NB && qb >= q0 && qb < q1;
+        if (va) { const double2* pp = (const double2*)(col + 4 * qa); a01 = pp[0]; a23 = pp[1]; }
+        if (vb) { const double2* pp = (const double2*)(col + 4 * qb); b01 = pp[0]; b23 = pp[1]; }
+      };
+      int b = 0, blk = first_blk(0);
+      advance(b, blk);
+      const double2 z2 = make_double2(0.0, 0.0);
+      double2 ca01 = z2, ca23 = z2, cb01 = z2, cb23 = z2;
+      bool cva = false, cvb = false;
+      if (b < nbat) load(b, blk, ca01, ca23, cb01, cb23, cva, cvb);
+      double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;   // four short chains
+      while (b < nbat) {
+        // the next unit, its loads in flight during this unit's arithmetic
+        int nb = b, nbk = blk + 2 * NW;
+        advance(nb, nbk);
+        double2 na01 = z2, na23 = z2, nb01 = z2, nb23 = z2;
+        bool nva = false, nvb = false;
+        if (nb < nbat) load(nb, nbk, na01, na23, nb01, nb23, nva, nvb);
         const int t = 4 * b + g;
         const bool act = t < nl;
         double* col = W + (long long)(act ? S.lc[t] : 0) * ldw;
         const double twv = act ? S.tw[t] : 0.0;
-        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;   // four short chains
-        // two blocks at a time: four 16-byte loads in flight per lane
-        for (int blk = (warp - (b * NB) % NW + NW) % NW; blk < NB; blk += 2 * NW) {
-          int qa = 8 * (B0 + blk) + i8, qb = qa + 8 * NW;
-          const bool va = act && qa >= q0 && qa < q1;
-          const bool vb = act && blk + NW < NB && qb >= q0 && qb < q1;
-          double2 a01, a23, b01, b23;
-          if (va) { const double2* pp = (const double2*)(col + 4 * qa); a01 = pp[0]; a23 = pp[1]; }
-          if (vb) { const double2* pp = (const double2*)(col + 4 * qb); b01 = pp[0]; b23 = pp[1]; }
+        const int qa = 8 * (B0 + blk) + i8, qb = qa + 8 * NW;
 #pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2) {
-            const bool v = h2 ? vb : va;
-            if (!v) continue;
-            const int r = 4 * (h2 ? qb : qa);
-            double x[4] = {h2 ? b01.x : a01.x, h2 ? b01.y : a01.y, h2 ? b23.x : a23.x, h2 ? b23.y : a23.y};
-            const double2 p01 = *(const double2*)(vp + r), p23 = *(const double2*)(vp + r + 2);
-            const double2 c01 = *(const double2*)(vc + r), c23 = *(const double2*)(vc + r + 2);
-            const double pv[4] = {p01.x, p01.y, p23.x, p23.y};
-            const double cv[4] = {c01.x, c01.y, c23.x, c23.y};
-            if (r >= j && r + 4 <= d) {
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const bool v = h2 ? cvb : cva;
+          if (!v) continue;
+          const int r = 4 * (h2 ? qb : qa);
+          double x[4] = {h2 ? cb01.x : ca01.x, h2 ? cb01.y : ca01.y, h2 ? cb23.x : ca23.x, h2 ? cb23.y : ca23.y};
+          const double2 p01 = *(const double2*)(vp + r), p23 = *(const double2*)(vp + r + 2);
+          const double2 c01 = *(const double2*)(vc + r), c23 = *(const double2*)(vc + r + 2);
+          const double pv[4] = {p01.x, p01.y, p23.x, p23.y};
+          const double cv[4] = {r == j ? uj : c01.x, r + 1 == j ? uj : c01.y, r + 2 == j ? uj : c23.x,
+                                r + 3 == j ? uj : c23.y};
+          if (r >= j && r + 4 <= d) {
 #pragma unroll
-              for (int u = 0; u < 4; ++u) x[u] = __fma_rn(-twv, pv[u], x[u]);
-              acc0 = __fma_rn(cv[0], x[0], acc0);
-              acc1 = __fma_rn(cv[1], x[1], acc1);
-              acc2 = __fma_rn(cv[2], x[2], acc2);
-              acc3 = __fma_rn(cv[3], x[3], acc3);
-              if (r == j) S.top[t] = x[0];
-            } else {
+            for (int u = 0; u < 4; ++u) x[u] = __fma_rn(-twv, pv[u], x[u]);
+            acc0 = __fma_rn(cv[0], x[0], acc0);
+            acc1 = __fma_rn(cv[1], x[1], acc1);
+            acc2 = __fma_rn(cv[2], x[2], acc2);
+            acc3 = __fma_rn(cv[3], x[3], acc3);
+            if (r == j) S.top[t] = x[0];
+          } else {
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                if (r + u >= j && r + u < d) {
-                  x[u] = __fma_rn(-twv, pv[u], x[u]);
-                  if (u == 0) acc0 = __fma_rn(cv[u], x[u], acc0);
-                  else if (u == 1) acc1 = __fma_rn(cv[u], x[u], acc1);
-                  else if (u == 2) acc2 = __fma_rn(cv[u], x[u], acc2);
-                  else acc3 = __fma_rn(cv[u], x[u], acc3);
-                }
-              }
-              if (r <= j && j < r + 4) {
-                const int u = j - r;   // select without indexing x (keeps it in registers)
-                S.top[t] = u == 0 ? x[0] : (u == 1 ? x[1] : (u == 2 ? x[2] : x[3]));
+            for (int u = 0; u < 4; ++u) {
+              if (r + u >= j && r + u < d) {
+                x[u] = __fma_rn(-twv, pv[u], x[u]);
+                if (u == 0) acc0 = __fma_rn(cv[u], x[u], acc0);
+                else if (u == 1) acc1 = __fma_rn(cv[u], x[u], acc1);
+                else if (u == 2) acc2 = __fma_rn(cv[u], x[u], acc2);
+                else acc3 = __fma_rn(cv[u], x[u], acc3);
               }
             }
-            double2* pp = (double2*)(col + r);
-            pp[0] = make_double2(x[0], x[1]);
-            pp[1] = make_double2(x[2], x[3]);
+            if (r <= j && j < r + 4) {
+              const int u = j - r;   // select without indexing x (keeps it in registers)
+              S.top[t] = u == 0 ? x[0] : (u == 1 ? x[1] : (u == 2 ? x[2] : x[3]));
+            }
           }
+          double2* pp = (double2*)(col + r);
+          pp[0] = make_double2(x[0], x[1]);
+          pp[1] = make_double2(x[2], x[3]);
         }
-        double acc = (acc0 + acc1) + (acc2 + acc3);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (act && i8 == 0) S.part[warp * NLMAX + t] = acc;
+        if (nb != b) {   // the batch is done: its partial dots
+          double acc = (acc0 + acc1) + (acc2 + acc3);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          if (act && i8 == 0) S.part[warp * NLMAX + t] = acc;
+          acc0 = acc1 = acc2 = acc3 = 0.0;
+        }
+        b = nb;
+        blk = nbk;
+        ca01 = na01; ca23 = na23; cb01 = nb01; cb23 = nb23;
+        cva = nva; cvb = nvb;
       }
       // swap the reflectors: v_j becomes the one to apply next
       double* tmp = vp;
@@ -470,60 +539,113 @@ __global__ void __launch_bounds__(NT, 2) k_qrcp(const QrcpJob* __restrict__ jobs
     }
   }
   if (jb.do_id && accepted && k > 0 && k < m) {
-    // X = R1^{-1} R2 in place on the own surviving columns (warp per column)
+    // X = R1^{-1} R2 in place on the own surviving columns, by blocks of up
+    // to EB rows from the bottom: the diagonal block is solved in shared
+    // memory (a thread per column), then the rows above take one update of
+    // depth EB, X(r, c) -= sum_b R1(r, i0 + b) X(i0 + b, c) (a thread per
+    // row), so an entry of X is read and written once per block, not once
+    // per row.  R1(r, i) = W(r, piv[i]) for r < i.
+    const int dp = (dmax + 3) & ~3;
     double* rd = S.v0;   // 1 / R_ii
+    double* xs = S.v1;   // the block's rows of X, row-major (ld nc)
+    double* rb = S.part; // the block of R1, rb[a * EB + b] = R1(i0 + a, i0 + b)
+    int* pb = S.rc;      // piv[i0 .. i1)
     for (int i = tid; i < k; i += NT) rd[i] = 1.0 / __ldcg(diag + i);
-    __syncthreads();
-    for (int t = warp; t < nl; t += NW) {
-      double* col = W + (long long)S.lc[t] * ldw;
-      for (int i = k - 1; i >= 0; --i) {
-        __syncwarp();
-        const double xi = col[i] * rd[i];
-        __syncwarp();
-        if (lane == 0) col[i] = xi;
-        const double* ri = W + (long long)__ldcg(jb.piv + i) * ldw;
-        for (int r = lane; r < i; r += 32) col[r] = __fma_rn(-__ldcg(ri + r), xi, col[r]);
+    for (int c0 = 0; c0 < nl; c0 += dp) {   // own columns in chunks whose block rows fit xs
+      const int nc = min(nl - c0, dp);
+      const int BR = max(1, min(EB, dp / nc));
+      for (int i1 = k; i1 > 0; i1 -= BR) {
+        const int i0 = max(0, i1 - BR), nb = i1 - i0;
+        __syncthreads();   // xs, rb, pb free; rd written
+        for (int a = tid; a < nb; a += NT) pb[a] = __ldcg(jb.piv + i0 + a);
+        for (int e = tid; e < nb * nc; e += NT) {
+          const int a = e / nc, c = e - a * nc;
+          xs[e] = W[(long long)S.lc[c0 + c] * ldw + i0 + a];
+        }
+        __syncthreads();
+        for (int e = tid; e < nb * nb; e += NT) {
+          const int a = e / nb, b = e - a * nb;
+          rb[a * EB + b] = a < b ? __ldcg(W + (long long)pb[b] * ldw + i0 + a) : 0.0;
+        }
+        __syncthreads();
+        for (int c = tid; c < nc; c += NT) {
+          double* col = W + (long long)S.lc[c0 + c] * ldw;
+          for (int b = nb - 1; b >= 0; --b) {
+            const double x = xs[b * nc + c] * rd[i0 + b];
+            xs[b * nc + c] = x;
+            col[i0 + b] = x;
+            for (int a = 0; a < b; ++a) xs[a * nc + c] = __fma_rn(-rb[a * EB + b], x, xs[a * nc + c]);
+          }
+        }
+        __syncthreads();
+        for (int r = tid; r < i0; r += NT) {
+          double rv[EB];
+#pragma unroll
+          for (int b = 0; b < EB; ++b) rv[b] = b < nb ? __ldcg(W + (long long)pb[b] * ldw + r) : 0.0;
+          for (int c = 0; c < nc; ++c) {
+            double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+            for (int b = 0; b < EB; b += 2) {
+              if (b < nb) a0 = __fma_rn(rv[b], xs[b * nc + c], a0);
+              if (b + 1 < nb) a1 = __fma_rn(rv[b + 1], xs[(b + 1) * nc + c], a1);
+            }
+            double* dst = W + (long long)S.lc[c0 + c] * ldw + r;
+            *dst -= a0 + a1;
+          }
+        }
       }
     }
   }
   if (rank == 0 && tid == 0) { jb.out[0] = k; jb.out[1] = stopped; jb.out[2] = accepted; }
 }
 
-size_t smem_for(int dmax) {
+size_t smem_for(int dmax, int nt) {
   const size_t dp = ((size_t)dmax + 3) & ~(size_t)3;
-  return sizeof(double) * (2 * dp + (NW + 4) * (size_t)NLMAX) + 2 * sizeof(int) * NLMAX;
+  return sizeof(double) * (2 * dp + (nt / 32 + 4) * (size_t)NLMAX) + 2 * sizeof(int) * NLMAX;
+}
+
+template <int NT>
+int group_capacity(int dmax) {
+  int dev = 0, sms = 0, per = 0;
+  const size_t sm = smem_for(dmax, NT);
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(k_qrcp<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qrcp<NT>, NT, sm) != cudaSuccess) return 0;
+  return sms * per;
+}
+
+template <int NT>
+cudaError_t launch(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int dmax, int* err, cudaStream_t st) {
+  const size_t sm = smem_for(dmax, NT);
+  cudaError_t e = cudaFuncSetAttribute(k_qrcp<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  if (!map_dev) {
+    k_qrcp<NT><<<nctas, NT, sm, st>>>(jobs_dev, nullptr, err, dmax);
+    return cudaGetLastError();
+  }
+  void* args[] = {(void*)&jobs_dev, (void*)&map_dev, (void*)&err, (void*)&dmax};
+  return cudaLaunchCooperativeKernel((const void*)k_qrcp<NT>, dim3(nctas), dim3(NT), args, sm, st);
 }
 
 }  // namespace
 
 int qrcp_cols_per_cta() { return NLMAX; }
 
-// Co-resident CTAs of k_qrcp on this device for sample width dmax.
-int qrcp_group_capacity(int dmax) {
-  int dev = 0, sms = 0, per = 0;
-  const size_t sm = smem_for(dmax);
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qrcp, NT, sm) != cudaSuccess) return 0;
-  return sms * per;
+// Co-resident CTAs of k_qrcp on this device for sample width dmax, in the
+// wide (256 threads) or narrow (128 threads) shape.
+int qrcp_group_capacity(int dmax, int wide) {
+  return wide ? group_capacity<NT_WIDE>(dmax) : group_capacity<NT_NARROW>(dmax);
 }
 
 // map == nullptr: one CTA per job (ordinary launch); otherwise map[cta] =
 // (job, rank) and the launch is cooperative.  dmax: largest d of the jobs.
-cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int dmax, int* err,
+cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int dmax, int wide, int* err,
                         cudaStream_t st) {
   if (nctas <= 0) return cudaSuccess;
-  const size_t sm = smem_for(dmax);
-  cudaError_t e = cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  if (!map_dev) {
-    k_qrcp<<<nctas, NT, sm, st>>>(jobs_dev, nullptr, err, dmax);
-    return cudaGetLastError();
-  }
-  void* args[] = {(void*)&jobs_dev, (void*)&map_dev, (void*)&err, (void*)&dmax};
-  return cudaLaunchCooperativeKernel((const void*)k_qrcp, dim3(nctas), dim3(NT), args, sm, st);
+  return wide ? launch<NT_WIDE>(jobs_dev, map_dev, nctas, dmax, err, st)
+              : launch<NT_NARROW>(jobs_dev, map_dev, nctas, dmax, err, st);
 }
 
 }  // namespace hss
