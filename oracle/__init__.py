@@ -17,9 +17,11 @@ hss      Algorithm 3 (adaptive compression) with Algorithm 2 (local samples,
          stopping_criteria) and the Doubling test (Algorithm 4).
 apply    expansion of the generators to a dense matrix (eq. nestedUV),
          matrix-vector product and the relative error of Table 3.
+operator a user sampling product for Toeplitz matrices through the FFT of
+         a circulant embedding (section 3.1, partially matrix-free).
 
 Every function is written in FP64 and follows the paper's order of steps;
 the readings taken where the paper is ambiguous are listed in the module
 docstrings (P-numbers refer to the same list in the design notes).
 """
-from . import tree, qrcp, hss, apply  # noqa: F401
+from . import tree, qrcp, hss, apply, operator  # noqa: F401

@@ -105,14 +105,20 @@ class Result:
 
 class _Sampler:
     """S^r = A R and S^c = A^T R for the new columns of R, through the
-    source's entries in row panels (a plain product, no structure used)."""
+    source's entries in row panels (a plain product, no structure used), or
+    through a user product(X, trans) -> A X / A^T X (section 3.1)."""
 
-    def __init__(self, src):
+    def __init__(self, src, product=None):
         self.src = src
         self.n = src.n
-        self.dense = src.to_dense() if (src.dense is not None or src.n <= 8192) else None
+        self.product = product
+        self.dense = (src.to_dense() if product is None and (src.dense is not None or src.n <= 8192)
+                      else None)
 
     def sample(self, Rnew, symmetric=False):
+        if self.product is not None:
+            Sr = self.product(Rnew, False)
+            return Sr, (Sr if symmetric else self.product(Rnew, True))
         if self.dense is not None:
             Sr = self.dense @ Rnew
             return Sr, (Sr if symmetric else self.dense.T @ Rnew)
@@ -134,16 +140,19 @@ class _Sampler:
         return self.src.entries(I, J)
 
 
-def compress(src, R: np.ndarray, opts: Options) -> Result:
+def compress(src, R: np.ndarray, opts: Options, product=None) -> Result:
     """HSSCompressAdaptive (Algorithm 3).  ``R`` is the caller's n x d_max
-    Gaussian matrix; the pass with d columns uses R[:, :d]."""
+    Gaussian matrix; the pass with d columns uses R[:, :d].  ``product``:
+    optional user sampling operator, product(X, trans) = A X or A^T X (the
+    partially matrix-free interface of section 3.1); the entries for the
+    generators and the leaf diagonal blocks still come from ``src``."""
     if opts.criterion not in ("new", "hmt"):
         raise ValueError(f"unknown criterion {opts.criterion!r}")
     if opts.criterion == "hmt" and (opts.strategy != "incrementing" or not opts.hmt_alpha > 1.0):
         raise ValueError("the HMT criterion is an Incrementing test with alpha > 1")
     n = src.n
     nodes = halving_tree(n, opts.leaf)
-    A = _Sampler(src)
+    A = _Sampler(src, product)
     d_max = min(opts.d_max, R.shape[1])
     d = min(opts.d0, d_max)
     Sr, Sc = A.sample(R[:, :d], opts.symmetric)

@@ -472,3 +472,37 @@ def test_known_rank_single_pass():
     for d, ok in ((20, False), (21, True)):
         res = compress(w.dense_source(A), R, Options(leaf=leaf, rtol=1e-10, atol=1e-14, d0=d, dd=8, d_max=d))
         assert res.converged == ok and res.n_adapt == 0 and res.d_final == d
+
+
+# --------------------------------------- user sampling operator (section 3.1)
+def test_toeplitz_fft_product_is_the_toeplitz_product():
+    """The circulant embedding gives T X exactly up to rounding: against the
+    dense Toeplitz matrix built from its definition, both orientations,
+    n odd and even."""
+    from oracle.operator import toeplitz_product
+    rng = np.random.default_rng(31)
+    for n in (1, 2, 7, 64, 301):
+        col, row = rng.standard_normal(n), rng.standard_normal(n)
+        row[0] = col[0]
+        T = np.array([[col[i - j] if i >= j else row[j - i] for j in range(n)] for i in range(n)])
+        X = rng.standard_normal((n, 5))
+        for trans in (False, True):
+            ref = (T.T if trans else T) @ X
+            got = toeplitz_product(col, row, X, trans)
+            assert np.max(np.abs(got - ref)) <= 1e-13 * (np.abs(T).max() * np.abs(X).sum(axis=0).max() + 1.0)
+
+
+def test_compress_with_user_product_matches_entries():
+    """Sampling through the user product instead of the entries changes only
+    the rounding of S = A R: the same adaptations, ranks and error."""
+    from oracle.operator import toeplitz_product
+    src = w.toeplitz_cos(1500)
+    col, row = src.col, src.row
+    R = w.gaussian_matrix(4, src.n, 0, 1024)
+    o = Options(leaf=100, rtol=1e-6, atol=1e-12, d0=32, dd=32, d_max=1024)
+    a = compress(src, R, o)
+    b = compress(src, R, o, product=lambda X, tr: toeplitz_product(col, row, X, tr))
+    assert a.converged and b.converged and a.d_final == b.d_final and a.n_adapt == b.n_adapt
+    assert a.ranks() == b.ranks()
+    A = src.to_dense()
+    assert abs(apply.rel_error(a, A) - apply.rel_error(b, A)) <= 1e-3 * apply.rel_error(a, A)
