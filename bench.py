@@ -407,7 +407,31 @@ CONFIG_WORKLOADS = {
     "c3": "laplace_sphere_n32768_incrementing_bf16x3",
     "c4": "batch64_toeplitz_gauss3_n2048_16384_doubling_tf32x2",
     "c5": "toeplitz_cos_n131072_incrementing_tf32x2",
+    "c5op": "toeplitz_cos_n131072_incrementing_fp64_fft_operator",
 }
+
+
+def _toeplitz_fft_operator(col, row):
+    """A user sampling operator (section 3.1): S = T R for a Toeplitz T
+    through the FFT of its circulant embedding of size 2n, on the library's
+    stream."""
+    import torch
+    n = col.numel()
+
+    def spectrum(c_, r_):
+        c = torch.zeros(2 * n, dtype=torch.float64, device=col.device)
+        c[:n] = c_
+        c[n + 1:] = r_[1:].flip(0)
+        return torch.fft.rfft(c)
+
+    F, FT = spectrum(col, row), spectrum(row, col)
+    torch.cuda.synchronize()
+
+    def fn(trans, R, S, stream):
+        Y = torch.zeros((2 * n, R.shape[1]), dtype=torch.float64, device=R.device)
+        Y[:n] = R
+        S.copy_(torch.fft.irfft((FT if trans else F)[:, None] * torch.fft.rfft(Y, dim=0), n=2 * n, dim=0)[:n])
+    return fn
 
 
 def _entries_block(src_kind, data, n, j0, w, dev):
@@ -459,7 +483,7 @@ def run_config(args):
         leaf, rtol, atol, strat, d0, dd, prec = 128, 1e-5, 1e-8, "doubling", 64, 64, "tf32x2"
     else:
         W = {"c1": wl.workload_toeplitz_1024, "c3": wl.workload_laplace_sphere,
-             "c5": wl.workload_toeplitz_cos}[c]()
+             "c5": wl.workload_toeplitz_cos, "c5op": wl.workload_toeplitz_cos}[c]()
         src = W.source
         if W.needs_rcb:
             src = src.permuted(hss.hss_rcb_order(src.points, W.leaf))
@@ -475,28 +499,32 @@ def run_config(args):
             edata = (src.kind, (X, src.p0))
         members.append((ds, src.n, edata))
         leaf, rtol, atol, strat, d0, dd, prec = W.leaf, W.rtol, W.atol, W.strategy, W.d0, W.dd, W.precision
+    op = None
+    if c == "c5op":   # FP64 sampling through the FFT operator; entries from the Toeplitz source
+        op = hss.make_operator(_toeplitz_fft_operator(edata[1][0], edata[1][1]))
+        prec = "fp64"
 
-    def opts(p, n):
-        return hss.make_opts(leaf, rtol, atol, d0, dd, min(n, 4096 if c != "c5" else 1024), STRAT[strat],
-                             PREC[p], 10, 0)
+    def opts(p, n, use_op=True):
+        return hss.make_opts(leaf, rtol, atol, d0, dd, min(n, 1024 if c in ("c5", "c5op") else 4096), STRAT[strat],
+                             PREC[p], 10, 0, op=op if use_op else None)
 
-    def compress_all(p):
+    def compress_all(p, use_op=True):
         with torch.cuda.stream(stream):
             if c == "c4":
                 return hss.hss_compress_batched([m[0] for m in members], [opts(p, m[1]) for m in members],
                                                 stream=stream)
-            return [hss.hss_compress(members[0][0], opts(p, members[0][1]), stream=stream)]
+            return [hss.hss_compress(members[0][0], opts(p, members[0][1], use_op), stream=stream)]
 
-    def timed(p, steps, warm):
+    def timed(p, steps, warm, use_op=True):
         for _ in range(warm):
-            del_ = compress_all(p)
+            del_ = compress_all(p, use_op)
             del del_
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stats = []
         e0.record(stream)
         for _ in range(steps):
-            Hs = compress_all(p)
+            Hs = compress_all(p, use_op)
             stats.append([h.stats() for h in Hs])
             del Hs
         e1.record(stream)
@@ -533,7 +561,8 @@ def run_config(args):
            "dtype": "f64" if prec == "fp64" else f"{prec} sampling, f64 QR/ID", "data": "synthetic",
            "gpu_launches": int(sum(s.launches for s in st)),
            "config": {"workload": CONFIG_WORKLOADS[c], "leaf": leaf, "rtol": rtol, "atol": atol,
-                      "strategy": strat, "d0": d0, "dd": dd, "precision": prec, "members": len(members)},
+                      "strategy": strat, "d0": d0, "dd": dd, "precision": prec, "members": len(members),
+                      "sampling": "user FFT operator" if op is not None else "entries"},
            "compress_s": ms / 1e3, "rel_error": err,
            "result": {"d_final": max(s.d_final for s in st), "n_adapt": max(s.n_adapt for s in st),
                       "max_rank": max(max(s.max_rank_r, s.max_rank_c) for s in st),
@@ -549,6 +578,16 @@ def run_config(args):
             del H
         torch.cuda.synchronize()
         out["sum_of_single_runs_s"] = time.perf_counter() - t0
+    if c == "c5op" and not args.no_compare:
+        # the entry form of the same configuration (TF32x2 sampling of A's entries)
+        ms_e, st_e = timed("tf32x2", max(1, args.steps), 1, use_op=False)
+        out["entry_form_tf32x2"] = {"compress_s": ms_e / 1e3,
+                                    "phases_ms": {"sample": sum(s.ms_sample for s in st_e),
+                                                  "id": sum(s.ms_id for s in st_e),
+                                                  "test": sum(s.ms_test for s in st_e),
+                                                  "merge_reduce": sum(s.ms_merge for s in st_e)},
+                                    "max_rank": max(max(s.max_rank_r, s.max_rank_c) for s in st_e)}
+        out["speedup_vs_entry_form"] = ms_e / ms
     if prec != "fp64" and not args.no_compare:
         ms64, st64 = timed("fp64", 1, 1)
         out["fp64_plain"] = {"compress_s": ms64 / 1e3,
@@ -789,7 +828,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="diagnostic override of the matrix order")
     ap.add_argument("--tol", type=float, default=0.0, help="rtol = atol of --config table4 (default 1e-12)")
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "table3", "table4"],
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5op", "table3", "table4"],
                     help="workload configuration (c2, the default, is the one the metric is quoted on)")
     args = ap.parse_args()
     if args.impl == "reference":

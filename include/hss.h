@@ -34,7 +34,8 @@ typedef enum {
                                  but holds no usable generators                */
   HSS_ERR_NONFINITE = 5,      /* NaN or Inf found in the random samples        */
   HSS_ERR_TIMEOUT = 6,        /* a bounded device wait expired                 */
-  HSS_ERR_UNSUPPORTED = 7     /* option combination not implemented            */
+  HSS_ERR_UNSUPPORTED = 7,    /* option combination not implemented            */
+  HSS_ERR_OPERATOR = 8        /* the user sampling operator returned nonzero   */
 } hss_status;
 
 /* Sample growth strategy (paper section 2.4): Doubling = Algorithm 4 with
@@ -93,6 +94,26 @@ typedef struct hss_source {
 /* Node states of Algorithm 3. */
 enum { HSS_UNTOUCHED = 0, HSS_PARTIALLY_COMPRESSED = 1, HSS_COMPRESSED = 2 };
 
+/* A user sampling product (section 3.1, the partially matrix-free
+ * interface: the construction needs only products with A and A^T and
+ * selected entries of A).  apply(ctx, trans, n, ncols, R, ldr, S, lds, stream)
+ * must enqueue on `stream` (a cudaStream_t) the product S = A R (trans = 0)
+ * or S = A^T R (trans = 1): R and S are device col-major n x ncols with
+ * leading dimensions ldr, lds >= n; R is only read, S only written, both
+ * owned by the library and valid until the stream reaches the work enqueued
+ * after the call returns.  It returns 0, or nonzero on failure (the
+ * compression then stops with HSS_ERR_OPERATOR).  The entries of A for the
+ * generators (D and B blocks, and the leaf diagonal blocks removed from the
+ * samples) still come from the hss_source, which must describe the same A.
+ * The callback runs on the host thread of the compression (a worker thread
+ * of hss_compress_batched), once per orientation and pass. */
+typedef int (*hss_apply_fn)(void* ctx, int trans, int n, int ncols, const double* R, long long ldr,
+                            double* S, long long lds, void* stream);
+typedef struct hss_operator {
+  hss_apply_fn apply;
+  void* ctx;             /* passed through unchanged                          */
+} hss_operator;
+
 typedef struct hss_opts {
   int leaf;              /* leaf size of the halving cluster tree (>= 1)     */
   int strategy;          /* HSS_DOUBLING or HSS_INCREMENTING                  */
@@ -115,6 +136,12 @@ typedef struct hss_opts {
   int criterion;         /* HSS_CRIT_NEW (0, default) or HSS_CRIT_HMT        */
   double hmt_alpha;      /* alpha > 1 of the HMT criterion (Lemma 4.1; the
                             paper's example takes 10); ignored with NEW       */
+  const hss_operator* op; /* host; NULL: the library samples A from the
+                            source's entries.  Otherwise every pass samples
+                            through op (precision must be HSS_PREC_FP64: the
+                            product's arithmetic is the operator's) and the
+                            library removes the leaf diagonal blocks
+                            D_tau R(I_tau) from its result (Algorithm 2)      */
 } hss_opts;
 
 typedef struct hss_stats {
@@ -126,7 +153,9 @@ typedef struct hss_stats {
   double ms_id;          /* QRCP / ID kernels                                 */
   double ms_test;        /* Incrementing projection + QR kernels              */
   double ms_merge;       /* extraction, merge, reduction and bookkeeping      */
-  double flop_sample;    /* algorithmic sampling flops, sum of 4 n^2 Delta d */
+  double flop_sample;    /* algorithmic sampling flops, sum of 4 n^2 Delta d
+                            (the dense product's count, also with a user
+                            operator, whose own work may be far less)       */
   double bytes_sample;   /* algorithmic sampling bytes: one read of A (dense
                             source) + R read + S^r, S^c written, summed      */
   long long launches;    /* kernels launched by the call                      */

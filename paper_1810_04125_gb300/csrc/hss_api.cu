@@ -192,6 +192,7 @@ struct hss_matrix_s {
   double* Sg_r = nullptr;  // n x dmax row-major: leaf samples
   double* Sg_c = nullptr;
   int* leaf_id = nullptr;
+  int* leaf_lo = nullptr;  // nleaves + 1 row bounds (with a user operator)
   int* iota = nullptr;
   int* d_flag = nullptr;   // device int scratch
   int* h_pinned = nullptr; // host pinned readback buffer
@@ -428,7 +429,24 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
   SrcDev s = make_src(H->src, H->leaf_id);
   const double* Rc = H->R + (long long)c0 * n;
   const int norient = H->sym ? 1 : 2;   // A^T R is A R for a symmetric A
-  if (H->o.precision == HSS_PREC_FP64) {
+  if (H->o.op) {
+    // the user's product A R (and A^T R), then the leaf diagonal blocks off
+    CK(H->timer.mark(PH_SAMPLE, st));
+    double* T = nullptr;
+    CK(cudaMallocAsync(&T, sizeof(double) * (size_t)n * w * norient, st));
+    for (int side = 0; side < norient; ++side) {
+      const int rc = H->o.op->apply(H->o.op->ctx, side, n, w, Rc, n, T + (size_t)side * n * w, n, (void*)st);
+      if (rc != 0) {
+        cudaFreeAsync(T, st);
+        return fail(HSS_ERR_OPERATOR, "user operator returned %d (trans = %d, columns %d..%d)", rc, side, c0, c1);
+      }
+    }
+    CK(launch_leaf_diag_sub(s, H->leaf_lo, n, w, Rc, n, T, n, H->Sg_r + c0, H->dmax, 0, st));
+    if (!H->sym) CK(launch_leaf_diag_sub(s, H->leaf_lo, n, w, Rc, n, T + (size_t)n * w, n, H->Sg_c + c0, H->dmax, 1, st));
+    H->launches += norient;
+    H->st.sample_launches += norient;
+    CK(cudaFreeAsync(T, st));
+  } else if (H->o.precision == HSS_PREC_FP64) {
     CK(H->timer.mark(PH_SAMPLE, st));
     CK(launch_sample_fp64(s, w, Rc, n, H->Sg_r + c0, H->sym ? nullptr : H->Sg_c + c0, H->dmax, st));
     H->launches += norient;
@@ -496,7 +514,8 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
   // (FP64: 8 B per entry; packed TF32x2: 8 B; packed BF16x3: 6 B), R read,
   // S written
   double abytes = 0.0;
-  if (H->src.kind == HSS_SRC_DENSE || (H->o.precision != HSS_PREC_FP64 && H->pack_decided == 1))
+  if (H->o.op) abytes = 0.0;   // the operator's own traffic is not the library's
+  else if (H->src.kind == HSS_SRC_DENSE || (H->o.precision != HSS_PREC_FP64 && H->pack_decided == 1))
     abytes = (H->o.precision == HSS_PREC_BF16X3 ? 6.0 : 8.0) * n * (double)n;
   H->st.bytes_sample += norient * (abytes + 2.0 * 8.0 * n * (double)w);
   CK(cudaMemsetAsync(H->d_flag, 0, sizeof(int), st));
@@ -1189,6 +1208,15 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
   if (!H->leaf_id || !H->iota || !H->d_flag || !H->Sg_r || !H->Sg_c || !H->R)
     return fail(HSS_ERR_NOMEM, "device allocation of %zu bytes for samples failed", 3 * nd * 8);
   CKS(upload(H, H->leaf_id, lid.data(), sizeof(int) * n, st));
+  if (o->op) {
+    std::vector<int> lb;
+    for (auto& t : H->nodes)
+      if (t.leaf) lb.push_back(t.lo);
+    lb.push_back(n);
+    H->leaf_lo = (int*)H->arena.alloc(sizeof(int) * lb.size());
+    if (!H->leaf_lo) return fail(HSS_ERR_NOMEM, "device allocation of the leaf bounds failed");
+    CKS(upload(H, H->leaf_lo, lb.data(), sizeof(int) * lb.size(), st));
+  }
   CKS(upload(H, H->iota, io.data(), sizeof(int) * n, st));
   CK(cudaMemsetAsync(H->d_flag, 0, 256, st));
 
@@ -1245,6 +1273,7 @@ const char* hss_status_str(hss_status s) {
     case HSS_ERR_NONFINITE: return "HSS_ERR_NONFINITE";
     case HSS_ERR_TIMEOUT: return "HSS_ERR_TIMEOUT";
     case HSS_ERR_UNSUPPORTED: return "HSS_ERR_UNSUPPORTED";
+    case HSS_ERR_OPERATOR: return "HSS_ERR_OPERATOR";
   }
   return "HSS_ERR_UNKNOWN";
 }
@@ -1265,6 +1294,8 @@ hss_status hss_compress(const hss_source* A, const hss_opts* o, void* stream, hs
     return fail(HSS_ERR_ARG, "unknown precision %d", o->precision);
   if (!(o->rtol >= 0.0) || !(o->atol >= 0.0)) return fail(HSS_ERR_ARG, "tolerances must be >= 0");
   if (o->oversample_p < 0) return fail(HSS_ERR_ARG, "oversample_p must be >= 0");
+  if (o->op && (!o->op->apply || o->precision != HSS_PREC_FP64))
+    return fail(HSS_ERR_ARG, "a user operator needs an apply function and HSS_PREC_FP64");
   if (o->criterion != HSS_CRIT_NEW && o->criterion != HSS_CRIT_HMT)
     return fail(HSS_ERR_ARG, "unknown criterion %d", o->criterion);
   if (o->criterion == HSS_CRIT_HMT) {

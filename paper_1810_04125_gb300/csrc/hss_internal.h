@@ -181,6 +181,14 @@ int qrcp_cols_per_cta();
 int qrcp_group_capacity(int d_max, int wide);
 cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, int wide, int* err,
                         cudaStream_t st);
+// With a user sampling operator: S(i, c0 + q) = T(i, q) - sum_{j in leaf(i)}
+// A(i, j) R(j, q) (trans = 0) or A(j, i) (trans = 1) for i < n, q < w: the
+// leaf diagonal blocks removed from the user's product T (col-major, ld ldt)
+// into the row-major samples S (ld lds, column offset applied by the caller).
+// leaf_lo: nleaves + 1 row bounds of the leaves; s.leaf_id gives each row's leaf.
+cudaError_t launch_leaf_diag_sub(const SrcDev& s, const int* leaf_lo, int n, int w, const double* R, long long ldr,
+                                 const double* T, long long ldt, double* S, long long lds, int trans,
+                                 cudaStream_t st);
 cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
 // The same test with the rows of each side split over a group of P CTAs
 // (map[cta] = (job, rank), cooperative launch); b_max: largest block, at

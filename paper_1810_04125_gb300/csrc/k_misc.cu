@@ -27,6 +27,38 @@ __global__ void k_extract(SrcDev src, const ExtractJob* __restrict__ jobs) {
   }
 }
 
+// With a user sampling operator the leaf diagonal blocks come off the
+// user's product (Algorithm 2 at a leaf: (A R)(I_tau) - D_tau R(I_tau)): a
+// CTA takes a 32 x 32 tile (rows i0.., columns q0..), evaluates its leaf
+// block products in FP64 from the source's entries and writes the tile
+// transposed into the row-major samples through shared memory.
+__global__ void __launch_bounds__(256) k_leaf_diag_sub(SrcDev s, const int* __restrict__ leaf_lo, int n, int w,
+                                                     const double* __restrict__ R, long long ldr,
+                                                     const double* __restrict__ T, long long ldt,
+                                                     double* __restrict__ S, long long lds, int trans) {
+  __shared__ double tile[32][33];
+  const int i0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int qq = ty; qq < 32; qq += 8) {
+    const int i = i0 + tx, q = q0 + qq;
+    double v = 0.0;
+    if (i < n && q < w) {
+      const int L = s.leaf_id[i];
+      const int lo = leaf_lo[L], hi = leaf_lo[L + 1];
+      const double* Rq = R + (long long)q * ldr;
+      double acc = 0.0;
+      for (int j = lo; j < hi; ++j) acc = __fma_rn(trans ? entry(s, j, i) : entry(s, i, j), Rq[j], acc);
+      v = T[(long long)q * ldt + i] - acc;
+    }
+    tile[qq][tx] = v;
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, q = q0 + tx;
+    if (i < n && q < w) S[(long long)i * lds + q] = tile[tx][ii];
+  }
+}
+
 __global__ void k_nonfinite(const double* __restrict__ S, long long lds, int n, int c0, int c1,
                             int* flag) {
   int w = c1 - c0;
@@ -73,6 +105,15 @@ cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int nj
   if (njobs <= 0) return cudaSuccess;
   int gx = max_tiles < 1 ? 1 : (max_tiles > 64 ? 64 : max_tiles);
   k_extract<<<dim3(gx, njobs), 256, 0, st>>>(src, jobs_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_diag_sub(const SrcDev& s, const int* leaf_lo, int n, int w, const double* R, long long ldr,
+                                 const double* T, long long ldt, double* S, long long lds, int trans,
+                                 cudaStream_t st) {
+  if (n <= 0 || w <= 0) return cudaSuccess;
+  dim3 grid((n + 31) / 32, (w + 31) / 32);
+  k_leaf_diag_sub<<<grid, 256, 0, st>>>(s, leaf_lo, n, w, R, ldr, T, ldt, S, lds, trans);
   return cudaGetLastError();
 }
 

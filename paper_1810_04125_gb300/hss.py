@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhss.so")
 
 HSS_OK, HSS_ERR_ARG, HSS_ERR_NOMEM, HSS_ERR_CUDA = 0, 1, 2, 3
 HSS_ERR_NOT_CONVERGED, HSS_ERR_NONFINITE, HSS_ERR_TIMEOUT, HSS_ERR_UNSUPPORTED = 4, 5, 6, 7
+HSS_ERR_OPERATOR = 8
 HSS_DOUBLING, HSS_INCREMENTING = 0, 1
 HSS_CRIT_NEW, HSS_CRIT_HMT = 0, 1
 HSS_PREC_FP64, HSS_PREC_TF32X2, HSS_PREC_BF16X3 = 0, 1, 2
@@ -34,12 +35,20 @@ class hss_source(C.Structure):
                 ("p0", C.c_double), ("p1", C.c_double)]
 
 
+APPLY_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p,
+                       C.c_longlong, C.c_void_p)
+
+
+class hss_operator(C.Structure):
+    _fields_ = [("apply", APPLY_FN), ("ctx", C.c_void_p)]
+
+
 class hss_opts(C.Structure):
     _fields_ = [("leaf", C.c_int), ("strategy", C.c_int), ("precision", C.c_int),
                 ("level_tol_scaling", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
                 ("d0", C.c_int), ("dd", C.c_int), ("d_max", C.c_int), ("oversample_p", C.c_int),
                 ("seed", C.c_ulonglong), ("R", C.c_void_p), ("symmetric", C.c_int),
-                ("criterion", C.c_int), ("hmt_alpha", C.c_double)]
+                ("criterion", C.c_int), ("hmt_alpha", C.c_double), ("op", C.POINTER(hss_operator))]
 
 
 class hss_stats(C.Structure):
@@ -132,11 +141,51 @@ def make_source(kind, n, a, b=None, ld=0, dim=0, p0=0.0, p1=0.0):
 
 
 def make_opts(leaf, rtol, atol, d0, dd, d_max, strategy, precision=HSS_PREC_FP64, p=10, seed=0,
-              R=None, level_tol_scaling=1, symmetric=0, criterion=0, hmt_alpha=10.0):
+              R=None, level_tol_scaling=1, symmetric=0, criterion=0, hmt_alpha=10.0, op=None):
     o = hss_opts(leaf, strategy, precision, level_tol_scaling, rtol, atol, d0, dd, d_max, p,
-                 seed, _ptr(R), int(symmetric), int(criterion), float(hmt_alpha))
-    o._keep = R
+                 seed, _ptr(R), int(symmetric), int(criterion), float(hmt_alpha),
+                 C.pointer(op) if op is not None else None)
+    o._keep = (R, op)
     return o
+
+
+def _device_matrix(ptr, rows, cols, ld):
+    """A column-major rows x cols view (leading dimension ld) of FP64 device
+    memory owned by the library."""
+    import torch
+
+    class _View:
+        __cuda_array_interface__ = {"shape": (rows, cols), "strides": (8, 8 * ld), "typestr": "<f8",
+                                    "data": (ptr, False), "version": 3}
+    return torch.as_tensor(_View(), device="cuda")
+
+
+last_operator_error = None
+
+
+def make_operator(fn):
+    """hss_operator around fn(trans, R, S, stream): R and S are n x ncols
+    column-major views of the library's buffers and stream the library's
+    stream (made current); fn enqueues S = A R (trans 0) or S = A^T R
+    (trans 1).  An exception becomes a nonzero status (HSS_ERR_OPERATOR);
+    it is kept in last_operator_error."""
+    import torch
+
+    def cb(ctx, trans, n, ncols, R, ldr, S, lds, stream):
+        global last_operator_error
+        try:
+            st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(st):
+                fn(trans, _device_matrix(R, n, ncols, ldr), _device_matrix(S, n, ncols, lds), st)
+            return 0
+        except Exception as e:   # the status carries the failure back through the C ABI
+            last_operator_error = e
+            return 1
+
+    c = APPLY_FN(cb)
+    op = hss_operator(c, None)
+    op._keep = (c, fn)
+    return op
 
 
 def hss_compress(source, opts, stream=None, allow_not_converged=False):

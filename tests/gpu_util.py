@@ -35,14 +35,44 @@ STRAT = {"incrementing": 1, "doubling": 0}
 PREC = {"fp64": 0, "tf32x2": 1, "bf16x3": 2}
 
 
-def gpu_compress(src, R, o, precision="fp64", pass_R=True, seed=0, allow_not_converged=False):
+def toeplitz_fft_operator(col, row):
+    """A user sampling operator for a Toeplitz matrix (device tensors col,
+    row): S = T R through the FFT of its circulant embedding of size 2n
+    (torch.fft on the library's stream), the GPU counterpart of
+    oracle.operator.toeplitz_product."""
+    import torch
+    n = col.numel()
+
+    def spectrum(c_, r_):
+        c = torch.zeros(2 * n, dtype=torch.float64, device=col.device)
+        c[:n] = c_
+        c[n + 1:] = r_[1:].flip(0)
+        return torch.fft.rfft(c)
+
+    F, FT = spectrum(col, row), spectrum(row, col)
+    torch.cuda.synchronize()
+    calls = []
+
+    def fn(trans, R, S, stream):
+        calls.append(trans)
+        Y = torch.zeros((2 * n, R.shape[1]), dtype=torch.float64, device=R.device)
+        Y[:n] = R
+        Z = torch.fft.irfft((FT if trans else F)[:, None] * torch.fft.rfft(Y, dim=0), n=2 * n, dim=0)
+        S.copy_(Z[:n])
+
+    fn.calls = calls
+    return fn
+
+
+def gpu_compress(src, R, o, precision="fp64", pass_R=True, seed=0, allow_not_converged=False, op=None):
     from paper_1810_04125_gb300 import hss
     s = device_source(src)
     Rd = col_major(R) if pass_R else None
     opts = hss.make_opts(o.leaf, o.rtol, o.atol, o.d0, o.dd, o.d_max, STRAT[o.strategy],
                          PREC[precision], o.p, seed, Rd, int(o.level_tol_scaling),
                          int(getattr(o, "symmetric", False)),
-                         1 if getattr(o, "criterion", "new") == "hmt" else 0, getattr(o, "hmt_alpha", 10.0))
+                         1 if getattr(o, "criterion", "new") == "hmt" else 0, getattr(o, "hmt_alpha", 10.0),
+                         op=op)
     return hss.hss_compress(s, opts, allow_not_converged=allow_not_converged)
 
 

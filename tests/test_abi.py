@@ -71,6 +71,14 @@ def test_argument_validation_without_gpu(hss):
     assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
     bad = hss.make_opts(64, 1e-6, 1e-12, 64, 32, 256, 7)
     assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
+    # a user operator needs an apply function and the FP64 form
+    op = hss.make_operator(lambda *a: None)
+    bad = hss.make_opts(64, 1e-6, 1e-12, 64, 32, 256, hss.HSS_INCREMENTING, hss.HSS_PREC_TF32X2, op=op)
+    assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
+    null_op = hss.hss_operator()
+    bad = hss.make_opts(64, 1e-6, 1e-12, 64, 32, 256, hss.HSS_INCREMENTING, op=null_op)
+    assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
+    assert L.hss_status_str(hss.HSS_ERR_OPERATOR) == b"HSS_ERR_OPERATOR"
     # the HMT criterion: Incrementing only, alpha > 1 and finite, known criterion codes
     for kw in (dict(strategy=hss.HSS_DOUBLING, criterion=hss.HSS_CRIT_HMT),
                dict(strategy=hss.HSS_INCREMENTING, criterion=hss.HSS_CRIT_HMT, hmt_alpha=1.0),

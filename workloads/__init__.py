@@ -181,6 +181,15 @@ def toeplitz_cos(n: int, w: float = 0.3) -> Source:
     return toeplitz_source(np.cos(w * k) / (1.0 + k), name=f"toeplitz_cos{w}k/(1+k)_n{n}")
 
 
+def toeplitz_nonsymmetric(n: int, p: float = 1.5, w: float = 0.3) -> Source:
+    """A_ij = (1+(i-j))^-p below the diagonal, cos(w (j-i))/(1+(j-i)) above
+    (both 1 on it): a Toeplitz matrix with A^T != A."""
+    k = np.arange(n, dtype=np.float64)
+    col = np.ascontiguousarray((1.0 + k) ** (-p))
+    row = np.ascontiguousarray(np.cos(w * k) / (1.0 + k))
+    return Source(SRC_TOEPLITZ, n, col=col, row=row, name=f"toeplitz_nonsym_n{n}")
+
+
 def uniform_points(n: int, dim: int, seed: int = 0) -> np.ndarray:
     return np.random.default_rng(seed).random((n, dim))
 
