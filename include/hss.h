@@ -245,6 +245,12 @@ hss_status hss_export_node(hss_matrix H, int node, int* Jr, int* Jc, int* Pr, in
                            double* B12, double* B21);
 
 void hss_free(hss_matrix H);
+
+/* hss_free (and a failed compression) keep the handle's device memory in
+ * 256 MB chunks, up to 32 GB per device, for the next compression on the same
+ * device (after waiting for the device, as cudaFree would).  This call
+ * returns the chunks cached for the current device with cudaFree. */
+hss_status hss_release_cached(void);
 const char* hss_status_str(hss_status s);
 const char* hss_last_error(void);
 

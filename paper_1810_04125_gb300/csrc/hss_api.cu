@@ -53,19 +53,47 @@ hss_status fail(hss_status s, const char* fmt, ...) {
   } while (0)
 
 // Chunked bump allocator for memory that lives as long as the handle.
+// Arena chunks of the standard size outlive their handle in a per-process
+// cache (up to kCacheCap bytes per device) and serve the next compression:
+// cudaMalloc and cudaFree of 256 MB chunks cost milliseconds each, and a
+// compression takes several.  A handle's release waits for the device first,
+// as cudaFree would, so no work still reading a chunk sees it reused.
+constexpr size_t kChunk = size_t(256) << 20;
+constexpr size_t kCacheCap = size_t(32) << 30;
+struct ChunkCache {
+  std::mutex mu;
+  std::vector<std::pair<int, void*>> free;   // (device, chunk of kChunk bytes)
+  size_t held[64] = {0};
+};
+ChunkCache& chunk_cache() {
+  static ChunkCache c;
+  return c;
+}
+
 struct Arena {
-  std::vector<void*> chunks;
+  std::vector<std::pair<void*, size_t>> chunks;
   char* cur = nullptr;
   size_t left = 0;
-  size_t chunk = size_t(256) << 20;
   void* alloc(size_t bytes) {
     bytes = (bytes + 255) & ~size_t(255);
     if (bytes == 0) bytes = 256;
     if (bytes > left) {
-      size_t sz = std::max(chunk, bytes);
+      const size_t sz = std::max(kChunk, bytes);
       void* p = nullptr;
-      if (cudaMalloc(&p, sz) != cudaSuccess) return nullptr;
-      chunks.push_back(p);
+      int dev = 0;
+      if (sz == kChunk && cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        ChunkCache& c = chunk_cache();
+        std::lock_guard<std::mutex> lock(c.mu);
+        for (size_t i = 0; i < c.free.size(); ++i)
+          if (c.free[i].first == dev) {
+            p = c.free[i].second;
+            c.free.erase(c.free.begin() + i);
+            c.held[dev] -= kChunk;
+            break;
+          }
+      }
+      if (!p && cudaMalloc(&p, sz) != cudaSuccess) return nullptr;
+      chunks.push_back({p, sz});
       cur = (char*)p;
       left = sz;
     }
@@ -75,7 +103,21 @@ struct Arena {
     return r;
   }
   void release() {
-    for (void* p : chunks) cudaFree(p);
+    int dev = -1;
+    if (!chunks.empty() && (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)) dev = -1;
+    ChunkCache& c = chunk_cache();
+    for (auto& ch : chunks) {
+      bool kept = false;
+      if (ch.second == kChunk && dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lock(c.mu);
+        if (c.held[dev] + kChunk <= kCacheCap) {
+          c.free.push_back({dev, ch.first});
+          c.held[dev] += kChunk;
+          kept = true;
+        }
+      }
+      if (!kept) cudaFree(ch.first);
+    }
     chunks.clear();
     cur = nullptr;
     left = 0;
@@ -1423,6 +1465,23 @@ hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int c
 }
 
 void hss_free(hss_matrix H) { delete H; }
+
+hss_status hss_release_cached(void) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  ChunkCache& c = chunk_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  for (size_t i = 0; i < c.free.size();) {
+    if (c.free[i].first == dev) {
+      cudaFree(c.free[i].second);
+      c.free.erase(c.free.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+  if (dev >= 0 && dev < 64) c.held[dev] = 0;
+  return HSS_OK;
+}
 
 hss_status hss_get_stats(hss_matrix H, hss_stats* s) {
   if (!H || !s) return fail(HSS_ERR_ARG, "NULL argument");

@@ -25,7 +25,7 @@ HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE = 0, 1, 2, 3
 HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
 
 EXPORTS = ["hss_compress", "hss_compress_restart", "hss_compress_batched", "hss_matvec", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
-           "hss_free", "hss_status_str", "hss_last_error", "hss_rcb_order",
+           "hss_free", "hss_release_cached", "hss_status_str", "hss_last_error", "hss_rcb_order",
            "hss_random_normal", "hss_sample_offdiag", "hss_sample_offdiag_noalloc"]
 
 
@@ -89,6 +89,7 @@ def lib():
         L.hss_get_node.argtypes = [vp, i, C.POINTER(hss_node_info)]
         L.hss_export_node.argtypes = [vp, i] + [vp] * 11
         L.hss_free.argtypes = [vp]
+        L.hss_release_cached.argtypes = []
         L.hss_free.restype = None
         L.hss_status_str.argtypes = [i]
         L.hss_status_str.restype = C.c_char_p
@@ -207,6 +208,11 @@ def hss_compress_restart(source, opts, stream=None, allow_not_converged=False):
         return HSSMatrix(h.value, converged=False), k.value
     _check(st)
     return HSSMatrix(h.value), k.value
+
+
+def hss_release_cached():
+    """Return the device memory cached from freed handles (current device)."""
+    _check(lib().hss_release_cached())
 
 
 def hss_to_dense(H, out, stream=None):

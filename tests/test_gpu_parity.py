@@ -248,3 +248,22 @@ def test_device_generated_R(hss, torch):
     assert not gu.compare_with_oracle(H, ref, o, 1024)
     A = src.to_dense()
     assert gu.rel_err(A, gu.gpu_dense(H, 1024)) <= 1.1 * apply.rel_error(ref, A) + 1e-15
+
+
+def test_freed_memory_is_reused(hss, torch):
+    """A freed handle's device chunks serve the next compression (the chunk
+    cache), and hss_release_cached returns them: the results of the second
+    and third compressions equal the first's."""
+    src = w.toeplitz_inverse_distance(1024)
+    o = Options(leaf=64, rtol=1e-6, atol=1e-12, d0=32, dd=32, d_max=512)
+    R = w.gaussian_matrix(7, src.n, 0, 512)
+    H = gu.gpu_compress(src, R, o)
+    ranks, dense = H.ranks(), gu.gpu_dense(H, src.n)
+    del H
+    H = gu.gpu_compress(src, R, o)
+    assert H.ranks() == ranks
+    np.testing.assert_allclose(gu.gpu_dense(H, src.n), dense, rtol=0, atol=1e-13)
+    del H
+    hss.hss_release_cached()
+    H = gu.gpu_compress(src, R, o)
+    assert H.ranks() == ranks
