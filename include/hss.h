@@ -246,6 +246,25 @@ hss_status hss_export_node(hss_matrix H, int node, int* Jr, int* Jc, int* Pr, in
 
 void hss_free(hss_matrix H);
 
+/* Launch-shape parameters, process-wide.  The defaults are the built-in
+ * heuristics; the package's tuning script times the candidates on the GPU at
+ * hand and records the fastest in a table that the Python binding applies
+ * when it loads the library.  They change launch shapes only: any choice
+ * gives the same method, with rounding differences only. */
+typedef struct hss_tuning {
+  int qrcp_wide_max_sides;    /* QRCP launches over at most this many node
+                                 sides use 256 threads and two CTAs per SM,
+                                 larger ones 128 threads and four (default 8) */
+  int sample_waves_packed;    /* K split of the packed tensor-core sampling
+                                 kernel: CTAs for this many waves of the SMs
+                                 (default 4; at least 64 k-tiles per CTA)      */
+  int sample_waves_generated; /* the same for the generated-entry kernel
+                                 (default 2)                                   */
+} hss_tuning;
+hss_status hss_set_tuning(const hss_tuning* t);   /* NULL: back to the defaults;
+                                                     HSS_ERR_ARG on values < 1  */
+hss_status hss_get_tuning(hss_tuning* t);
+
 /* hss_free (and a failed compression) keep the handle's device memory in
  * 256 MB chunks, up to 32 GB per device, for the next compression on the same
  * device (after waiting for the device, as cudaFree would).  This call

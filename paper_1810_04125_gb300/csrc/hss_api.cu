@@ -647,6 +647,15 @@ void reduce_jobs(hss_matrix_s* H, Node& t, int cs, int d, std::vector<GemmJob>& 
   }
 }
 
+std::mutex& tuning_mutex() {
+  static std::mutex m;
+  return m;
+}
+hss_tuning& tuning_ref() {
+  static hss_tuning t{8, 4, 2};
+  return t;
+}
+
 std::mutex& coop_launch_mutex() {
   static std::mutex m;
   return m;
@@ -667,7 +676,7 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   // CTAs; one cooperative launch per batch (plain launch when every P is 1).
   // few node sides (the top levels): the wide shape, whose groups have half
   // as many CTAs; otherwise the narrow one
-  const int wide = nj <= 8 ? 1 : 0;
+  const int wide = (int)nj <= tuning_get().qrcp_wide_max_sides ? 1 : 0;
   if (H->qrcp_cap_d != d || H->qrcp_cap_w != wide) {
     H->qrcp_cap = qrcp_group_capacity(d, wide);
     H->qrcp_cap_d = d;
@@ -1466,6 +1475,22 @@ hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int c
 
 void hss_free(hss_matrix H) { delete H; }
 
+hss_status hss_set_tuning(const hss_tuning* t) {
+  const hss_tuning def{8, 4, 2};
+  if (t && (t->qrcp_wide_max_sides < 1 || t->sample_waves_packed < 1 || t->sample_waves_generated < 1))
+    return fail(HSS_ERR_ARG, "tuning values must be >= 1");
+  std::lock_guard<std::mutex> lock(tuning_mutex());
+  tuning_ref() = t ? *t : def;
+  return HSS_OK;
+}
+
+hss_status hss_get_tuning(hss_tuning* t) {
+  if (!t) return fail(HSS_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lock(tuning_mutex());
+  *t = tuning_ref();
+  return HSS_OK;
+}
+
 hss_status hss_release_cached(void) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -1867,3 +1892,10 @@ extern "C" hss_status hss_sample_offdiag_noalloc(const hss_source* A, int leaf, 
   CK(launch_sample_fp64(s, ncols, R, ldr, Sr, Sc, lds, st));
   return HSS_OK;
 }
+
+namespace hss {
+hss_tuning tuning_get() {
+  std::lock_guard<std::mutex> lock(tuning_mutex());
+  return tuning_ref();
+}
+}  // namespace hss

@@ -176,6 +176,8 @@ cudaError_t launch_gemm_tc(const GemmJob* jobs_dev, const GemmTile* tiles_dev, i
 // the job's group) and the launch is cooperative.  d_max: largest d.  A CTA
 // owns at most qrcp_cols_per_cta() columns (m / P); W is col-major with
 // ldw a multiple of 4; nrm holds m doubles.
+// The process-wide launch-shape parameters (hss_set_tuning).
+hss_tuning tuning_get();
 // wide: 256 threads and two CTAs per SM (else 128 threads, four per SM).
 int qrcp_cols_per_cta();
 int qrcp_group_capacity(int d_max, int wide);

@@ -509,13 +509,13 @@ cudaError_t launch_pack_r(const double* R, long long ldr, int n, int ncols, int 
 int sample_tc_packed_ksplit(int n, int ncols, int precision) {
   const int N = tile_n(ncols);
   const int gx = (n + BM - 1) / BM, gy = (ncols + N - 1) / N, nkt = (n + bk_of(precision) - 1) / bk_of(precision);
-  return ksplit_for(gx, gy, nkt, 4);
+  return ksplit_for(gx, gy, nkt, tuning_get().sample_waves_packed);
 }
 
 int sample_tc_ksplit(int n, int ncols, int precision) {
   const int N = tile_n(ncols);
   const int gx = (n + BM - 1) / BM, gy = (ncols + N - 1) / N, nkt = (n + bk_of(precision) - 1) / bk_of(precision);
-  return ksplit_for(gx, gy, nkt, 2);
+  return ksplit_for(gx, gy, nkt, tuning_get().sample_waves_generated);
 }
 
 cudaError_t launch_sample_tc_packed(const void* A, const void* Rp, int n, int ncols, int precision,

@@ -14,6 +14,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhss.so")
+# launch-shape table written by tune.py for this GPU family (applied on load)
+TUNING_PATH = os.path.join(_HERE, "tuning_sm103.json")
 
 HSS_OK, HSS_ERR_ARG, HSS_ERR_NOMEM, HSS_ERR_CUDA = 0, 1, 2, 3
 HSS_ERR_NOT_CONVERGED, HSS_ERR_NONFINITE, HSS_ERR_TIMEOUT, HSS_ERR_UNSUPPORTED = 4, 5, 6, 7
@@ -25,7 +27,8 @@ HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE = 0, 1, 2, 3
 HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
 
 EXPORTS = ["hss_compress", "hss_compress_restart", "hss_compress_batched", "hss_matvec", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
-           "hss_free", "hss_release_cached", "hss_status_str", "hss_last_error", "hss_rcb_order",
+           "hss_free", "hss_release_cached", "hss_set_tuning", "hss_get_tuning", "hss_status_str",
+           "hss_last_error", "hss_rcb_order",
            "hss_random_normal", "hss_sample_offdiag", "hss_sample_offdiag_noalloc"]
 
 
@@ -62,6 +65,11 @@ class hss_stats(C.Structure):
                 ("bytes_d2h", C.c_longlong), ("flop_id", C.c_double)]
 
 
+class hss_tuning(C.Structure):
+    _fields_ = [("qrcp_wide_max_sides", C.c_int), ("sample_waves_packed", C.c_int),
+                ("sample_waves_generated", C.c_int)]
+
+
 class hss_node_info(C.Structure):
     _fields_ = [(f, C.c_int) for f in ("lo", "size", "level", "parent", "child0", "child1",
                                        "state", "mr", "mc", "kr", "kc")]
@@ -90,6 +98,8 @@ def lib():
         L.hss_export_node.argtypes = [vp, i] + [vp] * 11
         L.hss_free.argtypes = [vp]
         L.hss_release_cached.argtypes = []
+        L.hss_set_tuning.argtypes = [C.POINTER(hss_tuning)]
+        L.hss_get_tuning.argtypes = [C.POINTER(hss_tuning)]
         L.hss_free.restype = None
         L.hss_status_str.argtypes = [i]
         L.hss_status_str.restype = C.c_char_p
@@ -104,7 +114,36 @@ def lib():
             if f not in ("hss_free", "hss_status_str", "hss_last_error"):
                 getattr(L, f).restype = C.c_int
         _lib = L
+        _apply_tuning_table()
     return _lib
+
+
+def _apply_tuning_table():
+    """Apply the launch-shape table of tune.py when one is present."""
+    if not os.path.exists(TUNING_PATH):
+        return
+    import json
+    t = json.load(open(TUNING_PATH))
+    set_tuning(**{k: int(t[k]) for k in ("qrcp_wide_max_sides", "sample_waves_packed",
+                                         "sample_waves_generated") if k in t})
+
+
+def get_tuning() -> dict:
+    t = hss_tuning()
+    _check(lib().hss_get_tuning(C.byref(t)))
+    return {f: getattr(t, f) for f, _ in hss_tuning._fields_}
+
+
+def set_tuning(**kw):
+    """hss_set_tuning with the given fields changed (no arguments: defaults)."""
+    if not kw:
+        _check(lib().hss_set_tuning(None))
+        return
+    t = hss_tuning()
+    _check(lib().hss_get_tuning(C.byref(t)))
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    _check(lib().hss_set_tuning(C.byref(t)))
 
 
 class HSSError(RuntimeError):

@@ -79,6 +79,16 @@ def test_argument_validation_without_gpu(hss):
     bad = hss.make_opts(64, 1e-6, 1e-12, 64, 32, 256, hss.HSS_INCREMENTING, op=null_op)
     assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
     assert L.hss_status_str(hss.HSS_ERR_OPERATOR) == b"HSS_ERR_OPERATOR"
+    # launch-shape parameters: validated, settable, restorable
+    saved = hss.get_tuning()
+    bad_t = hss.hss_tuning(0, 4, 2)
+    assert L.hss_set_tuning(C.byref(bad_t)) == hss.HSS_ERR_ARG
+    hss.set_tuning()
+    assert hss.get_tuning() == {"qrcp_wide_max_sides": 8, "sample_waves_packed": 4, "sample_waves_generated": 2}
+    hss.set_tuning(qrcp_wide_max_sides=16)
+    assert hss.get_tuning()["qrcp_wide_max_sides"] == 16
+    hss.set_tuning(**saved)
+    assert hss.get_tuning() == saved
     # the HMT criterion: Incrementing only, alpha > 1 and finite, known criterion codes
     for kw in (dict(strategy=hss.HSS_DOUBLING, criterion=hss.HSS_CRIT_HMT),
                dict(strategy=hss.HSS_INCREMENTING, criterion=hss.HSS_CRIT_HMT, hmt_alpha=1.0),
