@@ -22,7 +22,7 @@ error ||A - H||_F / ||A||_F.
   python bench.py --config table4      # known-rank vs Incrementing vs hard restart
 
 Multi-GPU (torchrun): every rank compresses its own replica of the matrix
-(the path does not shard in this build), value = all ranks' flops / the
+(the path is not sharded), value = all ranks' flops / the
 slowest rank's time.
 """
 from __future__ import annotations
