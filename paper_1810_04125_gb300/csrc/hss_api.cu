@@ -740,7 +740,7 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     need += Scratch::rnd(sizeof(double) * (size_t)ldw * mj[i]) + Scratch::rnd(sizeof(double) * mj[i]) +
             Scratch::rnd(sizeof(double) * (size_t)std::max(1, std::min(mj[i], d))) +
             Scratch::rnd(sizeof(unsigned)) + Scratch::rnd(sizeof(double) * 4 * P[i]) +
-            Scratch::rnd(sizeof(double) * 2 * P[i]);
+            Scratch::rnd(sizeof(double) * 2 * P[i]) + Scratch::rnd(sizeof(double) * 8);
   }
   need += Scratch::rnd(sizeof(int) * 3 * nj);
   CK(H->scratch.ensure(need, st));
@@ -772,6 +772,7 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     j.bar = bars + i;
     j.redv = (double*)H->scratch.take(sizeof(double) * 4 * P[i]);   // 2 P (key, index) pairs
     j.redt = (double*)H->scratch.take(sizeof(double) * 2 * P[i]);
+    j.xfer = (double*)H->scratch.take(sizeof(double) * 8);
     wbuf.push_back(j.W);
     jobs.push_back(j);
   }

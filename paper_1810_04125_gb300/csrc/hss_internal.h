@@ -101,6 +101,8 @@ struct QrcpJob {
   double* redv;         // 2 P partial maxima as 16-byte (norm bits, column) pairs,
                         // two steps in flight, 16-byte aligned
   double* redt;         // 2 P pending-update coefficients of the candidates
+  double* xfer;         // 2 x 4: the column moved between CTAs at a step (id, tw,
+                        // norm^2, orig), two steps in flight
 };
 
 // One Incrementing block test on one side of a node (Algorithm 5):

@@ -142,11 +142,13 @@ __device__ __forceinline__ void rank_thresholds(const QrcpJob& jb, int d, int j,
 
 // shared-memory carve-up (dynamic part): two reflectors of d_max entries,
 // then per own live column: partial dots of the warps, tw, top, norm^2,
-// norm^2 at the last exact computation, column index
+// norm^2 at the last exact computation, column index, position in the
+// group's live list
 struct Carve {
   double *v0, *v1, *part, *tw, *top, *nrm, *orig;
   int* lc;
   int* rc;   // columns whose norm is recomputed this step
+  int* gp;
 };
 
 template <int NW>
@@ -162,6 +164,7 @@ __device__ __forceinline__ Carve carve(double* base, int dmax) {
   c.orig = c.nrm + NLMAX;
   c.lc = (int*)(c.orig + NLMAX);
   c.rc = c.lc + NLMAX;
+  c.gp = c.rc + NLMAX;
   return c;
 }
 
@@ -184,7 +187,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
   __shared__ double sh[NW];
   __shared__ unsigned long long shk[NW];
   __shared__ int shi[NW], shp[NW];
-  __shared__ int s_ok, s_p, s_pos, s_stop, s_nl, s_nrc;
+  __shared__ int s_ok, s_p, s_pos, s_stop, s_nl, s_nrc, s_tl;
+  __shared__ double s_xf[4];   // the column moved to the pivot's owner: id, tw, norm^2, orig
   __shared__ double s_twp, s_tau, s_scal, s_r11, s_uj;
   __shared__ double s_th[2][2];   // stop thresholds (eps_a, eps_r |R_11|) by step parity
   unsigned epoch = 0;
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
     if (tid == 0) atomicCAS(err, 0, 9);
     return;
   }
-  for (int t = tid; t < nl; t += NT) S.lc[t] = rank + P * t;
+  for (int t = tid; t < nl; t += NT) S.lc[t] = S.gp[t] = rank + P * t;
   for (int r = tid; r < 2 * ((dmax + 3) & ~3); r += NT) S.v0[r] = 0.0;
   __syncthreads();
   for (int t = warp; t < nl; t += NW) {
@@ -264,10 +268,28 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
     }
     // argmax on integer keys: the bit patterns of non-negative doubles are
     // ordered like their values (no FP64 compares on the critical path)
+    // the column at the last position of the group's live list goes to the
+    // pivot's owner after this step (the live list stays balanced, one
+    // position in P per CTA): its owner publishes its state beside the
+    // argmax partials
+    const int lastpos = m - 1 - j;
+    if (tid == 0) s_tl = -1;
+    __syncthreads();
     unsigned long long bk = 0ull;
     int bi = 0x7fffffff, bp = -1;
-    for (int t = tid; t < nl; t += NT)
+    for (int t = tid; t < nl; t += NT) {
       key_max(bk, bi, bp, (unsigned long long)__double_as_longlong(S.nrm[t]), S.lc[t], t);
+      if (S.gp[t] == lastpos) {
+        s_tl = t;
+        if (P > 1) {
+          double* xf = jb.xfer + (j & 1) * 4;
+          __stcg(xf, (double)S.lc[t]);
+          __stcg(xf + 1, S.tw[t]);
+          __stcg(xf + 2, S.nrm[t]);
+          __stcg(xf + 3, S.orig[t]);
+        }
+      }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
@@ -295,6 +317,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
     }
     // ---- (b) the pivot of step j over the group
     if (!group_barrier(jb.bar, P, epoch, err, &s_ok)) return;
+    if (P > 1 && warp == 1 && lane < 4) s_xf[lane] = __ldcg(jb.xfer + (j & 1) * 4 + lane);
     if (P > 1 && warp == 0) {
       unsigned long long kk = 0ull;
       int i = 0x7fffffff, q2 = -1;
@@ -367,21 +390,37 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
           if (!stop) {
             s_tau = (beta - x0) / beta;
             s_uj = x0 - beta;
-            const int pos = s_pos;
+            // live list update: the pivot leaves; the column at the last
+            // position takes the pivot's position, and so moves to the
+            // pivot's owner (possibly from another CTA of the group)
+            const int pos = s_pos, tl = s_tl;
+            int nn = nl;
+            auto move = [&](int to, int from) {
+              S.lc[to] = S.lc[from]; S.tw[to] = S.tw[from]; S.nrm[to] = S.nrm[from];
+              S.orig[to] = S.orig[from]; S.gp[to] = S.gp[from];
+            };
             if (pos >= 0) {
-              // the own pivot column leaves the live list
               __stcg(diag + j, beta);
               __stcg(jb.piv + j, p);
               liveg[p] = -1.0;
-              const int last = nl - 1;
-              S.lc[pos] = S.lc[last];
-              S.tw[pos] = S.tw[last];
-              S.nrm[pos] = S.nrm[last];
-              S.orig[pos] = S.orig[last];
-              s_nl = last;
-            } else {
-              s_nl = nl;
+              const int gpos = S.gp[pos];
+              if (gpos == lastpos) {            // the pivot was the last column
+                move(pos, nn - 1);
+                nn -= 1;
+              } else if (tl >= 0) {             // the last column is this CTA's too
+                move(pos, tl);
+                S.gp[pos] = gpos;
+                if (tl != nn - 1) move(tl, nn - 1);
+                nn -= 1;
+              } else {                          // it comes from another CTA
+                S.lc[pos] = (int)s_xf[0]; S.tw[pos] = s_xf[1]; S.nrm[pos] = s_xf[2]; S.orig[pos] = s_xf[3];
+                S.gp[pos] = gpos;
+              }
+            } else if (tl >= 0) {               // this CTA's last column went to the pivot's owner
+              if (tl != nn - 1) move(tl, nn - 1);
+              nn -= 1;
             }
+            s_nl = nn;
           }
         }
       }
@@ -601,7 +640,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
 
 size_t smem_for(int dmax, int nt) {
   const size_t dp = ((size_t)dmax + 3) & ~(size_t)3;
-  return sizeof(double) * (2 * dp + (nt / 32 + 4) * (size_t)NLMAX) + 2 * sizeof(int) * NLMAX;
+  return sizeof(double) * (2 * dp + (nt / 32 + 4) * (size_t)NLMAX) + 3 * sizeof(int) * NLMAX;
 }
 
 template <int NT>
