@@ -1037,9 +1037,13 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         flag0 = (int*)H->scratch.take(sizeof(int) * 2 * ij.size());
         for (size_t i = 0; i < ij.size(); ++i) { ij[i].res = res0 + 4 * i; ij[i].flag = flag0 + 2 * i; }
         CKS(run_gemms(H, g1, st, "test-copy"));
-        for (int rep = 0; rep < 2; ++rep) {   // (I - Q Q^T)^2
-          CKS(run_gemms(H, g2, st, "test-QtS"));
-          CKS(run_gemms(H, g3, st, "test-S-QT"));
+        // (I - Q Q^T)^2; in the mixed forms both products take the tensor
+        // cores with the three-term split of the merges (error below 2^-32
+        // of |Q||S| per product, under the samples' own noise); the norms,
+        // the QR and every decision stay FP64
+        for (int rep = 0; rep < 2; ++rep) {
+          CKS(run_gemms(H, g2, st, "test-QtS", true));
+          CKS(run_gemms(H, g3, st, "test-S-QT", true));
         }
         // the rows of each side over a group of CTAs (one cooperative launch
         // per batch of sides that fits the co-resident slots); blocks wider
