@@ -320,14 +320,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
     if (P > 1 && warp == 1 && lane < 4) s_xf[lane] = __ldcg(jb.xfer + (j & 1) * 4 + lane);
     if (P > 1 && warp == 0) {
       unsigned long long kk = 0ull;
-      int i = 0x7fffffff, q2 = -1;
+      int i = 0x7fffffff;
       double tw2 = 0.0;
       const int pb = (j & 1) * P;
       for (int q = lane; q < P; q += 32) {
         const ulonglong2 e = __ldcg((const ulonglong2*)jb.redv + pb + q);
         const double t2 = __ldcg(jb.redt + pb + q);
         const int i2 = (int)(unsigned)e.y;
-        if (e.x > kk || (e.x == kk && i2 < i)) { kk = e.x; i = i2; q2 = q; tw2 = t2; }
+        if (e.x > kk || (e.x == kk && i2 < i)) { kk = e.x; i = i2; tw2 = t2; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -336,7 +336,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
         const double t2 = __shfl_xor_sync(0xffffffffu, tw2, o);
         if (k2 > kk || (k2 == kk && i2 < i)) { kk = k2; i = i2; tw2 = t2; }
       }
-      (void)q2;
       if (lane == 0) {
         if (s_p != i) s_pos = -1;   // the pivot is another CTA's column
         s_p = i;
