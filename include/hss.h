@@ -265,6 +265,20 @@ hss_status hss_set_tuning(const hss_tuning* t);   /* NULL: back to the defaults;
                                                      HSS_ERR_ARG on values < 1  */
 hss_status hss_get_tuning(hss_tuning* t);
 
+/* Checkpoint of a compressed handle (no counterpart in the paper, which
+ * keeps its compression in memory; its warm restart of Algorithm 3 is
+ * in-process).  hss_save writes to the host file `path` the tree, node
+ * states and ranks, statistics and every generator (D, U and V as pivots and
+ * X, skeleton indices, B12, B21) in a plain binary format (8-byte magic
+ * "HSSGEN01", native byte order); the handle must hold usable generators
+ * (HSS_ERR_ARG otherwise).  hss_load reads such a file into a new handle on
+ * the current device, serving hss_matvec, hss_to_dense, hss_get_node,
+ * hss_export_node and hss_get_stats like the original; it cannot resume a
+ * compression (the samples are not saved).  HSS_ERR_ARG on a file that is
+ * not a checkpoint or is truncated; *out is NULL then. */
+hss_status hss_save(hss_matrix H, const char* path);
+hss_status hss_load(const char* path, hss_matrix* out);
+
 /* hss_free (and a failed compression) keep the handle's device memory in
  * 256 MB chunks, up to 32 GB per device, for the next compression on the same
  * device (after waiting for the device, as cudaFree would).  This call

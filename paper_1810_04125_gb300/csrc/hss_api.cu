@@ -1317,6 +1317,38 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
 }  // namespace
 
 // ======================================================================= ABI
+// ------------------------------------------------ checkpoint of generators
+namespace {
+constexpr char kMagic[8] = {'H', 'S', 'S', 'G', 'E', 'N', '0', '1'};
+
+bool put(FILE* f, const void* p, size_t bytes) { return bytes == 0 || fwrite(p, 1, bytes, f) == bytes; }
+bool get(FILE* f, void* p, size_t bytes) { return bytes == 0 || fread(p, 1, bytes, f) == bytes; }
+
+// one device array: its element count (-1 when absent), then the elements
+template <class T>
+bool put_array(FILE* f, const T* dev, long long count) {
+  const long long c = dev ? count : -1;
+  if (!put(f, &c, sizeof c)) return false;
+  if (c <= 0) return true;
+  std::vector<T> h((size_t)c);
+  if (cudaMemcpy(h.data(), dev, sizeof(T) * (size_t)c, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  return put(f, h.data(), sizeof(T) * (size_t)c);
+}
+
+template <class T>
+bool get_array(FILE* f, Arena& arena, T** dev, long long max_count) {
+  long long c = 0;
+  if (!get(f, &c, sizeof c) || c > max_count) return false;
+  if (c < 0) { *dev = nullptr; return true; }
+  *dev = (T*)arena.alloc(sizeof(T) * (size_t)std::max<long long>(c, 1));
+  if (!*dev) return false;
+  if (c == 0) return true;
+  std::vector<T> h((size_t)c);
+  if (!get(f, h.data(), sizeof(T) * (size_t)c)) return false;
+  return cudaMemcpy(*dev, h.data(), sizeof(T) * (size_t)c, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+}  // namespace
+
 extern "C" {
 
 const char* hss_status_str(hss_status s) {
@@ -1510,6 +1542,107 @@ hss_status hss_release_cached(void) {
     }
   }
   if (dev >= 0 && dev < 64) c.held[dev] = 0;
+  return HSS_OK;
+}
+
+
+hss_status hss_save(hss_matrix H, const char* path) {
+  if (!H || !path) return fail(HSS_ERR_ARG, "NULL argument");
+  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators (not converged)");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(HSS_ERR_ARG, "cannot open %s for writing", path);
+  const int hdr[8] = {H->n, (int)H->nodes.size(), H->max_level, H->usable ? 1 : 0, H->converged, H->d_final,
+                      H->n_adapt, H->o.leaf};
+  const long long sst = (long long)sizeof(hss_stats);
+  bool ok = put(f, kMagic, sizeof kMagic) && put(f, hdr, sizeof hdr) && put(f, &sst, sizeof sst) &&
+            put(f, &H->st, sizeof(hss_stats));
+  for (size_t i = 0; ok && i < H->nodes.size(); ++i) {
+    const Node& t = H->nodes[i];
+    const int rec[12] = {t.lo, t.size, t.level, t.parent, t.ch[0], t.ch[1], t.leaf ? 1 : 0, t.state,
+                         t.r.m, t.r.k, t.c.m, t.c.k};
+    ok = put(f, rec, sizeof rec);
+    for (const Side* sd : {&t.r, &t.c}) {
+      ok = ok && put_array(f, i ? sd->piv : (int*)nullptr, sd->m) &&
+           put_array(f, i ? sd->X : (double*)nullptr, (long long)sd->k * (sd->m - sd->k)) &&
+           put_array(f, i ? sd->I : (int*)nullptr, sd->k);
+    }
+    long long nb12 = 0, nb21 = 0;
+    if (!t.leaf) {
+      const Node& a = H->nodes[t.ch[0]];
+      const Node& b = H->nodes[t.ch[1]];
+      nb12 = (long long)a.r.k * b.c.k;
+      nb21 = (long long)b.r.k * a.c.k;
+    }
+    ok = ok && put_array(f, t.leaf ? t.D : (double*)nullptr, (long long)t.size * t.size) &&
+         put_array(f, t.leaf ? (double*)nullptr : t.B12, nb12) &&
+         put_array(f, t.leaf ? (double*)nullptr : t.B21, nb21);
+  }
+  ok = (fclose(f) == 0) && ok;
+  return ok ? HSS_OK : fail(HSS_ERR_CUDA, "writing %s failed", path);
+}
+
+hss_status hss_load(const char* path, hss_matrix* out) {
+  if (!path || !out) return fail(HSS_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(HSS_ERR_ARG, "cannot open %s", path);
+  hss_matrix_s* H = new (std::nothrow) hss_matrix_s();
+  if (!H) {
+    fclose(f);
+    return fail(HSS_ERR_NOMEM, "host allocation failed");
+  }
+  char magic[8];
+  int hdr[8];
+  long long sst = 0;
+  bool ok = get(f, magic, sizeof magic) && memcmp(magic, kMagic, sizeof kMagic) == 0 && get(f, hdr, sizeof hdr) &&
+            get(f, &sst, sizeof sst) && sst == (long long)sizeof(hss_stats) && get(f, &H->st, sizeof(hss_stats));
+  const int n = ok ? hdr[0] : 0, nn = ok ? hdr[1] : 0;
+  ok = ok && n > 0 && nn > 0 && nn <= 2 * n && hdr[2] >= 0 && hdr[2] < 64 && hdr[3] == 1;
+  if (ok) {
+    cudaGetDevice(&H->device);
+    H->n = n;
+    H->max_level = hdr[2];
+    H->usable = true;
+    H->converged = hdr[4];
+    H->d_final = hdr[5];
+    H->n_adapt = hdr[6];
+    H->o.leaf = hdr[7];
+    H->nodes.resize(nn);
+    H->by_level.assign(H->max_level + 1, {});
+  }
+  for (int i = 0; ok && i < nn; ++i) {
+    Node& t = H->nodes[i];
+    int rec[12];
+    ok = get(f, rec, sizeof rec);
+    if (!ok) break;
+    t.lo = rec[0]; t.size = rec[1]; t.level = rec[2]; t.parent = rec[3]; t.ch[0] = rec[4]; t.ch[1] = rec[5];
+    t.leaf = rec[6] != 0; t.state = rec[7];
+    t.r.m = rec[8]; t.r.k = rec[9]; t.c.m = rec[10]; t.c.k = rec[11];
+    ok = t.lo >= 0 && t.size > 0 && t.lo + t.size <= n && t.level >= 0 && t.level <= H->max_level &&
+         (t.leaf || (t.ch[0] > i && t.ch[0] < nn && t.ch[1] > i && t.ch[1] < nn)) && t.r.k >= 0 &&
+         t.r.k <= t.r.m && t.c.k >= 0 && t.c.k <= t.c.m && t.r.m <= n && t.c.m <= n;
+    for (Side* sd : {&t.r, &t.c}) {
+      ok = ok && get_array(f, H->arena, &sd->piv, sd->m) &&
+           get_array(f, H->arena, &sd->X, (long long)sd->k * (sd->m - sd->k)) &&
+           get_array(f, H->arena, &sd->I, sd->k);
+    }
+    ok = ok && get_array(f, H->arena, &t.D, (long long)t.size * t.size) &&
+         get_array(f, H->arena, &t.B12, (long long)n * n) && get_array(f, H->arena, &t.B21, (long long)n * n);
+    if (ok) H->by_level[t.level].push_back(i);
+  }
+  // every generator the products read must be there
+  for (int i = 0; ok && i < nn; ++i) {
+    const Node& t = H->nodes[i];
+    if (t.leaf && !t.D) ok = false;
+    if (!t.leaf && (!t.B12 || !t.B21)) ok = false;
+    if (i > 0 && (!t.r.piv || !t.c.piv || !t.r.X || !t.c.X)) ok = false;
+  }
+  fclose(f);
+  if (!ok) {
+    delete H;
+    return fail(HSS_ERR_ARG, "%s is not a readable HSS generator checkpoint", path);
+  }
+  *out = H;
   return HSS_OK;
 }
 

@@ -26,7 +26,7 @@ HSS_PREC_FP64, HSS_PREC_TF32X2, HSS_PREC_BF16X3 = 0, 1, 2
 HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE = 0, 1, 2, 3
 HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
 
-EXPORTS = ["hss_compress", "hss_compress_restart", "hss_compress_batched", "hss_matvec", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
+EXPORTS = ["hss_compress", "hss_compress_restart", "hss_compress_batched", "hss_save", "hss_load", "hss_matvec", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
            "hss_free", "hss_release_cached", "hss_set_tuning", "hss_get_tuning", "hss_status_str",
            "hss_last_error", "hss_rcb_order",
            "hss_random_normal", "hss_sample_offdiag", "hss_sample_offdiag_noalloc"]
@@ -98,6 +98,8 @@ def lib():
         L.hss_export_node.argtypes = [vp, i] + [vp] * 11
         L.hss_free.argtypes = [vp]
         L.hss_release_cached.argtypes = []
+        L.hss_save.argtypes = [vp, C.c_char_p]
+        L.hss_load.argtypes = [C.c_char_p, C.POINTER(vp)]
         L.hss_set_tuning.argtypes = [C.POINTER(hss_tuning)]
         L.hss_get_tuning.argtypes = [C.POINTER(hss_tuning)]
         L.hss_free.restype = None
@@ -247,6 +249,18 @@ def hss_compress_restart(source, opts, stream=None, allow_not_converged=False):
         return HSSMatrix(h.value, converged=False), k.value
     _check(st)
     return HSSMatrix(h.value), k.value
+
+
+def hss_save(H, path):
+    """Write H's generators to the file `path` (a checkpoint)."""
+    _check(lib().hss_save(H.handle, os.fsencode(path)))
+
+
+def hss_load(path):
+    """A new handle on the current device from a checkpoint file."""
+    h = C.c_void_p()
+    _check(lib().hss_load(os.fsencode(path), C.byref(h)))
+    return HSSMatrix(h.value)
 
 
 def hss_release_cached():

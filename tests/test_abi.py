@@ -79,6 +79,18 @@ def test_argument_validation_without_gpu(hss):
     bad = hss.make_opts(64, 1e-6, 1e-12, 64, 32, 256, hss.HSS_INCREMENTING, op=null_op)
     assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG
     assert L.hss_status_str(hss.HSS_ERR_OPERATOR) == b"HSS_ERR_OPERATOR"
+    # checkpoints: arguments and files checked on the host
+    assert L.hss_save(None, b"/nonexistent/x") == hss.HSS_ERR_ARG
+    hh = C.c_void_p(123)
+    assert L.hss_load(b"/nonexistent/dir/file", C.byref(hh)) == hss.HSS_ERR_ARG and not hh.value
+    import tempfile
+    with tempfile.NamedTemporaryFile(suffix=".hss", delete=False) as tf:
+        tf.write(b"not a checkpoint at all")
+    try:
+        hh = C.c_void_p(123)
+        assert L.hss_load(tf.name.encode(), C.byref(hh)) == hss.HSS_ERR_ARG and not hh.value
+    finally:
+        os.unlink(tf.name)
     # launch-shape parameters: validated, settable, restorable
     saved = hss.get_tuning()
     bad_t = hss.hss_tuning(0, 4, 2)

@@ -267,3 +267,30 @@ def test_freed_memory_is_reused(hss, torch):
     hss.hss_release_cached()
     H = gu.gpu_compress(src, R, o)
     assert H.ranks() == ranks
+
+
+def test_checkpoint_round_trip(hss, torch, tmp_path):
+    """hss_save / hss_load: the loaded handle has the same tree, ranks,
+    statistics and generators, and its products equal the original's."""
+    for o, src in ((Options(leaf=64, rtol=1e-6, atol=1e-12, d0=32, dd=32, d_max=512),
+                    w.toeplitz_inverse_distance(1024)),
+                   (Options(leaf=64, rtol=1e-6, atol=1e-12, d0=32, dd=32, d_max=512, symmetric=True),
+                    w.toeplitz_power(1000, 1.5))):
+        n = src.n
+        H = gu.gpu_compress(src, w.gaussian_matrix(7, n, 0, 512), o)
+        path = str(tmp_path / "h.hss")
+        hss.hss_save(H, path)
+        H2 = hss.hss_load(path)
+        assert H2.ranks() == H.ranks()
+        s1, s2 = H.stats(), H2.stats()
+        assert (s1.d_final, s1.n_adapt, s1.converged) == (s2.d_final, s2.n_adapt, s2.converged)
+        for i in range(H.stats().n_nodes):
+            e1, e2 = H.export_node(i), H2.export_node(i)
+            for k in e1:
+                if k == "info":
+                    continue
+                if e1[k] is None:
+                    assert e2[k] is None
+                else:
+                    np.testing.assert_array_equal(e1[k], e2[k])
+        np.testing.assert_allclose(gu.gpu_dense(H2, n), gu.gpu_dense(H, n), rtol=0, atol=1e-15)
