@@ -19,6 +19,8 @@
 
 #include "hss_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <mutex>
 #include <thread>
@@ -188,10 +190,18 @@ struct Node {
   double* B21 = nullptr; // kr(nu2) x kc(nu1) col-major, ld max(kr(nu2),1)
 };
 
+// Phase boundaries: CUDA events on the stream (the per-phase times of the
+// statistics) and one NVTX range per phase on the calling host thread (the
+// phases on a profiler's timeline; no cost without a tool attached).
 struct PhaseTimer {
   std::vector<cudaEvent_t> ev;
   std::vector<int> ph;
+  bool range_open = false;
   cudaError_t mark(int phase, cudaStream_t st) {
+    static const char* const names[] = {"hss sample", "hss id", "hss test", "hss merge", "hss other", "hss rng"};
+    if (range_open) nvtxRangePop();
+    nvtxRangePushA(phase >= 0 && phase < 6 ? names[phase] : "hss");
+    range_open = true;
     cudaEvent_t e;
     cudaError_t r = cudaEventCreate(&e);
     if (r != cudaSuccess) return r;
@@ -209,6 +219,10 @@ struct PhaseTimer {
         out[nph - 1] += ms;
       }
     }
+  }
+  void close_range() {
+    if (range_open) nvtxRangePop();
+    range_open = false;
   }
   void clear() {
     for (auto e : ev) cudaEventDestroy(e);
@@ -1396,6 +1410,7 @@ hss_status hss_compress(const hss_source* A, const hss_opts* o, void* stream, hs
   hss_matrix_s* H = new (std::nothrow) hss_matrix_s();
   if (!H) return fail(HSS_ERR_NOMEM, "host allocation failed");
   hss_status s = compress_impl(A, o, st, H);
+  H->timer.close_range();
   if (s != HSS_OK) {
     cudaStreamSynchronize(st);
     delete H;
