@@ -45,11 +45,6 @@ Readings (see the design notes for the full list):
      column side a copy of the row side — S^c = S^r, the same ID (J^c = J^r,
      V = U), R^c = R^r and B21 = B12^T — so only the row side is sampled,
      tested and factored, and the column side takes its results.
- P23 hard restart (section 4.3.2, Table 4): attempts with d = d0, 2 d0,
-     4 d0, ... (the last clipped to d_max), each Algorithm 3 with no growth
-     (d_max = d) on the first d columns of R and nothing carried over; the
-     strategy's own test is the failure check; the first converged attempt
-     is the result.  The known-rank mode is one attempt with d0 = d_max.
  P22 HMT criterion option (Lemma 4.1, eq. HMT_IQQH): Incrementing with the
      test of each block S_k replaced by  alpha sqrt(2/pi) max_i
      |((I - Q Q^T)^2 S_k)(:, i)|_2 <= eps_a  on the node's local sample
@@ -57,6 +52,15 @@ Readings (see the design notes for the full list):
      orthonormal basis joins Q, as in Algorithm 5.  The criterion has no
      relative form, so rtol is ignored and the final RRQR keeps the pivots
      with |R_jj| > eps_a.
+ P23 hard restart (section 4.3.2, Table 4): attempts with d = d0, 2 d0,
+     4 d0, ... (the last clipped to d_max), each Algorithm 3 with no growth
+     (d_max = d) on the first d columns of R and nothing carried over; the
+     strategy's own test is the failure check; the first converged attempt
+     is the result.  The known-rank mode is one attempt with d0 = d_max.
+ P24 user sampling operator (section 3.1, partially matrix-free): with
+     ``product`` the samples A R and A^T R come from the caller's product;
+     the leaf diagonal blocks D R(I) are still removed from the source's
+     entries (Algorithm 2), which also give every generator.
 """
 from __future__ import annotations
 
