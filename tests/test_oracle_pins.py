@@ -506,3 +506,213 @@ def test_compress_with_user_product_matches_entries():
     assert a.ranks() == b.ranks()
     A = src.to_dense()
     assert abs(apply.rel_error(a, A) - apply.rel_error(b, A)) <= 1e-3 * apply.rel_error(a, A)
+
+
+# ------------------------------- Doubling acceptance in closed form (Alg. 4)
+def doubling_side_accepts(m: int, r: int, d: int, p: int):
+    """Whether RRQR_HMT (eq. RRQRHMTstop) accepts a local sample of m rows
+    and exact rank r <= m drawn with d Gaussian vectors, and the rank it
+    keeps, worked out from the rule rather than run: the sample has rank
+    min(r, d), so in exact arithmetic the first vanishing pivot is the
+    1-based index r + 1, which exists when r < min(d, m); the scaled stop can
+    fire there only when the oversampling d - (r + 1) - 1 is positive (the
+    factor is infinite otherwise, and also at every later index).  A stop at
+    rank r is accepted when r <= d - p (Algorithm 4); without a stop the
+    factorisation selects min(d, m) rows and is accepted only when that is
+    every row (P9)."""
+    if r < min(d, m) and d - (r + 1) - 1 > 0:
+        return r <= d - p, r
+    k = min(d, m)
+    return k == m, k
+
+
+def doubling_closed_form(n, leaf, ranks, d0, p, d_max):
+    """(converged, d_final, n_adapt) of Algorithm 3 with Doubling on the
+    synthetic HSS matrix of the given per-level ranks: passes at d0, 2 d0,
+    ... (the last clipped to d_max); in a pass the levels are swept from the
+    leaves up, a node is tried once both children are COMPRESSED, and its
+    sample has m rows = its leaf size, or the sum of its children's kept
+    ranks."""
+    nodes = tree.halving_tree(n, leaf)
+    state, kept = {}, {}
+    d, n_adapt = min(d0, d_max), 0
+    while True:
+        for t in sorted(nodes[1:], key=lambda t: -t.level):
+            if state.get(t.idx) or (t.children and not all(state.get(c) for c in t.children)):
+                continue
+            m = t.size if not t.children else sum(kept[c] for c in t.children)
+            ok, k = doubling_side_accepts(m, ranks[t.level], d, p)
+            if ok:
+                state[t.idx], kept[t.idx] = True, k
+        if all(state.get(c) for c in nodes[0].children):
+            return True, d, n_adapt
+        if d >= d_max:
+            return False, d, n_adapt
+        d += min(d, d_max - d)
+        n_adapt += 1
+
+
+def test_doubling_side_rule_by_hand():
+    """A few values of the side rule checked by hand: a leaf of 64 rows and
+    rank 8 stops at rank 8 from d = 11 on (8 + 3) and needs d >= 18 with
+    p = 10; a full-rank side (r = m) is accepted as soon as d >= m; with
+    r < m <= r + 2 the window d in {r + 1, r + 2} selects every row."""
+    assert doubling_side_accepts(64, 8, 10, 0) == (False, 10)
+    assert doubling_side_accepts(64, 8, 11, 0) == (True, 8)
+    assert doubling_side_accepts(64, 8, 17, 10) == (False, 8)
+    assert doubling_side_accepts(64, 8, 18, 10) == (True, 8)
+    assert doubling_side_accepts(16, 16, 15, 10) == (False, 15)
+    assert doubling_side_accepts(16, 16, 16, 10) == (True, 16)
+    assert doubling_side_accepts(16, 15, 16, 10) == (True, 16)
+    assert doubling_side_accepts(16, 15, 18, 10) == (False, 15)
+    assert doubling_side_accepts(16, 15, 25, 10) == (True, 15)
+
+
+# (ranks per level, d0, p): sequences that land between r + 3 and r + p at
+# the level-1 sides (rank 20: d = 24, 26, 28 accept with p = 0, not with
+# p = 10), exactly at k = d - p (d = 30), below the HMT window (d = 22 = r + 2
+# with 32 rows: no stop, not every row), a full-rank level (level 3: 16 rows,
+# rank 16, accepted only by selecting every row) and the all-rows window
+# (level 3: 16 rows, rank 15, d = 16)
+DOUBLING_PINS = [({4: 8, 3: 12, 2: 16, 1: 20}, d0, p)
+                 for d0 in (5, 7, 8, 11, 12, 13, 15, 16) for p in (0, 10)]
+DOUBLING_PINS += [({4: 8, 3: 16, 2: 20, 1: 24}, d0, p) for d0 in (8, 12, 15, 16) for p in (0, 10)]
+DOUBLING_PINS += [({4: 8, 3: 15, 2: 20, 1: 24}, d0, p) for d0 in (8, 16) for p in (0, 3)]
+
+
+@pytest.mark.parametrize("ranks,d0,p", DOUBLING_PINS)
+def test_doubling_acceptance_closed_form(ranks, d0, p):
+    """Doubling on a matrix of exact HSS ranks: the passes, the final d and
+    the ranks kept follow from the acceptance rule k <= d - p / all rows
+    selected (Algorithm 4, eq. RRQRHMTstop, P6, P9) in closed form."""
+    n, leaf = 1024, 64
+    A = w.synthetic_hss(n, leaf, ranks, seed=3)
+    R = w.gaussian_matrix(5, n, 0, 128)
+    want = doubling_closed_form(n, leaf, ranks, d0, p, 128)
+    res = compress(w.dense_source(A), R, Options(leaf=leaf, rtol=1e-10, atol=1e-14, d0=d0, dd=d0,
+                                                 d_max=128, strategy="doubling", p=p))
+    assert (res.converged, res.d_final, res.n_adapt) == want
+    assert apply.rel_error(res, A) < 1e-12
+
+
+def test_doubling_closed_form_distinguishes_p():
+    """The pins above are not vacuous: p = 0 and p = 10, and k <= d - p
+    against k < d - p, give different passes on them."""
+    r = {4: 8, 3: 12, 2: 16, 1: 20}
+    assert doubling_closed_form(1024, 64, r, 12, 0, 128)[1:] == (24, 1)
+    assert doubling_closed_form(1024, 64, r, 12, 10, 128)[1:] == (48, 2)
+    assert doubling_closed_form(1024, 64, r, 15, 10, 128)[1:] == (30, 1)   # 20 <= 30 - 10
+    assert doubling_closed_form(1024, 64, {4: 8, 3: 16, 2: 20, 1: 24}, 8, 10, 128)[1:] == (64, 3)
+
+
+# ---------------------------------------- the RRQR_HMT factor by hand (P6)
+def _orthogonal_columns(d, norms, seed):
+    """d x m matrix with mutually orthogonal columns of the given norms (in
+    a shuffled order): its QRCP takes the columns by decreasing norm and has
+    |R_jj| equal to the sorted norms."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((d, len(norms))))
+    perm = rng.permutation(len(norms))
+    return (Q * np.asarray(norms)[perm])
+
+
+# d = 64 sample columns, Hankel block 100 x 900: f(k) = 1 + 4 sqrt(64) /
+# (64 - k - 1) sqrt(min(100, 900)) = 1 + 320 / (63 - k), so with
+# eps |R_11| = 1e-2 the thresholds of the 1-based pivots k = 2 .. 5 are
+# 1e-2 / (1 + 320/61) = 1.60105e-3, 1e-2 / (1 + 320/60) = 1.57895e-3,
+# 1e-2 / (1 + 320/59) = 1.55673e-3, 1e-2 / (1 + 320/58) = 1.53439e-3.
+# Pivots 2-4 sit 0.2 % above their thresholds and pivot 5 0.2 % below, so
+# the rule stops at k = 5 (rank 4).  Each plausible slip moves the stop: a 2
+# for the 4, d - k for d - k - 1 (or a 0-based k), a missing "1 +", or an
+# unscaled relative threshold stop at k = 2; d for sqrt(d), max for min, or
+# min(m, n) unsquare-rooted run past k = 5 to the tiny sixth pivot.
+HMT_NORMS = [1.0, 1.60425e-3, 1.58211e-3, 1.55984e-3, 1.53132e-3, 1e-6, 5e-7, 2e-7]
+
+
+@pytest.mark.parametrize("tol", ["relative", "absolute"])
+def test_hmt_stop_index_by_hand(tol):
+    W = _orthogonal_columns(64, HMT_NORMS, seed=17)
+    er, ea = (1e-2, 0.0) if tol == "relative" else (0.0, 1e-2)
+    piv, R, k, stopped = qrcp.qrcp(W, qrcp.hmt_rule(er, ea, 64, 100, 900))
+    assert stopped and k == 4
+    np.testing.assert_allclose(np.abs(np.diag(R)), HMT_NORMS[:4], rtol=1e-12)
+    # unscaled (the plain rule of the ID) the same tolerance stops at the
+    # second pivot, 1.6e-3 <= 1e-2
+    _, _, k_plain, st_plain = qrcp.qrcp(W, qrcp.plain_rule(er, ea))
+    assert st_plain and k_plain == 1
+    # with m and n swapped the factor is the same (min of the two)
+    assert qrcp.qrcp(W, qrcp.hmt_rule(er, ea, 64, 900, 100))[2] == 4
+
+
+# ----------------------- Incrementing's absolute and relative tests (eq. stopping_criteria)
+def _block_outside(Q, norms, seed, inside=None):
+    """m x b block S = Q G + Z with Z's columns orthogonal to span(Q) and to
+    each other, of the given norms; Q G (optional, scale ``inside``) lies in
+    span(Q), so (I - Q Q^T)^2 S = Z exactly up to rounding."""
+    rng = np.random.default_rng(seed)
+    m, q = Q.shape
+    b = len(norms)
+    Y = rng.standard_normal((m, b))
+    if q:
+        Y -= Q @ (Q.T @ Y)
+    Z, _ = np.linalg.qr(Y)
+    Z = Z * np.asarray(norms)
+    G = rng.standard_normal((q, b)) * (inside or 0.0)
+    return Q @ G + Z
+
+
+def _basis(m, q, seed):
+    return np.linalg.qr(np.random.default_rng(seed).standard_normal((m, q)))[0] if q else np.zeros((m, 0))
+
+
+@pytest.mark.parametrize("q", [0, 6])
+def test_incrementing_absolute_norm_test(q):
+    """|S^|_F / sqrt(b) < eps_a (P7).  The projected block has b = 8
+    orthogonal columns of norm 2, so |S^|_F / sqrt(b) = 2 and min |diag R| = 2:
+    atol just above 2 is sufficient, just below is not (a /b instead of
+    /sqrt(b) would make 0.707 < 1.98 sufficient).  The norm test comes
+    before the QR of S^ (Algorithm 5), so when it decides no |R_11| is
+    recorded for the side; if only the diagonal test fired, it would be."""
+    Q = _basis(40, q, 3)
+    S = _block_outside(Q, [2.0] * 8, seed=4, inside=5.0)
+    st = dict(Q=Q.copy(), rho=None)
+    assert hss.incrementing_block_test(S, st, 0.0, 2.02)
+    assert st["rho"] is None and st["Q"].shape[1] == q
+    st = dict(Q=Q.copy(), rho=None)
+    assert not hss.incrementing_block_test(S, st, 0.0, 1.98)
+    assert st["Q"].shape[1] == q + 8 and abs(st["rho"] - 2.0) < 1e-12
+
+
+@pytest.mark.parametrize("q", [0, 6])
+def test_incrementing_absolute_diagonal_test(q):
+    """min |diag R^| < eps_a alone decides: columns of norms 1, ..., 1, 1e-3
+    give |S^|_F / sqrt(8) = 0.935 but min |diag R| = 1e-3, and |R_11| = 1 is
+    recorded before the decision."""
+    Q = _basis(40, q, 5)
+    norms = [1.0] * 7 + [1e-3]
+    S = _block_outside(Q, norms, seed=6, inside=3.0)
+    for ea, want in ((0.5, True), (1.001e-3, True), (0.999e-3, False)):
+        st = dict(Q=Q.copy(), rho=None)
+        assert hss.incrementing_block_test(S, st, 0.0, ea) == want, ea
+        assert abs(st["rho"] - 1.0) < 1e-12
+
+
+def test_incrementing_relative_tests():
+    """|S^|_F < eps_r |S_k|_F and min |diag R^| < eps_r rho (rho = |R_11| of
+    the side's first block, P8), each deciding alone."""
+    m, q = 40, 6
+    Q = _basis(m, q, 7)
+    # |S^|_F = 0.1 * sqrt(8); |S_k|_F^2 = |Q G|_F^2 + 0.08 (Q G large)
+    S = _block_outside(Q, [0.1] * 8, seed=8, inside=10.0)
+    ratio = math.sqrt(0.08) / np.linalg.norm(S)
+    st = dict(Q=Q.copy(), rho=None)
+    assert hss.incrementing_block_test(S, st, 1.01 * ratio, 0.0) and st["rho"] is None
+    # just below: the norm test fails; the diagonal test (min 0.1 against
+    # eps_r rho with rho = 0.1 set by this block) fails too
+    st = dict(Q=Q.copy(), rho=None)
+    assert not hss.incrementing_block_test(S, st, 0.99 * ratio, 0.0)
+    # diagonal relative test against an earlier block's rho
+    S2 = _block_outside(_basis(m, 0, 9), [1.0] * 7 + [0.05], seed=10)
+    for rho, want in ((10.0, True), (4.0, False)):
+        st = dict(Q=np.zeros((m, 0)), rho=rho)
+        assert hss.incrementing_block_test(S2, st, 0.0051, 0.0) == want, rho
