@@ -35,7 +35,8 @@ typedef enum {
   HSS_ERR_NONFINITE = 5,      /* NaN or Inf found in the random samples        */
   HSS_ERR_TIMEOUT = 6,        /* a bounded device wait expired                 */
   HSS_ERR_UNSUPPORTED = 7,    /* option combination not implemented            */
-  HSS_ERR_OPERATOR = 8        /* the user sampling operator returned nonzero   */
+  HSS_ERR_OPERATOR = 8,       /* the user sampling operator returned nonzero   */
+  HSS_ERR_IO = 9              /* a file could not be opened, written or renamed */
 } hss_status;
 
 /* Sample growth strategy (paper section 2.4): Doubling = Algorithm 4 with
@@ -270,12 +271,21 @@ hss_status hss_get_tuning(hss_tuning* t);
  * in-process).  hss_save writes to the host file `path` the tree, node
  * states and ranks, statistics and every generator (D, U and V as pivots and
  * X, skeleton indices, B12, B21) in a plain binary format (8-byte magic
- * "HSSGEN01", native byte order); the handle must hold usable generators
- * (HSS_ERR_ARG otherwise).  hss_load reads such a file into a new handle on
- * the current device, serving hss_matvec, hss_to_dense, hss_get_node,
- * hss_export_node and hss_get_stats like the original; it cannot resume a
- * compression (the samples are not saved).  HSS_ERR_ARG on a file that is
- * not a checkpoint or is truncated; *out is NULL then. */
+ * "HSSGEN01", native byte order); the handle must have converged
+ * (HSS_ERR_ARG otherwise).  The file is written as `path`.tmp and renamed to
+ * `path` once complete; on failure the temporary file is removed and
+ * nothing is left at `path` (HSS_ERR_IO for a failed open, write, close or
+ * rename, HSS_ERR_CUDA for a failed copy of the generators to the host).
+ * hss_load reads such a file into a new handle on the current device,
+ * serving hss_matvec, hss_to_dense, hss_get_node, hss_export_node and
+ * hss_get_stats like the original; it cannot resume a compression (the
+ * samples are not saved).  Every count, index and pivot is checked on the
+ * host before anything is uploaded: the tree must be the halving tree of
+ * the saved n and leaf size, every array exactly as long as the ranks
+ * imply, the pivots of a node a permutation of its sample rows and its
+ * skeleton indices inside its index range.  HSS_ERR_IO when the file cannot
+ * be opened, HSS_ERR_ARG when it is not such a checkpoint, is truncated or
+ * fails a check; *out is NULL then. */
 hss_status hss_save(hss_matrix H, const char* path);
 hss_status hss_load(const char* path, hss_matrix* out);
 
@@ -326,9 +336,10 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
  * lives in a fixed device array inside the library (4 MiB, held on every
  * GPU that loads the library until the process exits), so n may not
  * exceed 2^20 (larger n returns HSS_ERR_ARG without launching anything).
- * The first call on a device looks up that array's device address (a
- * one-time set-up per device); make that first call before any stream
- * capture.  All calls share the array and overwrite the first n entries:
+ * The first call in a CUDA context looks up that array's device address (a
+ * one-time set-up per context, which may load the library's device code);
+ * make that first call before any stream capture.  A context destroyed and
+ * created again (cudaDeviceReset) gets the set-up anew.  All calls share the array and overwrite the first n entries:
  * calls that overlap on the GPU (on different streams, or from different
  * host threads) race on it and must be serialised by the caller.  The
  * paper has no counterpart to this entry point.  Asynchronous. */

@@ -1338,28 +1338,41 @@ constexpr char kMagic[8] = {'H', 'S', 'S', 'G', 'E', 'N', '0', '1'};
 bool put(FILE* f, const void* p, size_t bytes) { return bytes == 0 || fwrite(p, 1, bytes, f) == bytes; }
 bool get(FILE* f, void* p, size_t bytes) { return bytes == 0 || fread(p, 1, bytes, f) == bytes; }
 
-// one device array: its element count (-1 when absent), then the elements
+// one device array: its element count (-1 when absent), then the elements.
+// Returns 0, or 1 on a write failure, 2 on a failed device copy.
 template <class T>
-bool put_array(FILE* f, const T* dev, long long count) {
+int put_array(FILE* f, const T* dev, long long count) {
   const long long c = dev ? count : -1;
-  if (!put(f, &c, sizeof c)) return false;
-  if (c <= 0) return true;
+  if (!put(f, &c, sizeof c)) return 1;
+  if (c <= 0) return 0;
   std::vector<T> h((size_t)c);
-  if (cudaMemcpy(h.data(), dev, sizeof(T) * (size_t)c, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
-  return put(f, h.data(), sizeof(T) * (size_t)c);
+  if (cudaMemcpy(h.data(), dev, sizeof(T) * (size_t)c, cudaMemcpyDeviceToHost) != cudaSuccess) return 2;
+  return put(f, h.data(), sizeof(T) * (size_t)c) ? 0 : 1;
+}
+
+// Reads one array into host memory: its element count must be `want`
+// (-1: absent), or any count in [0, max_count] when want == -2 (checked by
+// the caller afterwards); *present tells whether it was there.
+template <class T>
+bool get_array(FILE* f, std::vector<T>& h, bool* present, long long want, long long max_count = 0) {
+  long long c = 0;
+  if (!get(f, &c, sizeof c)) return false;
+  if (want == -2 ? (c < 0 || c > max_count) : c != want) return false;
+  *present = c >= 0;
+  h.clear();
+  if (c <= 0) return true;
+  h.resize((size_t)c);
+  return get(f, h.data(), sizeof(T) * (size_t)c);
 }
 
 template <class T>
-bool get_array(FILE* f, Arena& arena, T** dev, long long max_count) {
-  long long c = 0;
-  if (!get(f, &c, sizeof c) || c > max_count) return false;
-  if (c < 0) { *dev = nullptr; return true; }
-  *dev = (T*)arena.alloc(sizeof(T) * (size_t)std::max<long long>(c, 1));
-  if (!*dev) return false;
-  if (c == 0) return true;
-  std::vector<T> h((size_t)c);
-  if (!get(f, h.data(), sizeof(T) * (size_t)c)) return false;
-  return cudaMemcpy(*dev, h.data(), sizeof(T) * (size_t)c, cudaMemcpyHostToDevice) == cudaSuccess;
+hss_status upload_array(Arena& arena, const std::vector<T>& h, bool present, T** dev) {
+  *dev = nullptr;
+  if (!present) return HSS_OK;
+  *dev = (T*)arena.alloc(sizeof(T) * std::max<size_t>(h.size(), 1));
+  if (!*dev) return fail(HSS_ERR_NOMEM, "device allocation for a checkpoint array failed");
+  if (!h.empty()) CK(cudaMemcpy(*dev, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return HSS_OK;
 }
 }  // namespace
 
@@ -1376,6 +1389,7 @@ const char* hss_status_str(hss_status s) {
     case HSS_ERR_TIMEOUT: return "HSS_ERR_TIMEOUT";
     case HSS_ERR_UNSUPPORTED: return "HSS_ERR_UNSUPPORTED";
     case HSS_ERR_OPERATOR: return "HSS_ERR_OPERATOR";
+    case HSS_ERR_IO: return "HSS_ERR_IO";
   }
   return "HSS_ERR_UNKNOWN";
 }
@@ -1563,23 +1577,27 @@ hss_status hss_release_cached(void) {
 
 hss_status hss_save(hss_matrix H, const char* path) {
   if (!H || !path) return fail(HSS_ERR_ARG, "NULL argument");
-  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators (not converged)");
-  FILE* f = fopen(path, "wb");
-  if (!f) return fail(HSS_ERR_ARG, "cannot open %s for writing", path);
+  if (!H->usable || !H->converged)
+    return fail(HSS_ERR_ARG, "only a converged handle can be saved");
+  // written to path.tmp and renamed into place once complete, so a failed
+  // save never leaves a partial file at path
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "wb");
+  if (!f) return fail(HSS_ERR_IO, "cannot open %s for writing", tmp.c_str());
   const int hdr[8] = {H->n, (int)H->nodes.size(), H->max_level, H->usable ? 1 : 0, H->converged, H->d_final,
                       H->n_adapt, H->o.leaf};
   const long long sst = (long long)sizeof(hss_stats);
-  bool ok = put(f, kMagic, sizeof kMagic) && put(f, hdr, sizeof hdr) && put(f, &sst, sizeof sst) &&
-            put(f, &H->st, sizeof(hss_stats));
-  for (size_t i = 0; ok && i < H->nodes.size(); ++i) {
+  int err = (put(f, kMagic, sizeof kMagic) && put(f, hdr, sizeof hdr) && put(f, &sst, sizeof sst) &&
+             put(f, &H->st, sizeof(hss_stats))) ? 0 : 1;
+  for (size_t i = 0; !err && i < H->nodes.size(); ++i) {
     const Node& t = H->nodes[i];
     const int rec[12] = {t.lo, t.size, t.level, t.parent, t.ch[0], t.ch[1], t.leaf ? 1 : 0, t.state,
                          t.r.m, t.r.k, t.c.m, t.c.k};
-    ok = put(f, rec, sizeof rec);
+    err = put(f, rec, sizeof rec) ? 0 : 1;
     for (const Side* sd : {&t.r, &t.c}) {
-      ok = ok && put_array(f, i ? sd->piv : (int*)nullptr, sd->m) &&
-           put_array(f, i ? sd->X : (double*)nullptr, (long long)sd->k * (sd->m - sd->k)) &&
-           put_array(f, i ? sd->I : (int*)nullptr, sd->k);
+      if (!err) err = put_array(f, i ? sd->piv : (int*)nullptr, sd->m);
+      if (!err) err = put_array(f, i ? sd->X : (double*)nullptr, (long long)sd->k * (sd->m - sd->k));
+      if (!err) err = put_array(f, i ? sd->I : (int*)nullptr, sd->k);
     }
     long long nb12 = 0, nb21 = 0;
     if (!t.leaf) {
@@ -1588,74 +1606,130 @@ hss_status hss_save(hss_matrix H, const char* path) {
       nb12 = (long long)a.r.k * b.c.k;
       nb21 = (long long)b.r.k * a.c.k;
     }
-    ok = ok && put_array(f, t.leaf ? t.D : (double*)nullptr, (long long)t.size * t.size) &&
-         put_array(f, t.leaf ? (double*)nullptr : t.B12, nb12) &&
-         put_array(f, t.leaf ? (double*)nullptr : t.B21, nb21);
+    if (!err) err = put_array(f, t.leaf ? t.D : (double*)nullptr, (long long)t.size * t.size);
+    if (!err) err = put_array(f, t.leaf ? (double*)nullptr : t.B12, nb12);
+    if (!err) err = put_array(f, t.leaf ? (double*)nullptr : t.B21, nb21);
   }
-  ok = (fclose(f) == 0) && ok;
-  return ok ? HSS_OK : fail(HSS_ERR_CUDA, "writing %s failed", path);
+  if (fclose(f) != 0 && !err) err = 1;
+  if (!err && rename(tmp.c_str(), path) != 0) err = 1;
+  if (err) {
+    remove(tmp.c_str());
+    return err == 2 ? fail(HSS_ERR_CUDA, "copying the generators to the host failed")
+                    : fail(HSS_ERR_IO, "writing %s failed", path);
+  }
+  return HSS_OK;
 }
 
 hss_status hss_load(const char* path, hss_matrix* out) {
   if (!path || !out) return fail(HSS_ERR_ARG, "NULL argument");
   *out = nullptr;
   FILE* f = fopen(path, "rb");
-  if (!f) return fail(HSS_ERR_ARG, "cannot open %s", path);
-  hss_matrix_s* H = new (std::nothrow) hss_matrix_s();
-  if (!H) {
-    fclose(f);
-    return fail(HSS_ERR_NOMEM, "host allocation failed");
-  }
+  if (!f) return fail(HSS_ERR_IO, "cannot open %s", path);
+  // The whole file is read and checked on the host first; nothing reaches
+  // the device unless every count, index and pivot is consistent.
   char magic[8];
   int hdr[8];
   long long sst = 0;
+  hss_stats st{};
   bool ok = get(f, magic, sizeof magic) && memcmp(magic, kMagic, sizeof kMagic) == 0 && get(f, hdr, sizeof hdr) &&
-            get(f, &sst, sizeof sst) && sst == (long long)sizeof(hss_stats) && get(f, &H->st, sizeof(hss_stats));
-  const int n = ok ? hdr[0] : 0, nn = ok ? hdr[1] : 0;
-  ok = ok && n > 0 && nn > 0 && nn <= 2 * n && hdr[2] >= 0 && hdr[2] < 64 && hdr[3] == 1;
+            get(f, &sst, sizeof sst) && sst == (long long)sizeof(hss_stats) && get(f, &st, sizeof(hss_stats));
+  const int n = ok ? hdr[0] : 0, leaf = ok ? hdr[7] : 0;
+  // the tree must be the halving tree of (n, leaf) the saver used, node by node
+  std::vector<Node> tree;
+  int max_level = 0;
+  ok = ok && n > 0 && leaf >= 1 && hdr[3] == 1 && hdr[4] == 1;
   if (ok) {
-    cudaGetDevice(&H->device);
-    H->n = n;
-    H->max_level = hdr[2];
-    H->usable = true;
-    H->converged = hdr[4];
-    H->d_final = hdr[5];
-    H->n_adapt = hdr[6];
-    H->o.leaf = hdr[7];
-    H->nodes.resize(nn);
-    H->by_level.assign(H->max_level + 1, {});
+    build_tree(n, leaf, tree);
+    for (auto& t : tree) max_level = std::max(max_level, t.level);
+    ok = (int)tree.size() == hdr[1] && hdr[2] == max_level;
   }
+  const int nn = ok ? (int)tree.size() : 0;
+  struct HostSide { std::vector<int> piv, I; std::vector<double> X; bool hp = false, hx = false, hi = false; };
+  struct HostNode { HostSide sd[2]; std::vector<double> D, B12, B21; bool hd = false, hb12 = false, hb21 = false; };
+  std::vector<HostNode> hn(nn);
   for (int i = 0; ok && i < nn; ++i) {
-    Node& t = H->nodes[i];
+    Node& t = tree[i];
     int rec[12];
     ok = get(f, rec, sizeof rec);
     if (!ok) break;
-    t.lo = rec[0]; t.size = rec[1]; t.level = rec[2]; t.parent = rec[3]; t.ch[0] = rec[4]; t.ch[1] = rec[5];
-    t.leaf = rec[6] != 0; t.state = rec[7];
+    ok = rec[0] == t.lo && rec[1] == t.size && rec[2] == t.level && rec[3] == t.parent && rec[4] == t.ch[0] &&
+         rec[5] == t.ch[1] && (rec[6] != 0) == t.leaf && rec[7] == HSS_COMPRESSED;
+    t.state = HSS_COMPRESSED;
     t.r.m = rec[8]; t.r.k = rec[9]; t.c.m = rec[10]; t.c.k = rec[11];
-    ok = t.lo >= 0 && t.size > 0 && t.lo + t.size <= n && t.level >= 0 && t.level <= H->max_level &&
-         (t.leaf || (t.ch[0] > i && t.ch[0] < nn && t.ch[1] > i && t.ch[1] < nn)) && t.r.k >= 0 &&
-         t.r.k <= t.r.m && t.c.k >= 0 && t.c.k <= t.c.m && t.r.m <= n && t.c.m <= n;
-    for (Side* sd : {&t.r, &t.c}) {
-      ok = ok && get_array(f, H->arena, &sd->piv, sd->m) &&
-           get_array(f, H->arena, &sd->X, (long long)sd->k * (sd->m - sd->k)) &&
-           get_array(f, H->arena, &sd->I, sd->k);
+    if (i == 0) ok = ok && t.r.m == 0 && t.r.k == 0 && t.c.m == 0 && t.c.k == 0;
+    else
+      ok = ok && t.r.k >= 0 && t.r.k <= t.r.m && t.c.k >= 0 && t.c.k <= t.c.m && t.r.m <= t.size &&
+           t.c.m <= t.size && (!t.leaf || (t.r.m == t.size && t.c.m == t.size));
+    for (int q = 0; q < 2 && ok; ++q) {
+      const Side& sd = q ? t.c : t.r;
+      HostSide& h = hn[i].sd[q];
+      const int m = sd.m, k = sd.k;
+      ok = get_array(f, h.piv, &h.hp, i ? m : -1) && get_array(f, h.X, &h.hx, i ? (long long)k * (m - k) : -1) &&
+           get_array(f, h.I, &h.hi, i ? k : -1);
+      // the pivots a permutation of [0, m), the skeleton indices inside the
+      // node's index range
+      std::vector<char> seen((size_t)std::max(m, 0), 0);
+      for (int v : h.piv) {
+        if (!ok) break;
+        ok = v >= 0 && v < m && !seen[(size_t)v];
+        if (ok) seen[(size_t)v] = 1;
+      }
+      for (int v : h.I) ok = ok && v >= t.lo && v < t.lo + t.size;
     }
-    ok = ok && get_array(f, H->arena, &t.D, (long long)t.size * t.size) &&
-         get_array(f, H->arena, &t.B12, (long long)n * n) && get_array(f, H->arena, &t.B21, (long long)n * n);
-    if (ok) H->by_level[t.level].push_back(i);
+    HostNode& h = hn[i];
+    ok = ok && get_array(f, h.D, &h.hd, t.leaf ? (long long)t.size * t.size : -1) &&
+         get_array(f, h.B12, &h.hb12, t.leaf ? -1 : -2, (long long)n * n) &&
+         get_array(f, h.B21, &h.hb21, t.leaf ? -1 : -2, (long long)n * n);
   }
-  // every generator the products read must be there
+  // the sample rows and the B blocks agree with the children's ranks (the
+  // products index with them)
   for (int i = 0; ok && i < nn; ++i) {
-    const Node& t = H->nodes[i];
-    if (t.leaf && !t.D) ok = false;
-    if (!t.leaf && (!t.B12 || !t.B21)) ok = false;
-    if (i > 0 && (!t.r.piv || !t.c.piv || !t.r.X || !t.c.X)) ok = false;
+    const Node& t = tree[i];
+    if (t.leaf) continue;
+    const Node& a = tree[t.ch[0]];
+    const Node& b = tree[t.ch[1]];
+    ok = hn[i].B12.size() == (size_t)a.r.k * b.c.k && hn[i].B21.size() == (size_t)b.r.k * a.c.k;
+    if (i > 0) ok = ok && t.r.m == a.r.k + b.r.k && t.c.m == a.c.k + b.c.k;
   }
+  // nothing may follow the last node
+  char extra;
+  ok = ok && fread(&extra, 1, 1, f) == 0;
   fclose(f);
-  if (!ok) {
+  if (!ok) return fail(HSS_ERR_ARG, "%s is not a readable HSS generator checkpoint", path);
+
+  hss_matrix_s* H = new (std::nothrow) hss_matrix_s();
+  if (!H) return fail(HSS_ERR_NOMEM, "host allocation failed");
+  H->n = n;
+  H->max_level = max_level;
+  H->usable = true;
+  H->converged = 1;
+  H->d_final = hdr[5];
+  H->n_adapt = hdr[6];
+  H->o.leaf = leaf;
+  H->st = st;
+  H->st.n = n;
+  H->st.n_nodes = nn;
+  H->st.levels = max_level + 1;
+  H->nodes = tree;
+  H->by_level.assign(max_level + 1, {});
+  hss_status e = cudaGetDevice(&H->device) == cudaSuccess ? HSS_OK : fail(HSS_ERR_CUDA, "no CUDA device");
+  for (int i = 0; e == HSS_OK && i < nn; ++i) {
+    Node& t = H->nodes[i];
+    for (int q = 0; q < 2 && e == HSS_OK; ++q) {
+      Side& sd = q ? t.c : t.r;
+      const HostSide& h = hn[i].sd[q];
+      e = upload_array(H->arena, h.piv, h.hp, &sd.piv);
+      if (e == HSS_OK) e = upload_array(H->arena, h.X, h.hx, &sd.X);
+      if (e == HSS_OK) e = upload_array(H->arena, h.I, h.hi, &sd.I);
+    }
+    if (e == HSS_OK) e = upload_array(H->arena, hn[i].D, hn[i].hd, &t.D);
+    if (e == HSS_OK) e = upload_array(H->arena, hn[i].B12, hn[i].hb12, &t.B12);
+    if (e == HSS_OK) e = upload_array(H->arena, hn[i].B21, hn[i].hb21, &t.B21);
+    H->by_level[t.level].push_back(i);
+  }
+  if (e != HSS_OK) {
     delete H;
-    return fail(HSS_ERR_ARG, "%s is not a readable HSS generator checkpoint", path);
+    return e;
   }
   *out = H;
   return HSS_OK;
@@ -1976,8 +2050,9 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
 // ===================================================================
 #include <mutex>
 
+#include <cuda.h>
+
 #define HSS_NOALLOC_MAX_N (1 << 20)   /* 4 MiB of leaf labels */
-#define HSS_NOALLOC_MAX_DEVICES 64
 
 static __device__ __align__(256) int g_noalloc_leaf_label[HSS_NOALLOC_MAX_N];
 
@@ -1998,25 +2073,57 @@ __global__ void k_noalloc_leaf_label(int* label, int n, int leaf) {
 }
 
 std::mutex g_noalloc_mu;
-int* g_noalloc_ptr[HSS_NOALLOC_MAX_DEVICES] = {nullptr};
+// (context id, device address of the label array in that context): a
+// context that is destroyed and created again (cudaDeviceReset) reloads the
+// library's module at another address and gets a new id, so a cached
+// address never outlives its context
+std::vector<std::pair<unsigned long long, int*>> g_noalloc_ptr;
 
-// Device address of the label array on the current device, looked up once
-// per device (host code must not pass the symbol itself to a kernel).
-hss_status noalloc_table(int** out) {
-  int dev = -1;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= HSS_NOALLOC_MAX_DEVICES)
-    return fail(HSS_ERR_UNSUPPORTED, "device index %d beyond %d", dev, HSS_NOALLOC_MAX_DEVICES);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_leaf_label);
-    if (e != cudaSuccess || !p)
-      return fail(HSS_ERR_CUDA, "cudaGetSymbolAddress of the leaf-label array failed: %s",
-                  cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = (int*)p;
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+
+// Id of the current context (driver entry points looked up through the
+// runtime, so the library does not link the driver library itself); false
+// when there is no current context yet or the lookup is unavailable.
+bool current_context_id(unsigned long long* id) {
+  static ctx_get_current_fn get_current = nullptr;
+  static ctx_get_id_fn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return false;
+    get_current = (ctx_get_current_fn)f1;
+    get_id = (ctx_get_id_fn)f2;
   }
-  *out = g_noalloc_ptr[dev];
+  CUcontext ctx = nullptr;
+  return get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the label array in the current context, looked up once
+// per context (host code must not pass the symbol itself to a kernel).  The
+// first lookup in a context may load the library's device code; later calls
+// only read the table.
+hss_status noalloc_table(int** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
+  if (have_id)
+    for (auto& e : g_noalloc_ptr)
+      if (e.first == id) {
+        *out = e.second;
+        return HSS_OK;
+      }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_leaf_label);
+  if (e != cudaSuccess || !p)
+    return fail(HSS_ERR_CUDA, "cudaGetSymbolAddress of the leaf-label array failed: %s", cudaGetErrorString(e));
+  if (!have_id) have_id = current_context_id(&id);   // the lookup made the primary context current
+  if (have_id) g_noalloc_ptr.push_back({id, (int*)p});
+  *out = (int*)p;
   return HSS_OK;
 }
 

@@ -19,7 +19,7 @@ TUNING_PATH = os.path.join(_HERE, "tuning_sm103.json")
 
 HSS_OK, HSS_ERR_ARG, HSS_ERR_NOMEM, HSS_ERR_CUDA = 0, 1, 2, 3
 HSS_ERR_NOT_CONVERGED, HSS_ERR_NONFINITE, HSS_ERR_TIMEOUT, HSS_ERR_UNSUPPORTED = 4, 5, 6, 7
-HSS_ERR_OPERATOR = 8
+HSS_ERR_OPERATOR, HSS_ERR_IO = 8, 9
 HSS_DOUBLING, HSS_INCREMENTING = 0, 1
 HSS_CRIT_NEW, HSS_CRIT_HMT = 0, 1
 HSS_PREC_FP64, HSS_PREC_TF32X2, HSS_PREC_BF16X3 = 0, 1, 2

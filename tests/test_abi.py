@@ -82,7 +82,7 @@ def test_argument_validation_without_gpu(hss):
     # checkpoints: arguments and files checked on the host
     assert L.hss_save(None, b"/nonexistent/x") == hss.HSS_ERR_ARG
     hh = C.c_void_p(123)
-    assert L.hss_load(b"/nonexistent/dir/file", C.byref(hh)) == hss.HSS_ERR_ARG and not hh.value
+    assert L.hss_load(b"/nonexistent/dir/file", C.byref(hh)) == hss.HSS_ERR_IO and not hh.value
     import tempfile
     with tempfile.NamedTemporaryFile(suffix=".hss", delete=False) as tf:
         tf.write(b"not a checkpoint at all")
@@ -121,3 +121,99 @@ def test_argument_validation_without_gpu(hss):
     assert L.hss_compress_restart(C.byref(s), C.byref(bad), None, C.byref(h), None) == hss.HSS_ERR_ARG
     assert L.hss_rcb_order(None, 10, 2, 10, 4, None) == hss.HSS_ERR_ARG
     assert L.hss_random_normal(0, 10, 0, 1, None, 10, 0, None) == hss.HSS_ERR_ARG
+
+
+# ------------------------------------------------------------ checkpoint files
+def _checkpoint_bytes(hss, n=8, leaf=2, mutate=None):
+    """A well-formed checkpoint of a handle on the halving tree of (n, leaf)
+    with rank 1 at every node, written field by field in the file format of
+    hss_save (magic, header, statistics, then per node its record and
+    arrays as count + elements).  ``mutate(name, value)`` may replace a field
+    before it is written."""
+    import struct
+    nodes = otree.halving_tree(n, leaf)
+    mx = max(t.level for t in nodes)
+    mut = mutate or (lambda name, v: v)
+    out = [b"HSSGEN01"]
+    hdr = mut("hdr", [n, len(nodes), mx, 1, 1, 4, 0, leaf])
+    out.append(struct.pack("8i", *hdr))
+    sst = C.sizeof(hss.hss_stats)
+    out.append(struct.pack("q", sst) + bytes(sst))
+
+    def arr(name, vals, fmt):
+        vals = mut(name, vals)
+        if vals is None:
+            return struct.pack("q", -1)
+        return struct.pack("q", len(vals)) + struct.pack(f"{len(vals)}{fmt}", *vals)
+
+    for t in nodes:
+        root, leafn = t.idx == 0, not t.children
+        m = 0 if root else (t.size if leafn else 2)
+        k = 0 if root else 1
+        rec = mut(f"rec{t.idx}", [t.lo, t.size, t.level, t.parent,
+                                  t.children[0] if t.children else -1, t.children[1] if t.children else -1,
+                                  1 if leafn else 0, 2, m, k, m, k])
+        out.append(struct.pack("12i", *rec))
+        for side in "rc":
+            piv = None if root else list(range(m))[::-1]
+            X = None if root else [0.5] * (k * (m - k))
+            # skeleton index: the global index of the first pivot's row
+            I = None if root else [t.lo + (piv[0] if leafn else 0)]
+            out.append(arr(f"piv{t.idx}{side}", piv, "i"))
+            out.append(arr(f"X{t.idx}{side}", X, "d"))
+            out.append(arr(f"I{t.idx}{side}", I, "i"))
+        out.append(arr(f"D{t.idx}", [1.0] * (t.size * t.size) if leafn else None, "d"))
+        out.append(arr(f"B12{t.idx}", None if leafn else [0.7], "d"))
+        out.append(arr(f"B21{t.idx}", None if leafn else [0.3], "d"))
+    return b"".join(out)
+
+
+def _load_status(hss, blob, tmp_path):
+    p = tmp_path / "c.hss"
+    p.write_bytes(blob)
+    h = C.c_void_p(123)
+    st = hss.lib().hss_load(str(p).encode(), C.byref(h))
+    if st == hss.HSS_OK:
+        hss.lib().hss_free(h)
+    else:
+        assert not h.value
+    return st
+
+
+def test_checkpoint_checks_on_host(hss, tmp_path):
+    """hss_load checks the whole file on the host before it uploads
+    anything: a well-formed file gets past every check (without a GPU it then
+    fails at the device copy, HSS_ERR_CUDA), and each damaged variant is
+    rejected as HSS_ERR_ARG."""
+    import torch
+    good = _checkpoint_bytes(hss)
+    if not torch.cuda.is_available():
+        assert _load_status(hss, good, tmp_path) == hss.HSS_ERR_CUDA
+    else:
+        assert _load_status(hss, good, tmp_path) == hss.HSS_OK
+
+    def bad(name, fn):
+        return _checkpoint_bytes(hss, mutate=lambda nm, v: fn(v) if nm == name else v)
+
+    damaged = {
+        "truncated": good[:-8],
+        "trailing bytes": good + b"\0",
+        "pivot repeated": bad("piv3r", lambda v: [v[0], v[0]]),
+        "pivot out of range": bad("piv1c", lambda v: [2, 0]),
+        "pivot array short": bad("piv4r", lambda v: v[:1]),
+        "X count": bad("X2c", lambda v: v + [0.0]),
+        "X missing": bad("X5r", lambda v: None),
+        "skeleton index outside the node": bad("I6r", lambda v: [0]),
+        "B12 count": bad("B121", lambda v: v + [1.0, 2.0]),
+        "B21 missing": bad("B210", lambda v: None),
+        "D short": bad("D3", lambda v: v[:3]),
+        "D at a non-leaf": bad("D1", lambda v: [1.0]),
+        "tree record": bad("rec2", lambda v: [v[0], v[1] + 1] + v[2:]),
+        "sample rows of a non-leaf": bad("rec1", lambda v: v[:8] + [3, 1, 3, 1]),
+        "rank above rows": bad("rec3", lambda v: v[:8] + [2, 3, 2, 1]),
+        "not converged": bad("hdr", lambda v: v[:4] + [0] + v[5:]),
+        "leaf size": bad("hdr", lambda v: v[:7] + [4]),   # a 3-node tree
+        "node count": bad("hdr", lambda v: [v[0], v[1] + 2] + v[2:]),
+    }
+    for what, blob in damaged.items():
+        assert _load_status(hss, blob, tmp_path) == hss.HSS_ERR_ARG, what

@@ -294,3 +294,11 @@ def test_checkpoint_round_trip(hss, torch, tmp_path):
                 else:
                     np.testing.assert_array_equal(e1[k], e2[k])
         np.testing.assert_allclose(gu.gpu_dense(H2, n), gu.gpu_dense(H, n), rtol=0, atol=1e-15)
+        import os
+        assert not os.path.exists(path + ".tmp")
+    # a failed save (no such directory) is an I/O error and leaves no file
+    bad = str(tmp_path / "missing" / "h.hss")
+    with pytest.raises(hss.HSSError) as ei:
+        hss.hss_save(H, bad)
+    assert ei.value.status == hss.HSS_ERR_IO
+    assert not (tmp_path / "missing").exists()
