@@ -30,8 +30,9 @@ typedef enum {
   HSS_ERR_NOMEM = 2,          /* device or host allocation failed              */
   HSS_ERR_CUDA = 3,           /* a CUDA call failed (message in last_error)    */
   HSS_ERR_NOT_CONVERGED = 4,  /* d reached d_max with the root not COMPRESSED;
-                                 the handle is returned with per-node states,
-                                 but holds no usable generators                */
+                                 the handle is returned with per-node states
+                                 and is usable as a partial result (see
+                                 hss_compress)                                 */
   HSS_ERR_NONFINITE = 5,      /* NaN or Inf found in the random samples        */
   HSS_ERR_TIMEOUT = 6,        /* a bounded device wait expired                 */
   HSS_ERR_UNSUPPORTED = 7,    /* option combination not implemented            */
@@ -77,9 +78,39 @@ enum {
                             A_ij = r[j-i] for j > i (b may equal a)          */
   HSS_SRC_GAUSS = 2,     /* a: device points, col-major n x dim (ld);
                             A_ij = exp(-|x_i - x_j|^2 / (2 p0^2)) + p1 [i==j] */
-  HSS_SRC_LAPLACE = 3    /* a: device points, col-major n x 3 (ld);
+  HSS_SRC_LAPLACE = 3,   /* a: device points, col-major n x 3 (ld);
                             A_ij = 1 / (4 pi |x_i - x_j|), A_ii = p0          */
+  HSS_SRC_EXTRACT = 4    /* the caller's element extraction routine
+                            (extract, ctx below; a, b, ld, p0, p1 unused):
+                            the matrix is known only through it and the
+                            sampling operator opts->op, which is then
+                            required                                         */
 };
+
+/* One block request of the element extraction routine (section 3.1: the
+ * routine returns sub-blocks A(I, J) for row and column index sets):
+ * out(i, j) = A(I[i], J[j]) for i < nr, j < nc.  I, J: device int arrays of
+ * global indices (0-based); out: device, col-major, leading dimension
+ * ldo >= nr.  All three are owned by the library. */
+typedef struct hss_block {
+  int nr, nc;
+  const int* I;
+  const int* J;
+  double* out;
+  long long ldo;
+} hss_block;
+
+/* The element extraction routine of an HSS_SRC_EXTRACT source: fills the
+ * nblocks requests of `blocks` (a host array, valid during the call) by work
+ * it enqueues on `stream` (a cudaStream_t); returns 0, or nonzero on failure
+ * (the compression then stops with HSS_ERR_OPERATOR).  As in the paper's
+ * level-by-level traversal, the blocks of one tree level come in one call
+ * (the B12 and B21 generators of its nodes), the leaf diagonal blocks D in
+ * one call before the first sampling pass, and, when d_max is reached
+ * without convergence, the dense off-diagonal blocks of the nodes left
+ * uncompressed in one more call.  It runs on the host thread of the
+ * compression (a worker thread of hss_compress_batched). */
+typedef int (*hss_extract_fn)(void* ctx, int nblocks, const hss_block* blocks, void* stream);
 
 typedef struct hss_source {
   int kind;              /* HSS_SRC_*                                        */
@@ -90,6 +121,9 @@ typedef struct hss_source {
   const double* b;       /* device, TOEPLITZ first row; NULL otherwise       */
   long long ld;          /* leading dimension of a (DENSE, points)           */
   double p0, p1;         /* kernel parameters, see HSS_SRC_*                 */
+  hss_extract_fn extract; /* HSS_SRC_EXTRACT: the extraction routine; NULL
+                            otherwise                                        */
+  void* ctx;             /* passed to extract unchanged                      */
 } hss_source;
 
 /* Node states of Algorithm 3. */
@@ -105,7 +139,8 @@ enum { HSS_UNTOUCHED = 0, HSS_PARTIALLY_COMPRESSED = 1, HSS_COMPRESSED = 2 };
  * after the call returns.  It returns 0, or nonzero on failure (the
  * compression then stops with HSS_ERR_OPERATOR).  The entries of A for the
  * generators (D and B blocks, and the leaf diagonal blocks removed from the
- * samples) still come from the hss_source, which must describe the same A.
+ * samples) come from the hss_source, which must describe the same A (a
+ * built-in source, or the caller's extraction routine, HSS_SRC_EXTRACT).
  * The callback runs on the host thread of the compression (a worker thread
  * of hss_compress_batched), once per orientation and pass. */
 typedef int (*hss_apply_fn)(void* ctx, int trans, int n, int ncols, const double* R, long long ldr,
@@ -143,6 +178,13 @@ typedef struct hss_opts {
                             product's arithmetic is the operator's) and the
                             library removes the leaf diagonal blocks
                             D_tau R(I_tau) from its result (Algorithm 2)      */
+  long long wait_limit_ns; /* bound of each device-side wait of the kernels
+                            whose CTAs work on one node side together (QRCP
+                            and Incrementing test group barriers), in ns of
+                            the GPU's global timer; 0 = about 2 s.  A wait
+                            that runs out makes the kernels return and the
+                            call fail with HSS_ERR_TIMEOUT; the library stays
+                            usable                                           */
 } hss_opts;
 
 typedef struct hss_stats {
@@ -180,10 +222,19 @@ typedef struct hss_matrix_s* hss_matrix;   /* opaque; owns device memory    */
 /* Adaptive randomized HSS compression, Algorithm 3 (HSSCompressAdaptive and
  * CompressNodeAdaptive) with Algorithm 2 (ComputeLocalSamples,
  * ReduceLocalSamples), the ID of eq. ID and the strategy of opts->strategy.
- * A: source of the entries of A (device data).  out: receives a handle,
- * also on HSS_ERR_NOT_CONVERGED (then the states are valid but the
- * generators are not); on any other error *out is NULL.  The handle owns
- * all generator memory until hss_free. */
+ * A: source of the entries of A (device data, or the caller's extraction
+ * routine).  out: receives a handle, also on HSS_ERR_NOT_CONVERGED; on any
+ * other error *out is NULL.  The handle owns all generator memory until
+ * hss_free.
+ * HSS_ERR_NOT_CONVERGED (Algorithm 3's loop ends at d_max with the root not
+ * COMPRESSED): the node states are those of the last pass, the generators of
+ * the COMPRESSED subtrees stand, and the rest of A is kept as it is — for
+ * each uncompressed node with children the blocks A(I_nu1, I_nu2) and
+ * A(I_nu2, I_nu1) between its children, for the leaves D — so that
+ * hss_matvec and hss_to_dense reproduce A exactly outside the compressed
+ * subtrees.  When those blocks would take more than half of the free device
+ * memory they are not kept, and the handle then serves hss_get_stats,
+ * hss_get_node and hss_export_node only (HSS_ERR_ARG from the products). */
 hss_status hss_compress(const hss_source* A, const hss_opts* opts, void* stream,
                         hss_matrix* out);
 
@@ -216,12 +267,33 @@ hss_status hss_compress_restart(const hss_source* A, const hss_opts* opts, void*
 hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int count, void* stream,
                                 hss_matrix* out);
 
-/* Y = H X for a compressed handle: the O(r n) product of section 2.1
- * (up-sweep x^_tau = V_tau^T [...], sibling coupling with B12/B21, down-sweep
- * with U_tau, leaves D_tau).  X, Y: device col-major n x nrhs (ldx, ldy >= n);
- * Y is overwritten.  Asynchronous on the stream. */
+/* Y = H X (transpose = 0) or Y = H^T X (transpose = 1) for a compressed
+ * handle: the O(r n) product of section 2.1 (up-sweep
+ * x^_tau = V_tau^T [...], sibling coupling with B12 / B21, down-sweep with
+ * U_tau, leaves D_tau); H^T exchanges the roles of U and V, takes D^T and
+ * couples with B21^T, B12^T.  A partial result (HSS_ERR_NOT_CONVERGED)
+ * couples the children of its uncompressed nodes through the dense blocks
+ * it kept.  X, Y: device col-major n x nrhs (ldx, ldy >= n); Y is
+ * overwritten.  Asynchronous on the stream. */
 hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx,
-                      double* Y, long long ldy, void* stream);
+                      double* Y, long long ldy, int transpose, void* stream);
+
+/* Entries of a compressed handle, out(r, c) = H(I[r], J[c]) — the element
+ * extraction of section 3.1 applied to an HSS matrix, so that a matrix built
+ * from compressed ones (a sum, or a product through hss_matvec) can itself be
+ * compressed through a user operator and an extraction source.  For i and j
+ * in one leaf the entry is D(i, j); otherwise u_a(i) B v_b(j)^T with a, b the
+ * children of the lowest common ancestor holding i and j, u_a(i) the row of
+ * the nested basis U_a (eq. nestedUV: a leaf's U = Pi [I; X^T], each level
+ * up times the node's own basis) and v_b(j) that of V_b; the dense blocks of
+ * a partial result where they apply.  Cost: for each row index the products
+ * along its path to the root (sum over its ancestors of k^2), and k per
+ * entry.  I (nr), J (nc): device int arrays of indices in [0, n); out: device
+ * col-major nr x nc, ld ldo >= nr.  Uses a temporary device buffer; returns
+ * after a sync of the stream; HSS_ERR_ARG (entries left zero) when an index
+ * is out of range. */
+hss_status hss_get_entries(hss_matrix H, int nr, const int* I, int nc, const int* J, double* out,
+                           long long ldo, void* stream);
 
 /* The dense matrix H (eq. nestedUV expanded): out (device, col-major n x n,
  * ld >= n) = H applied to identity column blocks of up to 2048 columns with

@@ -188,6 +188,10 @@ struct Node {
   double* D = nullptr;   // leaf: size x size col-major
   double* B12 = nullptr; // kr(nu1) x kc(nu2) col-major, ld max(kr(nu1),1)
   double* B21 = nullptr; // kr(nu2) x kc(nu1) col-major, ld max(kr(nu2),1)
+  // a node that is not COMPRESSED when the compression stops at d_max: the
+  // blocks A(I_nu1, I_nu2) (|nu1| x |nu2|) and A(I_nu2, I_nu1), col-major
+  double* F12 = nullptr;
+  double* F21 = nullptr;
 };
 
 // Phase boundaries: CUDA events on the stream (the per-phase times of the
@@ -249,6 +253,8 @@ struct hss_matrix_s {
   double* Sg_c = nullptr;
   int* leaf_id = nullptr;
   int* leaf_lo = nullptr;  // nleaves + 1 row bounds (with a user operator)
+  long long* leaf_doff = nullptr; // offset of each leaf's D in the packed leaf blocks (user operator)
+  double* leaf_D = nullptr;       // the leaf blocks D, packed (user operator)
   int* iota = nullptr;
   int* d_flag = nullptr;   // device int scratch
   int* h_pinned = nullptr; // host pinned readback buffer
@@ -263,6 +269,7 @@ struct hss_matrix_s {
   cudaEvent_t trace_ev[2] = {nullptr, nullptr};
   void* packA = nullptr;   // packed tensor-core tiles of a dense A (during compress)
   bool usable = false;
+  bool partial = false;    // not converged; the uncompressed part kept dense (F12, F21)
   hss_stats st{};
   long long launches = 0;
   PhaseTimer timer;
@@ -297,6 +304,10 @@ SrcDev make_src(const hss_source& s, const int* leaf_id) {
 hss_status check_source(const hss_source* A) {
   if (!A) return fail(HSS_ERR_ARG, "source is NULL");
   if (A->n <= 0) return fail(HSS_ERR_ARG, "n must be positive (got %d)", A->n);
+  if (A->kind == HSS_SRC_EXTRACT) {
+    if (!A->extract) return fail(HSS_ERR_ARG, "an extraction source needs its extract routine");
+    return HSS_OK;
+  }
   if (!A->a) return fail(HSS_ERR_ARG, "source data pointer is NULL");
   switch (A->kind) {
     case HSS_SRC_DENSE:
@@ -451,6 +462,44 @@ hss_status upload_jobs(hss_matrix_s* H, const std::vector<T>& jobs, T** dev, cud
   return upload(H, *dev, jobs.data(), jobs.size() * sizeof(T), st);
 }
 
+// Element extraction out(i, j) = A(I[i], J[j]) for a list of blocks (one
+// tree level, or the leaf blocks): one launch of the gather / generator
+// kernel for a built-in source, one call of the caller's routine for an
+// extraction source (section 3.1: all blocks of a level at once).
+hss_status extract_blocks(hss_matrix_s* H, const std::vector<ExtractJob>& ex, cudaStream_t st) {
+  if (ex.empty()) return HSS_OK;
+  if (H->src.kind == HSS_SRC_EXTRACT) {
+    std::vector<hss_block> blk;
+    blk.reserve(ex.size());
+    for (const ExtractJob& e : ex) {
+      if (e.mi <= 0 || e.nj <= 0) continue;
+      hss_block b;
+      b.nr = e.mi; b.nc = e.nj;
+      b.I = e.I ? e.I : H->iota + e.i0;
+      b.J = e.J ? e.J : H->iota + e.j0;
+      b.out = e.out; b.ldo = e.ldo;
+      blk.push_back(b);
+    }
+    if (blk.empty()) return HSS_OK;
+    const int rc = H->src.extract(H->src.ctx, (int)blk.size(), blk.data(), (void*)st);
+    if (rc != 0) return fail(HSS_ERR_OPERATOR, "user element extraction returned %d (%zu blocks)", rc, blk.size());
+    return HSS_OK;
+  }
+  int max_tiles = 1;
+  for (const ExtractJob& e : ex) max_tiles = std::max(max_tiles, ((e.mi + 31) / 32) * ((e.nj + 31) / 32));
+  ExtractJob* dj;
+  CKS(upload_jobs(H, ex, &dj, st));
+  CK(launch_extract(make_src(H->src, H->leaf_id), dj, (int)ex.size(), max_tiles, st));
+  H->launches++;
+  CK(cudaFreeAsync(dj, st));
+  return HSS_OK;
+}
+
+// bound of one device-side group wait: the caller's, else about 2 s
+unsigned long long wait_limit(const hss_matrix_s* H) {
+  return H->o.wait_limit_ns > 0 ? (unsigned long long)H->o.wait_limit_ns : 2000000000ull;
+}
+
 double tol_scale(const hss_matrix_s* H, int level) {
   return H->o.level_tol_scaling ? 1.0 / (double)level : 1.0;
 }
@@ -497,8 +546,11 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
         return fail(HSS_ERR_OPERATOR, "user operator returned %d (trans = %d, columns %d..%d)", rc, side, c0, c1);
       }
     }
-    CK(launch_leaf_diag_sub(s, H->leaf_lo, n, w, Rc, n, T, n, H->Sg_r + c0, H->dmax, 0, st));
-    if (!H->sym) CK(launch_leaf_diag_sub(s, H->leaf_lo, n, w, Rc, n, T + (size_t)n * w, n, H->Sg_c + c0, H->dmax, 1, st));
+    CK(launch_leaf_diag_sub(H->leaf_D, H->leaf_doff, H->leaf_id, H->leaf_lo, n, w, Rc, n, T, n, H->Sg_r + c0,
+                            H->dmax, 0, st));
+    if (!H->sym)
+      CK(launch_leaf_diag_sub(H->leaf_D, H->leaf_doff, H->leaf_id, H->leaf_lo, n, w, Rc, n, T + (size_t)n * w, n,
+                              H->Sg_c + c0, H->dmax, 1, st));
     H->launches += norient;
     H->st.sample_launches += norient;
     CK(cudaFreeAsync(T, st));
@@ -787,6 +839,7 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     j.redv = (double*)H->scratch.take(sizeof(double) * 4 * P[i]);   // 2 P (key, index) pairs
     j.redt = (double*)H->scratch.take(sizeof(double) * 2 * P[i]);
     j.xfer = (double*)H->scratch.take(sizeof(double) * 8);
+    j.wait_ns = wait_limit(H);
     wbuf.push_back(j.W);
     jobs.push_back(j);
   }
@@ -896,7 +949,6 @@ hss_status finalize_id(hss_matrix_s* H, int node, int side, const double* W, int
 
 hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
   const bool dbl = H->o.strategy == HSS_DOUBLING;
-  SrcDev src = make_src(H->src, H->leaf_id);
   for (int lev = H->max_level; lev >= 1; --lev) {
     LevelWork lw;
     for (int id : H->by_level[lev]) {
@@ -910,20 +962,20 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
     CK(H->timer.mark(PH_MERGE, st));
     // --- extraction of D (new leaves) and B12/B21 (new non-leaves)
     std::vector<ExtractJob> ex;
-    int max_tiles = 1;
     auto add_ex = [&](const int* I, int i0, int mi, const int* J, int j0, int nj, double* out, long long ldo) {
       if (mi <= 0 || nj <= 0) return;
       ExtractJob e{I, i0, mi, J, j0, nj, out, ldo};
       ex.push_back(e);
-      max_tiles = std::max(max_tiles, ((mi + 31) / 32) * ((nj + 31) / 32));
     };
     for (int id : lw.cand) {
       Node& t = H->nodes[id];
       if (t.state != HSS_UNTOUCHED) continue;
       if (t.leaf) {
-        t.D = (double*)H->arena.alloc(sizeof(double) * (size_t)t.size * t.size);
-        if (!t.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
-        add_ex(nullptr, t.lo, t.size, nullptr, t.lo, t.size, t.D, t.size);
+        if (!t.D) {   // (already there with a user operator)
+          t.D = (double*)H->arena.alloc(sizeof(double) * (size_t)t.size * t.size);
+          if (!t.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
+          add_ex(nullptr, t.lo, t.size, nullptr, t.lo, t.size, t.D, t.size);
+        }
         CKS(alloc_side(H, t.r, true, H->Sg_r + (long long)t.lo * H->dmax, t.size));
         if (H->sym) t.c = t.r;
         else CKS(alloc_side(H, t.c, true, H->Sg_c + (long long)t.lo * H->dmax, t.size));
@@ -940,13 +992,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
         else CKS(alloc_side(H, t.c, false, nullptr, a.c.k + b.c.k));
       }
     }
-    if (!ex.empty()) {
-      ExtractJob* dj;
-      CKS(upload_jobs(H, ex, &dj, st));
-      CK(launch_extract(src, dj, (int)ex.size(), max_tiles, st));
-      H->launches++;
-      CK(cudaFreeAsync(dj, st));
-    }
+    CKS(extract_blocks(H, ex, st));
     // --- local samples of non-leaf nodes (upward merge)
     std::vector<GemmJob> mj;
     for (int id : lw.cand) {
@@ -1023,6 +1069,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
           j.rho = s.rho;
           j.hmt = H->o.criterion == HSS_CRIT_HMT;
           j.hmt_c = j.hmt ? H->o.hmt_alpha * std::sqrt(2.0 / std::acos(-1.0)) : 0.0;
+          j.wait_ns = wait_limit(H);
           ij.push_back(j);
           // Sh = S(:, tested:tested+b)
           GemmJob c = gemm_job();
@@ -1193,15 +1240,10 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
   Node& root = H->nodes[0];
   if (root.leaf || (H->nodes[root.ch[0]].state == HSS_COMPRESSED &&
                     H->nodes[root.ch[1]].state == HSS_COMPRESSED)) {
-    if (root.leaf && root.state == HSS_UNTOUCHED) {
+    if (root.leaf && root.state == HSS_UNTOUCHED && !root.D) {
       root.D = (double*)H->arena.alloc(sizeof(double) * (size_t)root.size * root.size);
       if (!root.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
-      std::vector<ExtractJob> ex{{nullptr, 0, root.size, nullptr, 0, root.size, root.D, root.size}};
-      ExtractJob* dj;
-      CKS(upload_jobs(H, ex, &dj, st));
-      CK(launch_extract(src, dj, 1, ((root.size + 31) / 32) * ((root.size + 31) / 32), st));
-      H->launches++;
-      CK(cudaFreeAsync(dj, st));
+      CKS(extract_blocks(H, {{nullptr, 0, root.size, nullptr, 0, root.size, root.D, root.size}}, st));
     }
     if (!root.leaf && root.state == HSS_UNTOUCHED) {
       // the root keeps B12 = A(nu1.I^r, nu2.I^c) and B21 = A(nu2.I^r, nu1.I^c)
@@ -1211,25 +1253,45 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
       root.B21 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(b.r.k, 1) * std::max(a.c.k, 1));
       if (!root.B12 || !root.B21) return fail(HSS_ERR_NOMEM, "device arena allocation failed (B)");
       std::vector<ExtractJob> ex;
-      int tiles = 1;
-      if (a.r.k > 0 && b.c.k > 0) {
-        ex.push_back({a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, root.B12, std::max(a.r.k, 1)});
-        tiles = std::max(tiles, ((a.r.k + 31) / 32) * ((b.c.k + 31) / 32));
-      }
-      if (b.r.k > 0 && a.c.k > 0) {
-        ex.push_back({b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, root.B21, std::max(b.r.k, 1)});
-        tiles = std::max(tiles, ((b.r.k + 31) / 32) * ((a.c.k + 31) / 32));
-      }
-      if (!ex.empty()) {
-        ExtractJob* dj;
-        CKS(upload_jobs(H, ex, &dj, st));
-        CK(launch_extract(src, dj, (int)ex.size(), tiles, st));
-        H->launches++;
-        CK(cudaFreeAsync(dj, st));
-      }
+      if (a.r.k > 0 && b.c.k > 0) ex.push_back({a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, root.B12, std::max(a.r.k, 1)});
+      if (b.r.k > 0 && a.c.k > 0) ex.push_back({b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, root.B21, std::max(b.r.k, 1)});
+      CKS(extract_blocks(H, ex, st));
     }
     root.state = HSS_COMPRESSED;
   }
+  return HSS_OK;
+}
+
+// When d_max is reached with the root not COMPRESSED (Algorithm 3's loop
+// ends there), the generators of the compressed subtrees stand, and the
+// rest of A is kept as it is: for every node with children that is not
+// COMPRESSED, the blocks A(I_nu1, I_nu2) and A(I_nu2, I_nu1) between its
+// children (the leaves keep D).  The products and the dense expansion then
+// reproduce A exactly outside the compressed subtrees.  The blocks take
+// sum 2 |nu1| |nu2| doubles; when that exceeds half of the free device
+// memory they are not kept and the handle holds no usable generators.
+hss_status keep_dense_blocks(hss_matrix_s* H, cudaStream_t st) {
+  double need = 0.0;
+  for (auto& t : H->nodes)
+    if (!t.leaf && t.state != HSS_COMPRESSED)
+      need += 2.0 * 8.0 * (double)H->nodes[t.ch[0]].size * (double)H->nodes[t.ch[1]].size;
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  if (need > 0.5 * (double)fr) return HSS_OK;
+  std::vector<ExtractJob> ex;
+  for (auto& t : H->nodes) {
+    if (t.leaf || t.state == HSS_COMPRESSED) continue;
+    const Node& a = H->nodes[t.ch[0]];
+    const Node& b = H->nodes[t.ch[1]];
+    t.F12 = (double*)H->arena.alloc(sizeof(double) * (size_t)a.size * b.size);
+    t.F21 = (double*)H->arena.alloc(sizeof(double) * (size_t)b.size * a.size);
+    if (!t.F12 || !t.F21) return fail(HSS_ERR_NOMEM, "device allocation of the uncompressed blocks failed");
+    ex.push_back({nullptr, a.lo, a.size, nullptr, b.lo, b.size, t.F12, a.size});
+    ex.push_back({nullptr, b.lo, b.size, nullptr, a.lo, a.size, t.F21, b.size});
+  }
+  CK(H->timer.mark(PH_MERGE, st));
+  CKS(extract_blocks(H, ex, st));
+  H->partial = true;
   return HSS_OK;
 }
 
@@ -1288,6 +1350,30 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     CKS(upload(H, H->leaf_lo, lb.data(), sizeof(int) * lb.size(), st));
   }
   CKS(upload(H, H->iota, io.data(), sizeof(int) * n, st));
+  if (o->op) {
+    // the leaf blocks D_tau = A(I_tau, I_tau) first, packed: every sampling
+    // pass removes D_tau R(I_tau) from the operator's product (Algorithm 2)
+    std::vector<long long> off;
+    long long tot = 0;
+    for (auto& t : H->nodes)
+      if (t.leaf) {
+        off.push_back(tot);
+        tot += (long long)t.size * t.size;
+      }
+    H->leaf_D = (double*)H->arena.alloc(sizeof(double) * (size_t)tot);
+    H->leaf_doff = (long long*)H->arena.alloc(sizeof(long long) * off.size());
+    if (!H->leaf_D || !H->leaf_doff) return fail(HSS_ERR_NOMEM, "device allocation of the leaf blocks failed");
+    CKS(upload(H, H->leaf_doff, off.data(), sizeof(long long) * off.size(), st));
+    std::vector<ExtractJob> ex;
+    size_t q = 0;
+    for (auto& t : H->nodes)
+      if (t.leaf) {
+        t.D = H->leaf_D + off[q++];
+        ex.push_back({nullptr, t.lo, t.size, nullptr, t.lo, t.size, t.D, t.size});
+      }
+    CK(H->timer.mark(PH_MERGE, st));
+    CKS(extract_blocks(H, ex, st));
+  }
   CK(cudaMemsetAsync(H->d_flag, 0, 256, st));
 
   CK(H->timer.mark(PH_OTHER, st));
@@ -1311,10 +1397,11 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     CK(cudaFreeAsync(H->packA, st));
     H->packA = nullptr;
   }
+  if (!H->converged) CKS(keep_dense_blocks(H, st));
   CKS(readback(H, H->d_flag + 3, sizeof(int), st));
   if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "tensor-core tile product gave up waiting (code %d)", H->h_pinned[0]);
   H->d_final = d;
-  H->usable = H->converged != 0;
+  H->usable = H->converged != 0 || H->partial;
   double ph[PH_N];
   H->timer.sum(ph, PH_N);
   H->st.ms_sample = ph[PH_SAMPLE];
@@ -1409,9 +1496,12 @@ hss_status hss_compress(const hss_source* A, const hss_opts* o, void* stream, hs
   if (o->precision < HSS_PREC_FP64 || o->precision > HSS_PREC_BF16X3)
     return fail(HSS_ERR_ARG, "unknown precision %d", o->precision);
   if (!(o->rtol >= 0.0) || !(o->atol >= 0.0)) return fail(HSS_ERR_ARG, "tolerances must be >= 0");
+  if (o->wait_limit_ns < 0) return fail(HSS_ERR_ARG, "wait_limit_ns must be >= 0");
   if (o->oversample_p < 0) return fail(HSS_ERR_ARG, "oversample_p must be >= 0");
   if (o->op && (!o->op->apply || o->precision != HSS_PREC_FP64))
     return fail(HSS_ERR_ARG, "a user operator needs an apply function and HSS_PREC_FP64");
+  if (A->kind == HSS_SRC_EXTRACT && !o->op)
+    return fail(HSS_ERR_ARG, "an extraction source is sampled through a user operator (opts->op)");
   if (o->criterion != HSS_CRIT_NEW && o->criterion != HSS_CRIT_HMT)
     return fail(HSS_ERR_ARG, "unknown criterion %d", o->criterion);
   if (o->criterion == HSS_CRIT_HMT) {
@@ -1784,7 +1874,7 @@ hss_status hss_export_node(hss_matrix H, int node, int* Jr, int* Jc, int* Pr, in
 
 hss_status hss_to_dense(hss_matrix H, double* out, long long ld, void* stream) {
   if (!H || !out) return fail(HSS_ERR_ARG, "NULL argument");
-  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators (not converged)");
+  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators");
   if (ld < H->n) return fail(HSS_ERR_ARG, "ld %lld < n %d", ld, H->n);
   cudaStream_t st = (cudaStream_t)stream;
   const int n = H->n, blk = std::min(n, 2048);
@@ -1795,7 +1885,7 @@ hss_status hss_to_dense(hss_matrix H, double* out, long long ld, void* stream) {
     hss_status e = HSS_OK;
     if (launch_identity_block(X, n, c0, w, st) != cudaSuccess)
       e = fail(HSS_ERR_CUDA, "identity block launch failed");
-    if (e == HSS_OK) e = hss_matvec(H, w, X, n, out + (long long)c0 * ld, ld, stream);
+    if (e == HSS_OK) e = hss_matvec(H, w, X, n, out + (long long)c0 * ld, ld, 0, stream);
     if (e != HSS_OK) {
       cudaFreeAsync(X, st);
       return e;
@@ -1807,19 +1897,26 @@ hss_status hss_to_dense(hss_matrix H, double* out, long long ld, void* stream) {
 }
 
 hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, double* Y,
-                      long long ldy, void* stream) {
+                      long long ldy, int transpose, void* stream) {
   if (!H || !X || !Y) return fail(HSS_ERR_ARG, "NULL argument");
-  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators (not converged)");
+  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators");
   if (nrhs < 0 || ldx < H->n || ldy < H->n) return fail(HSS_ERR_ARG, "bad nrhs / leading dimension");
+  if (transpose != 0 && transpose != 1) return fail(HSS_ERR_ARG, "transpose must be 0 or 1");
   if (nrhs == 0) return HSS_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  const bool tr = transpose != 0;
   const int nn = (int)H->nodes.size();
-  // per-node x^ (kc x nrhs) and y^ (kr x nrhs), row-major (row stride nrhs)
+  // H^T has the roles of U and V exchanged, D^T at the leaves and
+  // B12' = B21^T, B21' = B12^T: the up-sweep runs with the "in" side
+  // (V for H, U for H^T), the down-sweep with the "out" side
+  auto in_side = [&](const Node& t) -> const Side& { return tr ? t.r : t.c; };
+  auto out_side = [&](const Node& t) -> const Side& { return tr ? t.c : t.r; };
+  // per-node x^ (in-side k x nrhs) and y^ (out-side k x nrhs), row-major
   std::vector<size_t> offx(nn), offy(nn);
   size_t tot = 0;
   for (int i = 1; i < nn; ++i) {
-    offx[i] = tot; tot += (size_t)H->nodes[i].c.k * nrhs;
-    offy[i] = tot; tot += (size_t)H->nodes[i].r.k * nrhs;
+    offx[i] = tot; tot += (size_t)in_side(H->nodes[i]).k * nrhs;
+    offy[i] = tot; tot += (size_t)out_side(H->nodes[i]).k * nrhs;
   }
   double* buf = nullptr;
   CK(cudaMallocAsync((void**)&buf, sizeof(double) * std::max<size_t>(tot, 1), st));
@@ -1831,10 +1928,10 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
     std::vector<GemmJob> jobs;
     for (int id : H->by_level[lev]) {
       Node& t = H->nodes[id];
-      const Side& s = t.c;
+      const Side& s = in_side(t);
       if (s.k <= 0) continue;
       Opnd x = t.leaf ? opnd(X + t.lo, 1, ldx)
-                      : opnd(xh(t.ch[0]), R_, 1, nullptr, xh(t.ch[1]), H->nodes[t.ch[0]].c.k);
+                      : opnd(xh(t.ch[0]), R_, 1, nullptr, xh(t.ch[1]), in_side(H->nodes[t.ch[0]]).k);
       GemmJob j = gemm_job();
       j.M = s.k; j.N = nrhs; j.K = s.m - s.k;
       j.C0 = x; j.C0.rows = s.piv; j.beta = 1.0;
@@ -1846,7 +1943,9 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
     hss_status e = run_gemms(H, jobs, st);
     if (e != HSS_OK) { cudaFreeAsync(buf, st); return e; }
   }
-  // down-sweep
+  // down-sweep; nodes that are not COMPRESSED (a partial result) couple
+  // their children through the dense blocks instead (after the leaves)
+  std::vector<std::vector<GemmJob>> dense(H->max_level + 1);
   for (int lev = 0; lev < H->max_level; ++lev) {
     std::vector<GemmJob> p0, p1;
     for (int id : H->by_level[lev]) {
@@ -1856,36 +1955,66 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
       const Node& na = H->nodes[a];
       const Node& nb = H->nodes[b];
       const bool root = (id == 0);
-      if (!root && t.r.k > 0) {
+      const Side& ts = out_side(t);
+      if (t.state != HSS_COMPRESSED) {
+        // y^ of the children starts at zero; Y(I_nu1) += A12 X(I_nu2),
+        // Y(I_nu2) += A21 X(I_nu1) (transposed: A21^T, A12^T)
+        for (int c : {a, b}) {
+          const Side& cs = out_side(H->nodes[c]);
+          if (cs.k <= 0) continue;
+          GemmJob z = gemm_job();
+          z.M = cs.k; z.N = nrhs; z.K = 0; z.alpha = 0.0;
+          z.C = yh(c); z.c_rs = R_; z.c_cs = 1;
+          p1.push_back(z);
+        }
+        for (int q = 0; q < 2; ++q) {
+          const Node& to = q ? nb : na;
+          const Node& from = q ? na : nb;
+          GemmJob g = gemm_job();
+          g.M = to.size; g.N = nrhs; g.K = from.size;
+          // A(I_to, I_from): F12 (to = nu1) or F21, col-major ld |I_to|;
+          // its transpose is the other block read across
+          const double* F = tr ? (q ? t.F12 : t.F21) : (q ? t.F21 : t.F12);
+          g.A = tr ? opnd(F, from.size, 1) : opnd(F, 1, to.size);
+          g.B = opnd(X + from.lo, 1, ldx);
+          g.gamma = 1.0;
+          g.C = Y + to.lo; g.c_rs = 1; g.c_cs = ldy;
+          dense[lev].push_back(g);
+        }
+        continue;
+      }
+      if (!root && ts.k > 0) {
         // [y^_nu1; y^_nu2] = U_tau y^_tau, U = Pi [I; Xr^T]
         GemmJob c = gemm_job();
-        c.M = t.r.k; c.N = nrhs; c.K = 0;
+        c.M = ts.k; c.N = nrhs; c.K = 0;
         c.C0 = opnd(yh(id), R_, 1); c.beta = 1.0;
-        c.C = yh(a); c.C2 = yh(b); c.c_split = na.r.k; c.c_rows = t.r.piv;
+        c.C = yh(a); c.C2 = yh(b); c.c_split = out_side(na).k; c.c_rows = ts.piv;
         c.c_rs = R_; c.c_cs = 1;
         p0.push_back(c);
-        if (t.r.m > t.r.k) {
+        if (ts.m > ts.k) {
           GemmJob g = gemm_job();
-          g.M = t.r.m - t.r.k; g.N = nrhs; g.K = t.r.k;
-          g.A = opnd(t.r.X, std::max(t.r.k, 1), 1);
+          g.M = ts.m - ts.k; g.N = nrhs; g.K = ts.k;
+          g.A = opnd(ts.X, std::max(ts.k, 1), 1);
           g.B = opnd(yh(id), R_, 1);
-          g.C = yh(a); g.C2 = yh(b); g.c_split = na.r.k; g.c_rows = t.r.piv + t.r.k;
+          g.C = yh(a); g.C2 = yh(b); g.c_split = out_side(na).k; g.c_rows = ts.piv + ts.k;
           g.c_rs = R_; g.c_cs = 1;
           p0.push_back(g);
         }
       }
-      const double gam = (root || t.r.k == 0) ? 0.0 : 1.0;
-      // y^_nu1 (+)= B12 x^_nu2 ; y^_nu2 (+)= B21 x^_nu1
+      const double gam = (root || ts.k == 0) ? 0.0 : 1.0;
+      // y^_nu1 (+)= B12 x^_nu2 ; y^_nu2 (+)= B21 x^_nu1  (transposed:
+      // B21^T x^_nu2 and B12^T x^_nu1; B12 is kr(nu1) x kc(nu2), ld max(kr(nu1), 1))
+      const int ld12 = std::max(na.r.k, 1), ld21 = std::max(nb.r.k, 1);
       GemmJob g1 = gemm_job();
-      g1.M = na.r.k; g1.N = nrhs; g1.K = nb.c.k;
-      g1.A = opnd(t.B12, 1, std::max(na.r.k, 1));
+      g1.M = out_side(na).k; g1.N = nrhs; g1.K = in_side(nb).k;
+      g1.A = tr ? opnd(t.B21, ld21, 1) : opnd(t.B12, 1, ld12);
       g1.B = opnd(xh(b), R_, 1);
       g1.gamma = gam;
       g1.C = yh(a); g1.c_rs = R_; g1.c_cs = 1;
       p1.push_back(g1);
       GemmJob g2 = gemm_job();
-      g2.M = nb.r.k; g2.N = nrhs; g2.K = na.c.k;
-      g2.A = opnd(t.B21, 1, std::max(nb.r.k, 1));
+      g2.M = out_side(nb).k; g2.N = nrhs; g2.K = in_side(na).k;
+      g2.A = tr ? opnd(t.B12, ld12, 1) : opnd(t.B21, 1, ld21);
       g2.B = opnd(xh(a), R_, 1);
       g2.gamma = gam;
       g2.C = yh(b); g2.c_rs = R_; g2.c_cs = 1;
@@ -1895,37 +2024,121 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
     if (e == HSS_OK) e = run_gemms(H, p1, st);
     if (e != HSS_OK) { cudaFreeAsync(buf, st); return e; }
   }
-  // leaves: Y(I) = D X(I) + U y^
+  // leaves: Y(I) = D X(I) + U y^  (D^T and V y^ transposed)
   std::vector<GemmJob> l0, l1;
   for (int id = 0; id < nn; ++id) {
     Node& t = H->nodes[id];
     if (!t.leaf) continue;
     GemmJob g = gemm_job();
     g.M = t.size; g.N = nrhs; g.K = t.size;
-    g.A = opnd(t.D, 1, t.size);
+    g.A = tr ? opnd(t.D, t.size, 1) : opnd(t.D, 1, t.size);
     g.B = opnd(X + t.lo, 1, ldx);
     g.C = Y + t.lo; g.c_rs = 1; g.c_cs = ldy;
     l0.push_back(g);
-    if (id == 0 || t.r.k <= 0) continue;
+    const Side& ts = out_side(t);
+    if (id == 0 || ts.k <= 0) continue;
     GemmJob c = gemm_job();
-    c.M = t.r.k; c.N = nrhs; c.K = 0;
+    c.M = ts.k; c.N = nrhs; c.K = 0;
     c.C0 = opnd(yh(id), R_, 1); c.beta = 1.0; c.gamma = 1.0;
-    c.C = Y + t.lo; c.c_rows = t.r.piv; c.c_rs = 1; c.c_cs = ldy;
+    c.C = Y + t.lo; c.c_rows = ts.piv; c.c_rs = 1; c.c_cs = ldy;
     l1.push_back(c);
-    if (t.r.m > t.r.k) {
+    if (ts.m > ts.k) {
       GemmJob e2 = gemm_job();
-      e2.M = t.r.m - t.r.k; e2.N = nrhs; e2.K = t.r.k;
-      e2.A = opnd(t.r.X, std::max(t.r.k, 1), 1);
+      e2.M = ts.m - ts.k; e2.N = nrhs; e2.K = ts.k;
+      e2.A = opnd(ts.X, std::max(ts.k, 1), 1);
       e2.B = opnd(yh(id), R_, 1);
       e2.gamma = 1.0;
-      e2.C = Y + t.lo; e2.c_rows = t.r.piv + t.r.k; e2.c_rs = 1; e2.c_cs = ldy;
+      e2.C = Y + t.lo; e2.c_rows = ts.piv + ts.k; e2.c_rs = 1; e2.c_cs = ldy;
       l1.push_back(e2);
     }
   }
   hss_status e = run_gemms(H, l0, st);
   if (e == HSS_OK) e = run_gemms(H, l1, st);
+  // dense couplings of a partial result, one launch per level (the blocks
+  // of one level write disjoint rows of Y)
+  for (int lev = 0; lev <= H->max_level && e == HSS_OK; ++lev) e = run_gemms(H, dense[lev], st);
   cudaFreeAsync(buf, st);
   return e;
+}
+
+hss_status hss_get_entries(hss_matrix H, int nr, const int* I, int nc, const int* J, double* out, long long ldo,
+                           void* stream) {
+  if (!H) return fail(HSS_ERR_ARG, "NULL handle");
+  if (!H->usable) return fail(HSS_ERR_ARG, "handle holds no usable generators");
+  if (nr < 0 || nc < 0 || ldo < std::max(nr, 1)) return fail(HSS_ERR_ARG, "bad sizes (nr %d, nc %d, ldo %lld)", nr, nc, ldo);
+  if (nr == 0 || nc == 0) return HSS_OK;
+  if (!I || !J || !out) return fail(HSS_ERR_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nn = (int)H->nodes.size(), n = H->n;
+  int kcap = 1;
+  size_t ninv = 0;
+  std::vector<int> leaf_of(n);
+  for (int id = 0; id < nn; ++id) {
+    const Node& t = H->nodes[id];
+    kcap = std::max(kcap, std::max(t.r.k, t.c.k));
+    if (id) ninv += (size_t)t.r.m + (size_t)t.c.m;
+    if (t.leaf)
+      for (int i = t.lo; i < t.lo + t.size; ++i) leaf_of[i] = id;
+  }
+  const int lp1 = H->max_level + 1;
+  // rows and columns in chunks whose path vectors take at most 512 MB each
+  // (and at most 65535 columns: one grid row per column)
+  const long long per = (long long)lp1 * kcap;
+  const int chunk =
+      (int)std::max<long long>(1, std::min<long long>({(long long)std::max(nr, nc), (64LL << 20) / per, 65535LL}));
+  const size_t b_nodes = Scratch::rnd(sizeof(EntryNode) * nn), b_inv = Scratch::rnd(sizeof(int) * std::max<size_t>(ninv, 1)),
+               b_leaf = Scratch::rnd(sizeof(int) * n), b_vec = Scratch::rnd(sizeof(double) * (size_t)chunk * per);
+  char* buf = nullptr;
+  CK(cudaMallocAsync((void**)&buf, b_nodes + b_inv + b_leaf + 2 * b_vec + 256, st));
+  EntryNode* dn = (EntryNode*)buf;
+  int* inv = (int*)(buf + b_nodes);
+  int* dleaf = (int*)(buf + b_nodes + b_inv);
+  double* Wrow = (double*)(buf + b_nodes + b_inv + b_leaf);
+  double* Vcol = Wrow + (size_t)chunk * per;
+  int* err = (int*)(buf + b_nodes + b_inv + b_leaf + 2 * b_vec);
+  std::vector<EntryNode> hn(nn);
+  size_t o = 0;
+  for (int id = 0; id < nn; ++id) {
+    const Node& t = H->nodes[id];
+    EntryNode& e = hn[id];
+    memset(&e, 0, sizeof e);
+    e.lo = t.lo; e.size = t.size; e.level = t.level; e.parent = t.parent; e.ch0 = t.ch[0]; e.ch1 = t.ch[1];
+    e.state = t.state;
+    e.D = t.D; e.B12 = t.B12; e.B21 = t.B21; e.F12 = t.F12; e.F21 = t.F21;
+    if (id && t.state == HSS_COMPRESSED) {
+      e.kr = t.r.k; e.kc = t.c.k; e.mr = t.r.m; e.mc = t.c.m;
+      e.pivr = t.r.piv; e.pivc = t.c.piv; e.Xr = t.r.X; e.Xc = t.c.X;
+      e.ipivr = inv + o; o += t.r.m;
+      e.ipivc = inv + o; o += t.c.m;
+    }
+  }
+  hss_status s = HSS_OK;
+  auto run = [&]() -> hss_status {
+    CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(inv, 0xff, sizeof(int) * std::max<size_t>(ninv, 1), st));   // -1: no position
+    CKS(upload(H, dn, hn.data(), sizeof(EntryNode) * nn, st));
+    CKS(upload(H, dleaf, leaf_of.data(), sizeof(int) * n, st));
+    CK(launch_inv_piv(dn, nn, err, st));
+    for (int c0 = 0; c0 < nc; c0 += chunk) {
+      const int w = std::min(chunk, nc - c0);
+      CK(launch_entry_paths(dn, dleaf, n, J + c0, w, Vcol, kcap, lp1, 1, err, st));
+      for (int r0 = 0; r0 < nr; r0 += chunk) {
+        const int h = std::min(chunk, nr - r0);
+        CK(launch_entry_paths(dn, dleaf, n, I + r0, h, Wrow, kcap, lp1, 0, err, st));
+        CK(launch_entry_pairs(dn, dleaf, n, I + r0, h, J + c0, w, Wrow, Vcol, kcap, lp1,
+                              out + r0 + (long long)c0 * ldo, ldo, st));
+      }
+    }
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr == 1) return fail(HSS_ERR_ARG, "an index of I or J is outside [0, %d)", n);
+    if (herr) return fail(HSS_ERR_CUDA, "inconsistent pivots in the handle (code %d)", herr);
+    return HSS_OK;
+  };
+  s = run();
+  cudaFreeAsync(buf, st);
+  return s;
 }
 
 hss_status hss_rcb_order(const double* points, int n, int dim, long long ld, int leaf, int* perm) {
@@ -1972,6 +2185,7 @@ hss_status hss_random_normal(unsigned long long seed, int n, int col0, int ncols
 hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int ncols, const double* R,
                               long long ldr, double* Sr, double* Sc, long long lds, void* stream) {
   CKS(check_source(A));
+  if (A->kind == HSS_SRC_EXTRACT) return fail(HSS_ERR_ARG, "sampling needs a source with entries on the device");
   const int n = A->n;
   if (leaf < 1 || ncols < 0 || !R || ldr < n || lds < ncols)
     return fail(HSS_ERR_ARG, "bad arguments to hss_sample_offdiag");
@@ -2134,6 +2348,7 @@ extern "C" hss_status hss_sample_offdiag_noalloc(const hss_source* A, int leaf, 
                                                  double* Sr, double* Sc, long long lds,
                                                  void* stream) {
   CKS(check_source(A));
+  if (A->kind == HSS_SRC_EXTRACT) return fail(HSS_ERR_ARG, "sampling needs a source with entries on the device");
   const int n = A->n;
   if (leaf < 1 || ncols < 0 || !R || ldr < n || lds < ncols)
     return fail(HSS_ERR_ARG, "bad arguments to hss_sample_offdiag_noalloc");

@@ -103,6 +103,7 @@ struct QrcpJob {
   double* redt;         // 2 P pending-update coefficients of the candidates
   double* xfer;         // 2 x 4: the column moved between CTAs at a step (id, tw,
                         // norm^2, orig), two steps in flight
+  unsigned long long wait_ns;  // bound of one group-barrier wait (%globaltimer ns)
 };
 
 // One Incrementing block test on one side of a node (Algorithm 5):
@@ -128,6 +129,7 @@ struct IncJob {
   int P;
   unsigned* bar;        // group barrier counter, zero before the launch
   double* part;         // 2 x P x (b + 2) partial sums
+  unsigned long long wait_ns;  // bound of one group-barrier wait (%globaltimer ns)
 };
 
 // Gather of sub-blocks of A: out(i, j) = A(I[i], J[j]) (col-major, ld ldo);
@@ -136,6 +138,26 @@ struct ExtractJob {
   const int* I; int i0, mi;
   const int* J; int j0, nj;
   double* out; long long ldo;
+};
+
+// One node of a compressed handle as the entry kernels read it
+// (k_entries.cu): tree, state, ranks, inverse pivot orders (position of each
+// sample row in the pivot order), X of U and V, and the blocks D, B12, B21
+// (F12, F21: the dense blocks of a node left uncompressed).
+struct EntryNode {
+  int lo, size, level, parent, ch0, ch1, state;
+  int kr, kc, mr, mc;
+  const int* pivr;
+  const int* pivc;
+  int* ipivr;
+  int* ipivc;
+  const double* Xr;
+  const double* Xc;
+  const double* D;
+  const double* B12;
+  const double* B21;
+  const double* F12;
+  const double* F21;
 };
 
 // Launch wrappers (return cudaError_t of the launch).
@@ -189,10 +211,11 @@ cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas,
 // A(i, j) R(j, q) (trans = 0) or A(j, i) (trans = 1) for i < n, q < w: the
 // leaf diagonal blocks removed from the user's product T (col-major, ld ldt)
 // into the row-major samples S (ld lds, column offset applied by the caller).
-// leaf_lo: nleaves + 1 row bounds of the leaves; s.leaf_id gives each row's leaf.
-cudaError_t launch_leaf_diag_sub(const SrcDev& s, const int* leaf_lo, int n, int w, const double* R, long long ldr,
-                                 const double* T, long long ldt, double* S, long long lds, int trans,
-                                 cudaStream_t st);
+// Dp + doff[L]: leaf L's block D (col-major, ld = its size); leaf_id gives
+// each row's leaf, leaf_lo the nleaves + 1 row bounds.
+cudaError_t launch_leaf_diag_sub(const double* Dp, const long long* doff, const int* leaf_id, const int* leaf_lo,
+                                 int n, int w, const double* R, long long ldr, const double* T, long long ldt,
+                                 double* S, long long lds, int trans, cudaStream_t st);
 cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
 // The same test with the rows of each side split over a group of P CTAs
 // (map[cta] = (job, rank), cooperative launch); b_max: largest block, at
@@ -207,5 +230,13 @@ cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int 
 cudaError_t launch_identity_block(double* X, int n, int c0, int w, cudaStream_t st);
 cudaError_t launch_gather_int(const int* src, const int* idx, int* dst, int cnt,
                               const int* src2, int split, cudaStream_t st);
+// entries of a compressed handle (k_entries.cu); err: 1 = index out of
+// range, 2 = pivot out of range
+cudaError_t launch_inv_piv(const EntryNode* nodes, int nn, int* err, cudaStream_t st);
+cudaError_t launch_entry_paths(const EntryNode* nodes, const int* leaf_of, int n, const int* idx, int count,
+                               double* out, int kcap, int lp1, int side, int* err, cudaStream_t st);
+cudaError_t launch_entry_pairs(const EntryNode* nodes, const int* leaf_of, int n, const int* I, int nr, const int* J,
+                               int nc, const double* Wrow, const double* Vcol, int kcap, int lp1, double* out,
+                               long long ldo, cudaStream_t st);
 
 }  // namespace hss

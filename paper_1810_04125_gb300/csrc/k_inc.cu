@@ -189,9 +189,9 @@ __device__ __forceinline__ unsigned ld_acq(const unsigned* p) {
   return v;
 }
 
-// bounded group barrier (about 2 s, or as soon as another CTA recorded an
-// error); false when it gave up
-__device__ bool gbar(unsigned* bar, int P, unsigned& epoch, int* err, int* s_ok) {
+// bounded group barrier (wait_ns of %globaltimer, about 2 s by default, or
+// as soon as another CTA recorded an error); false when it gave up
+__device__ bool gbar(unsigned* bar, int P, unsigned& epoch, int* err, int* s_ok, unsigned long long wait_ns) {
   __syncthreads();
   if (P == 1) return true;
   if (threadIdx.x == 0) {
@@ -202,9 +202,9 @@ __device__ bool gbar(unsigned* bar, int P, unsigned& epoch, int* err, int* s_ok)
     int ok = 1;
     const uint64_t t0 = gtime();
     for (unsigned it = 1; ld_acq(bar) < target; ++it) {
-      if ((it & 63u) == 0) {
+      if ((it & 63u) == 0 || it == 1) {   // the first spin too: a short limit is seen at once
         if (*(volatile int*)err) { ok = 0; break; }
-        if (gtime() - t0 > 2000000000ull) { atomicCAS(err, 0, 7); ok = 0; break; }
+        if (gtime() - t0 > wait_ns) { atomicCAS(err, 0, 7); ok = 0; break; }
       }
     }
     __threadfence();
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(NT, 2) k_inc_group(const IncJob* __restrict__ 
       if ((tid & 31) == 0) __stcg(slot(parity, rank) + 2 + c, w);
     }
   }
-  if (!gbar(jb.bar, P, epoch, err, &s_ok)) return;
+  if (!gbar(jb.bar, P, epoch, err, &s_ok, jb.wait_ns)) return;
   double nS = 0.0, nSh = 0.0;
   for (int q = 0; q < P; ++q) { nS += __ldcg(slot(parity, q)); nSh += __ldcg(slot(parity, q) + 1); }
   double est = 0.0;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(NT, 2) k_inc_group(const IncJob* __restrict__ 
       __stcg(slot(parity, rank), s);
       __stcg(slot(parity, rank) + 1, (j >= r0 && j < r0 + nr) ? V[(j - r0) + (size_t)j * RB] : 0.0);
     }
-    if (!gbar(jb.bar, P, epoch, err, &s_ok)) return;
+    if (!gbar(jb.bar, P, epoch, err, &s_ok, jb.wait_ns)) return;
     if (tid == 0) {
       double ss = 0.0, x0 = 0.0;
       for (int q = 0; q < P; ++q) { ss += __ldcg(slot(parity, q)); x0 += __ldcg(slot(parity, q) + 1); }
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(NT, 2) k_inc_group(const IncJob* __restrict__ 
         w = warp_sum(w);
         if ((tid & 31) == 0) __stcg(slot(parity, rank) + c, w);
       }
-      if (!gbar(jb.bar, P, epoch, err, &s_ok)) return;
+      if (!gbar(jb.bar, P, epoch, err, &s_ok, jb.wait_ns)) return;
       for (int c = tid; c < nc; c += NT) {
         double w = 0.0;
         for (int q = 0; q < P; ++q) w += __ldcg(slot(parity, q) + c);
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(NT, 2) k_inc_group(const IncJob* __restrict__ 
       w = warp_sum(w);
       if ((tid & 31) == 0) __stcg(slot(parity, rank) + c, w);
     }
-    if (!gbar(jb.bar, P, epoch, err, &s_ok)) return;
+    if (!gbar(jb.bar, P, epoch, err, &s_ok, jb.wait_ns)) return;
     for (int c = tid; c < nc; c += NT) {
       double w = 0.0;
       for (int q = 0; q < P; ++q) w += __ldcg(slot(parity, q) + c);

@@ -29,10 +29,14 @@ __global__ void k_extract(SrcDev src, const ExtractJob* __restrict__ jobs) {
 
 // With a user sampling operator the leaf diagonal blocks come off the
 // user's product (Algorithm 2 at a leaf: (A R)(I_tau) - D_tau R(I_tau)): a
-// CTA takes a 32 x 32 tile (rows i0.., columns q0..), evaluates its leaf
-// block products in FP64 from the source's entries and writes the tile
-// transposed into the row-major samples through shared memory.
-__global__ void __launch_bounds__(256) k_leaf_diag_sub(SrcDev s, const int* __restrict__ leaf_lo, int n, int w,
+// CTA takes a 32 x 32 tile (rows i0.., columns q0..), forms its rows' leaf
+// block products in FP64 from the packed blocks D (leaf L at Dp + doff[L],
+// col-major) and writes the tile transposed into the row-major samples
+// through shared memory.
+__global__ void __launch_bounds__(256) k_leaf_diag_sub(const double* __restrict__ Dp,
+                                                     const long long* __restrict__ doff,
+                                                     const int* __restrict__ leaf_id,
+                                                     const int* __restrict__ leaf_lo, int n, int w,
                                                      const double* __restrict__ R, long long ldr,
                                                      const double* __restrict__ T, long long ldt,
                                                      double* __restrict__ S, long long lds, int trans) {
@@ -43,11 +47,15 @@ __global__ void __launch_bounds__(256) k_leaf_diag_sub(SrcDev s, const int* __re
     const int i = i0 + tx, q = q0 + qq;
     double v = 0.0;
     if (i < n && q < w) {
-      const int L = s.leaf_id[i];
-      const int lo = leaf_lo[L], hi = leaf_lo[L + 1];
+      const int L = leaf_id[i];
+      const int lo = leaf_lo[L], hi = leaf_lo[L + 1], m = hi - lo;
+      const double* D = Dp + doff[L];
       const double* Rq = R + (long long)q * ldr;
       double acc = 0.0;
-      for (int j = lo; j < hi; ++j) acc = __fma_rn(trans ? entry(s, j, i) : entry(s, i, j), Rq[j], acc);
+      // A(i, j) = D(i - lo, j - lo); the transposed product takes A(j, i)
+      for (int j = lo; j < hi; ++j)
+        acc = __fma_rn(trans ? D[(j - lo) + (long long)(i - lo) * m] : D[(i - lo) + (long long)(j - lo) * m], Rq[j],
+                       acc);
       v = T[(long long)q * ldt + i] - acc;
     }
     tile[qq][tx] = v;
@@ -103,17 +111,18 @@ cudaError_t launch_identity_block(double* X, int n, int c0, int w, cudaStream_t 
 cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int njobs, int max_tiles,
                            cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
+  if (src.kind < HSS_SRC_DENSE || src.kind > HSS_SRC_LAPLACE) return cudaErrorInvalidValue;   // no entries on the device
   int gx = max_tiles < 1 ? 1 : (max_tiles > 64 ? 64 : max_tiles);
   k_extract<<<dim3(gx, njobs), 256, 0, st>>>(src, jobs_dev);
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_diag_sub(const SrcDev& s, const int* leaf_lo, int n, int w, const double* R, long long ldr,
-                                 const double* T, long long ldt, double* S, long long lds, int trans,
-                                 cudaStream_t st) {
+cudaError_t launch_leaf_diag_sub(const double* Dp, const long long* doff, const int* leaf_id, const int* leaf_lo,
+                                 int n, int w, const double* R, long long ldr, const double* T, long long ldt,
+                                 double* S, long long lds, int trans, cudaStream_t st) {
   if (n <= 0 || w <= 0) return cudaSuccess;
   dim3 grid((n + 31) / 32, (w + 31) / 32);
-  k_leaf_diag_sub<<<grid, 256, 0, st>>>(s, leaf_lo, n, w, R, ldr, T, ldt, S, lds, trans);
+  k_leaf_diag_sub<<<grid, 256, 0, st>>>(Dp, doff, leaf_id, leaf_lo, n, w, R, ldr, T, ldt, S, lds, trans);
   return cudaGetLastError();
 }
 

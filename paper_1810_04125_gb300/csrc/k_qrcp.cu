@@ -87,7 +87,8 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 // Group barrier of the P CTAs of a job (a plain __syncthreads when P == 1).
-__device__ bool group_barrier(unsigned* bar, int P, unsigned& epoch, int* err, int* s_ok) {
+__device__ bool group_barrier(unsigned* bar, int P, unsigned& epoch, int* err, int* s_ok,
+                              unsigned long long wait_ns) {
   __syncthreads();
   if (P == 1) return true;
   if (threadIdx.x == 0) {
@@ -98,9 +99,9 @@ __device__ bool group_barrier(unsigned* bar, int P, unsigned& epoch, int* err, i
     int ok = 1;
     const uint64_t t0 = gtimer();
     for (unsigned it = 1; ld_acquire(bar) < target; ++it) {
-      if ((it & 63u) == 0) {
+      if ((it & 63u) == 0 || it == 1) {   // the first spin too: a short limit is seen at once
         if (*(volatile int*)err) { ok = 0; break; }
-        if (gtimer() - t0 > 2000000000ull) { atomicCAS(err, 0, 6); ok = 0; break; }
+        if (gtimer() - t0 > wait_ns) { atomicCAS(err, 0, 6); ok = 0; break; }
       }
     }
     __threadfence();
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
       s_twp = twc;
     }
     // ---- (b) the pivot of step j over the group
-    if (!group_barrier(jb.bar, P, epoch, err, &s_ok)) return;
+    if (!group_barrier(jb.bar, P, epoch, err, &s_ok, jb.wait_ns)) return;
     if (P > 1 && warp == 1 && lane < 4) s_xf[lane] = __ldcg(jb.xfer + (j & 1) * 4 + lane);
     if (P > 1 && warp == 0) {
       unsigned long long kk = 0ull;
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict
   }
 
   // every R entry, pivot and liveness flag of the group visible before the solve
-  if (!group_barrier(jb.bar, P, epoch, err, &s_ok)) return;
+  if (!group_barrier(jb.bar, P, epoch, err, &s_ok, jb.wait_ns)) return;
 
   int accepted = 1;
   if (jb.rule == 1) accepted = stopped ? (k <= d - jb.p) : (k == m);

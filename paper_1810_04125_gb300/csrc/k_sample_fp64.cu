@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(256) k_sample_fp64(SrcDev src, int ncols, cons
 
 cudaError_t launch_sample_fp64(const SrcDev& src, int ncols, const double* R, long long ldr,
                                double* Sr, double* Sc, long long lds, cudaStream_t st) {
+  if (src.kind < HSS_SRC_DENSE || src.kind > HSS_SRC_LAPLACE) return cudaErrorInvalidValue;   // no entries on the device
   if (src.n <= 0 || ncols <= 0) return cudaSuccess;
   dim3 grid((src.n + BM - 1) / BM, (ncols + BN - 1) / BN);
   if (Sr) k_sample_fp64<false><<<grid, 256, 0, st>>>(src, ncols, R, ldr, Sr, lds);

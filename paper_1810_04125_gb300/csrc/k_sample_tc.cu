@@ -482,6 +482,7 @@ size_t packed_r_bytes(int n, int ncols, int precision) {
 }
 
 cudaError_t launch_pack_a(const SrcDev& src, int leaf, int precision, void* out, cudaStream_t st) {
+  if (src.kind < HSS_SRC_DENSE || src.kind > HSS_SRC_LAPLACE) return cudaErrorInvalidValue;   // no entries on the device
   const int n = src.n;
   const int bk = bk_of(precision);
   const int nrb = (n + BM - 1) / BM, nkt = (n + bk - 1) / bk;
@@ -549,6 +550,7 @@ cudaError_t launch_sample_tc_packed(const void* A, const void* Rp, int n, int nc
 cudaError_t launch_sample_tc(const SrcDev& src, int leaf, int precision, int trans, int ncols,
                              const void* Rp, double* S, long long lds, int* err, int* used_atomic,
                              cudaStream_t st) {
+  if (src.kind < HSS_SRC_DENSE || src.kind > HSS_SRC_LAPLACE) return cudaErrorInvalidValue;   // no entries on the device
   const int n = src.n;
   if (n <= 0 || ncols <= 0) return cudaSuccess;
   TcArgs a;

@@ -23,19 +23,27 @@ HSS_ERR_OPERATOR, HSS_ERR_IO = 8, 9
 HSS_DOUBLING, HSS_INCREMENTING = 0, 1
 HSS_CRIT_NEW, HSS_CRIT_HMT = 0, 1
 HSS_PREC_FP64, HSS_PREC_TF32X2, HSS_PREC_BF16X3 = 0, 1, 2
-HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE = 0, 1, 2, 3
+HSS_SRC_DENSE, HSS_SRC_TOEPLITZ, HSS_SRC_GAUSS, HSS_SRC_LAPLACE, HSS_SRC_EXTRACT = 0, 1, 2, 3, 4
 HSS_UNTOUCHED, HSS_PARTIALLY_COMPRESSED, HSS_COMPRESSED = 0, 1, 2
 
-EXPORTS = ["hss_compress", "hss_compress_restart", "hss_compress_batched", "hss_save", "hss_load", "hss_matvec", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
+EXPORTS = ["hss_compress", "hss_compress_restart", "hss_compress_batched", "hss_save", "hss_load", "hss_matvec", "hss_get_entries", "hss_to_dense", "hss_get_stats", "hss_get_node", "hss_export_node",
            "hss_free", "hss_release_cached", "hss_set_tuning", "hss_get_tuning", "hss_status_str",
            "hss_last_error", "hss_rcb_order",
            "hss_random_normal", "hss_sample_offdiag", "hss_sample_offdiag_noalloc"]
 
 
+class hss_block(C.Structure):
+    _fields_ = [("nr", C.c_int), ("nc", C.c_int), ("I", C.c_void_p), ("J", C.c_void_p),
+                ("out", C.c_void_p), ("ldo", C.c_longlong)]
+
+
+EXTRACT_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.POINTER(hss_block), C.c_void_p)
+
+
 class hss_source(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int), ("dim", C.c_int), ("reserved", C.c_int),
                 ("a", C.c_void_p), ("b", C.c_void_p), ("ld", C.c_longlong),
-                ("p0", C.c_double), ("p1", C.c_double)]
+                ("p0", C.c_double), ("p1", C.c_double), ("extract", EXTRACT_FN), ("ctx", C.c_void_p)]
 
 
 APPLY_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_void_p,
@@ -51,7 +59,8 @@ class hss_opts(C.Structure):
                 ("level_tol_scaling", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
                 ("d0", C.c_int), ("dd", C.c_int), ("d_max", C.c_int), ("oversample_p", C.c_int),
                 ("seed", C.c_ulonglong), ("R", C.c_void_p), ("symmetric", C.c_int),
-                ("criterion", C.c_int), ("hmt_alpha", C.c_double), ("op", C.POINTER(hss_operator))]
+                ("criterion", C.c_int), ("hmt_alpha", C.c_double), ("op", C.POINTER(hss_operator)),
+                ("wait_limit_ns", C.c_longlong)]
 
 
 class hss_stats(C.Structure):
@@ -91,7 +100,8 @@ def lib():
         L.hss_compress_batched.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), i, vp, C.POINTER(vp)]
         L.hss_compress_restart.argtypes = [C.POINTER(hss_source), C.POINTER(hss_opts), vp, C.POINTER(vp),
                                            C.POINTER(i)]
-        L.hss_matvec.argtypes = [vp, i, vp, ll, vp, ll, vp]
+        L.hss_matvec.argtypes = [vp, i, vp, ll, vp, ll, i, vp]
+        L.hss_get_entries.argtypes = [vp, i, vp, i, vp, vp, ll, vp]
         L.hss_to_dense.argtypes = [vp, vp, ll, vp]
         L.hss_get_stats.argtypes = [vp, C.POINTER(hss_stats)]
         L.hss_get_node.argtypes = [vp, i, C.POINTER(hss_node_info)]
@@ -182,11 +192,56 @@ def make_source(kind, n, a, b=None, ld=0, dim=0, p0=0.0, p1=0.0):
     return s
 
 
+last_extract_error = None
+
+
+def _device_ints(ptr, count):
+    """A view of `count` int32 entries of device memory owned by the library."""
+    import torch
+
+    class _View:
+        __cuda_array_interface__ = {"shape": (count,), "strides": (4,), "typestr": "<i4",
+                                    "data": (ptr, True), "version": 3}
+    return torch.as_tensor(_View(), device="cuda")
+
+
+def extract_source(n, fn):
+    """hss_source of kind HSS_SRC_EXTRACT around fn(blocks, stream): blocks is
+    a list of (I, J, out) per requested block — I, J int32 device views of
+    the global indices, out a column-major view of the library's buffer — and
+    stream the library's stream (made current); fn enqueues
+    out[i, j] = A[I[i], J[j]] for every block.  An exception becomes a
+    nonzero status (HSS_ERR_OPERATOR); it is kept in last_extract_error."""
+    import torch
+
+    def cb(ctx, nblocks, blocks, stream):
+        global last_extract_error
+        try:
+            st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(st):
+                req = []
+                for q in range(nblocks):
+                    b = blocks[q]
+                    req.append((_device_ints(b.I, b.nr), _device_ints(b.J, b.nc),
+                                _device_matrix(b.out, b.nr, b.nc, b.ldo)))
+                fn(req, st)
+            return 0
+        except Exception as e:   # the status carries the failure back through the C ABI
+            last_extract_error = e
+            return 1
+
+    c = EXTRACT_FN(cb)
+    s = hss_source(HSS_SRC_EXTRACT, n, 0, 0, None, None, 0, 0.0, 0.0, c, None)
+    s._keep = (c, fn)
+    return s
+
+
 def make_opts(leaf, rtol, atol, d0, dd, d_max, strategy, precision=HSS_PREC_FP64, p=10, seed=0,
-              R=None, level_tol_scaling=1, symmetric=0, criterion=0, hmt_alpha=10.0, op=None):
+              R=None, level_tol_scaling=1, symmetric=0, criterion=0, hmt_alpha=10.0, op=None,
+              wait_limit_ns=0):
     o = hss_opts(leaf, strategy, precision, level_tol_scaling, rtol, atol, d0, dd, d_max, p,
                  seed, _ptr(R), int(symmetric), int(criterion), float(hmt_alpha),
-                 C.pointer(op) if op is not None else None)
+                 C.pointer(op) if op is not None else None, int(wait_limit_ns))
     o._keep = (R, op)
     return o
 
@@ -275,13 +330,23 @@ def hss_to_dense(H, out, stream=None):
     _check(lib().hss_to_dense(H.handle, _ptr(out), out.stride(1), _stream(stream)))
 
 
-def hss_matvec(H, X, Y, stream=None):
+def hss_matvec(H, X, Y, stream=None, transpose=False):
+    """Y = H X (or H^T X); X, Y column-major device tensors."""
     if X.dim() == 2 and (X.stride(0) != 1 or Y.stride(0) != 1):
         raise ValueError("hss_matvec needs column-major X and Y (stride(0) == 1)")
     n, nrhs = X.shape[0], (X.shape[1] if X.dim() == 2 else 1)
     ldx = X.stride(1) if X.dim() == 2 else n
     ldy = Y.stride(1) if Y.dim() == 2 else n
-    _check(lib().hss_matvec(H.handle, nrhs, _ptr(X), ldx, _ptr(Y), ldy, _stream(stream)))
+    _check(lib().hss_matvec(H.handle, nrhs, _ptr(X), ldx, _ptr(Y), ldy, int(bool(transpose)), _stream(stream)))
+
+
+def hss_get_entries(H, I, J, out, stream=None):
+    """out (len(I) x len(J), column-major device tensor) = H[I, J]; I, J
+    int32 device tensors."""
+    if out.dim() != 2 or (out.stride(0) != 1 and out.shape[0] > 1):
+        raise ValueError("hss_get_entries needs a column-major 2-D out")
+    _check(lib().hss_get_entries(H.handle, I.numel(), _ptr(I), J.numel(), _ptr(J), _ptr(out),
+                                 max(out.stride(1), out.shape[0], 1), _stream(stream)))
 
 
 def hss_rcb_order(points: np.ndarray, leaf: int) -> np.ndarray:

@@ -109,7 +109,16 @@ def test_argument_validation_without_gpu(hss):
         bad = hss.make_opts(64, 1e-6, 1e-12, 64, 32, 256, **kw)
         assert L.hss_compress(C.byref(s), C.byref(bad), None, C.byref(h)) == hss.HSS_ERR_ARG, kw
     assert h.value is None
-    assert L.hss_matvec(None, 1, None, 1, None, 1, None) == hss.HSS_ERR_ARG
+    assert L.hss_matvec(None, 1, None, 1, None, 1, 0, None) == hss.HSS_ERR_ARG
+    assert L.hss_get_entries(None, 1, None, 1, None, None, 1, None) == hss.HSS_ERR_ARG
+    # an extraction source needs its routine, and a sampling operator
+    s_x = hss.hss_source(hss.HSS_SRC_EXTRACT, 100, 0, 0, None, None, 0, 0.0, 0.0)
+    assert L.hss_compress(C.byref(s_x), C.byref(o), None, C.byref(h)) == hss.HSS_ERR_ARG
+    s_x = hss.extract_source(100, lambda blocks, stream: None)
+    assert L.hss_compress(C.byref(s_x), C.byref(o), None, C.byref(h)) == hss.HSS_ERR_ARG
+    assert b"operator" in L.hss_last_error()
+    assert L.hss_sample_offdiag(C.byref(s_x), 16, 0, 1, 1234, 100, None, None, 1, None) == hss.HSS_ERR_ARG
+    assert L.hss_status_str(hss.HSS_ERR_IO) == b"HSS_ERR_IO"
     hs = (C.c_void_p * 1)()
     assert L.hss_compress_batched(None, None, -1, None, hs) == hss.HSS_ERR_ARG
     assert L.hss_compress_batched(None, C.byref(o), 1, None, hs) == hss.HSS_ERR_ARG
