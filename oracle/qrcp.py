@@ -98,3 +98,29 @@ def interpolative(piv, R, k):
     U[piv[:k], np.arange(k)] = 1.0
     U[piv[k:], :] = X.T
     return J, X, U
+
+
+def near_threshold_count(S: np.ndarray, er: float, ea: float, rule: str, mh: int = 0, nh: int = 0,
+                         band: float = 0.1, noise: float = 0.0) -> int:
+    """Number of singular values of a local sample S (m x d) within +-band
+    of the rank threshold that the ID's rule applies at their position:
+    max(eps_a, eps_r |R_11|) (P4; |R_11| = the largest row norm of S, the
+    first pivot's norm whatever the pivot order), divided by the HMT factor
+    f(j + 1) of eq. RRQRHMTstop under ``rule == "hmt"``.  Where pivot order
+    diverges at near ties, a rank can cross such a value but not more of
+    them than there are (the tie rule of the rank comparison).  ``noise``:
+    a bound on the 2-norm of a perturbation of S (a sample computed in
+    another arithmetic); by Weyl's inequality it moves every singular value
+    by at most that much, so the band widens by it."""
+    sv = np.linalg.svd(np.asarray(S, dtype=np.float64), compute_uv=False)
+    if sv.size == 0:
+        return 0
+    r11 = float(np.max(np.linalg.norm(S, axis=1)))
+    d = S.shape[1]
+    cnt = 0
+    for j, s in enumerate(sv):
+        f = hmt_factor(j + 1, d, mh, nh) if rule == "hmt" else 1.0
+        thr = max(ea, er * r11) / f
+        if abs(s - thr) <= band * thr + noise:
+            cnt += 1
+    return cnt

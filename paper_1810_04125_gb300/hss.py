@@ -166,7 +166,12 @@ class HSSError(RuntimeError):
 
 def _check(status):
     if status != HSS_OK:
-        raise HSSError(status, lib().hss_last_error().decode())
+        msg = lib().hss_last_error().decode()
+        if status == HSS_ERR_OPERATOR:   # the caller's callback raised: say what
+            cause = last_extract_error if "extraction" in msg else last_operator_error
+            if cause is not None:
+                msg += f" ({type(cause).__name__}: {cause})"
+        raise HSSError(status, msg)
     return status
 
 
@@ -200,8 +205,8 @@ def _device_ints(ptr, count):
     import torch
 
     class _View:
-        __cuda_array_interface__ = {"shape": (count,), "strides": (4,), "typestr": "<i4",
-                                    "data": (ptr, True), "version": 3}
+        __cuda_array_interface__ = {"shape": (count,), "strides": None, "typestr": "<i4",
+                                    "data": (ptr, False), "version": 3}
     return torch.as_tensor(_View(), device="cuda")
 
 

@@ -106,7 +106,8 @@ def test_compress_mixed_parity(hss, torch, name, prec, mk, o):
     st = H.stats()
     assert st.converged == 1 and ref.converged
     assert st.d_final == ref.d_final
-    bad = gu.compare_with_oracle(H, ref, o, n)
+    # ranks under the tie rule widened by the mixed sampling error (Weyl)
+    bad = gu.compare_with_oracle(H, ref, o, n, noise=gu.mixed_noise(src, R, ref))
     assert not bad, bad
     A = src.to_dense()
     err_g = gu.rel_err(A, gu.gpu_dense(H, n))
@@ -137,10 +138,10 @@ def test_mixed_device_R_is_rounded(hss, torch):
     """Without a caller R the library draws Philox values already rounded to
     the tensor format, so the FP64 steps and the tensor cores see one R."""
     src = w.toeplitz_inverse_distance(1024)
-    o = Options(leaf=64, rtol=1e-6, atol=1e-12, d0=64, dd=32, d_max=1024)
+    o = Options(leaf=64, rtol=1e-4, atol=1e-10, d0=64, dd=32, d_max=1024)
     R = w.round_to_tf32(w.gaussian_matrix(11, 1024, 0, 1024))
     ref = compress(src, R, o)
     H = gu.gpu_compress(src, R, o, precision="tf32x2", pass_R=False, seed=11)
-    assert not gu.compare_with_oracle(H, ref, o, 1024)
+    assert not gu.compare_with_oracle(H, ref, o, 1024, noise=gu.mixed_noise(src, R, ref))
     A = src.to_dense()
     assert gu.rel_err(A, gu.gpu_dense(H, 1024)) <= 1.1 * apply.rel_error(ref, A) + 1e-15

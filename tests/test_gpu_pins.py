@@ -10,7 +10,7 @@ from oracle import apply
 from oracle.hss import Options, compress
 
 import gpu_util as gu
-from test_oracle_pins import doubling_closed_form, doubling_side_accepts
+from test_oracle_pins import doubling_closed_form
 
 pytestmark = pytest.mark.gpu
 
@@ -37,19 +37,14 @@ def test_doubling_acceptance_closed_form_gpu(hss, ranks, d0, p):
     o = Options(leaf=leaf, rtol=1e-10, atol=1e-14, d0=d0, dd=d0, d_max=128, strategy="doubling", p=p)
     H = gu.gpu_compress(w.dense_source(A), R, o)
     st = H.stats()
-    assert (bool(st.converged), st.d_final, st.n_adapt) == doubling_closed_form(n, leaf, ranks, d0, p, 128)
-    # kept ranks: the exact rank where the rule stopped, every row where it
-    # selected all of them (P9)
     kept = {}
-    for lev in sorted(ranks, reverse=True):
-        for i in range(1, st.n_nodes):
-            nd = H.node(i)
-            if nd.level != lev:
-                continue
-            m = nd.size if nd.child0 < 0 else kept[nd.child0] + kept[nd.child1]
-            ok, k = doubling_side_accepts(m, ranks[lev], st.d_final, p)
-            assert ok and (nd.kr, nd.kc) == (k, k) and nd.mr == nd.mc == m, (i, nd.kr, k)
-            kept[i] = k
+    assert (bool(st.converged), st.d_final, st.n_adapt) == doubling_closed_form(n, leaf, ranks, d0, p, 128, kept)
+    # rows and kept ranks: the exact rank where the rule stopped, every row
+    # where it selected all of them (P9), at the pass that accepted the node
+    for i in range(1, st.n_nodes):
+        nd = H.node(i)
+        m, k = kept[i]
+        assert (nd.mr, nd.mc, nd.kr, nd.kc) == (m, m, k, k), (i, nd.mr, nd.kr, m, k)
     assert gu.rel_err(A, gu.gpu_dense(H, n)) < 1e-12
 
 

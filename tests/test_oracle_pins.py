@@ -526,13 +526,13 @@ def doubling_side_accepts(m: int, r: int, d: int, p: int):
     return k == m, k
 
 
-def doubling_closed_form(n, leaf, ranks, d0, p, d_max):
+def doubling_closed_form(n, leaf, ranks, d0, p, d_max, kept_out=None):
     """(converged, d_final, n_adapt) of Algorithm 3 with Doubling on the
     synthetic HSS matrix of the given per-level ranks: passes at d0, 2 d0,
     ... (the last clipped to d_max); in a pass the levels are swept from the
     leaves up, a node is tried once both children are COMPRESSED, and its
     sample has m rows = its leaf size, or the sum of its children's kept
-    ranks."""
+    ranks.  ``kept_out`` (a dict) receives node -> (rows, kept rank)."""
     nodes = tree.halving_tree(n, leaf)
     state, kept = {}, {}
     d, n_adapt = min(d0, d_max), 0
@@ -544,6 +544,8 @@ def doubling_closed_form(n, leaf, ranks, d0, p, d_max):
             ok, k = doubling_side_accepts(m, ranks[t.level], d, p)
             if ok:
                 state[t.idx], kept[t.idx] = True, k
+                if kept_out is not None:
+                    kept_out[t.idx] = (m, k)
         if all(state.get(c) for c in nodes[0].children):
             return True, d, n_adapt
         if d >= d_max:
@@ -588,10 +590,14 @@ def test_doubling_acceptance_closed_form(ranks, d0, p):
     n, leaf = 1024, 64
     A = w.synthetic_hss(n, leaf, ranks, seed=3)
     R = w.gaussian_matrix(5, n, 0, 128)
-    want = doubling_closed_form(n, leaf, ranks, d0, p, 128)
+    kept = {}
+    want = doubling_closed_form(n, leaf, ranks, d0, p, 128, kept)
     res = compress(w.dense_source(A), R, Options(leaf=leaf, rtol=1e-10, atol=1e-14, d0=d0, dd=d0,
                                                  d_max=128, strategy="doubling", p=p))
     assert (res.converged, res.d_final, res.n_adapt) == want
+    for t in res.nodes[1:]:
+        m, k = kept[t.idx]
+        assert t.Sr.shape[0] == t.Sc.shape[0] == m and len(t.Jr) == len(t.Jc) == k, t.idx
     assert apply.rel_error(res, A) < 1e-12
 
 
