@@ -108,8 +108,8 @@ typedef struct hss_block {
  * (the B12 and B21 generators of its nodes), the leaf diagonal blocks D in
  * one call before the first sampling pass, and, when d_max is reached
  * without convergence, the dense off-diagonal blocks of the nodes left
- * uncompressed in one more call.  It runs on the host thread of the
- * compression (a worker thread of hss_compress_batched). */
+ * uncompressed in one more call.  It runs on the host thread that called the
+ * compression. */
 typedef int (*hss_extract_fn)(void* ctx, int nblocks, const hss_block* blocks, void* stream);
 
 typedef struct hss_source {
@@ -141,8 +141,8 @@ enum { HSS_UNTOUCHED = 0, HSS_PARTIALLY_COMPRESSED = 1, HSS_COMPRESSED = 2 };
  * generators (D and B blocks, and the leaf diagonal blocks removed from the
  * samples) come from the hss_source, which must describe the same A (a
  * built-in source, or the caller's extraction routine, HSS_SRC_EXTRACT).
- * The callback runs on the host thread of the compression (a worker thread
- * of hss_compress_batched), once per orientation and pass. */
+ * The callback runs on the host thread that called the compression, once per
+ * orientation and pass. */
 typedef int (*hss_apply_fn)(void* ctx, int trans, int n, int ncols, const double* R, long long ldr,
                             double* S, long long lds, void* stream);
 typedef struct hss_operator {
@@ -256,14 +256,21 @@ hss_status hss_compress_restart(const hss_source* A, const hss_opts* opts, void*
 
 /* hss_compress for a batch of independent matrices (the paper compresses
  * one matrix per call; the batch has no counterpart there): A[count] and
- * opts[count] (one options struct per matrix), out[count] receives the
- * handles.  The matrices are compressed side by side on worker streams
- * (largest n first) that start after the work already queued on `stream`;
- * `stream` waits for all of them before the call returns.  Errors: on any
- * status other than HSS_OK / HSS_ERR_NOT_CONVERGED every handle is freed,
- * out[] is all NULL and the first failing matrix's status is returned (its
- * message in hss_last_error); HSS_ERR_NOT_CONVERGED when some matrix did
- * not converge (all handles valid, as for hss_compress). */
+ * opts[count] (one options struct per matrix; strategies, precisions and
+ * sizes may differ), out[count] receives the handles.  The matrices are
+ * compressed in lockstep on `stream`, following Algorithm 3's level-by-level
+ * traversal (section 3.2) across the whole batch: every step of a level
+ * (extraction, merge, Incrementing test, QRCP / ID, reduction) is one launch
+ * over the nodes of that level of every matrix (the leaves of all matrices
+ * first), and the host reads back ranks and flags once per level for the
+ * whole batch.  Matrices run in groups whose estimated device memory fits
+ * 60 % of the free memory, largest first.  Each handle's phase times are
+ * those of its group; the launch and byte counts of a group are reported
+ * with its first matrix.  Errors: on any status other than HSS_OK /
+ * HSS_ERR_NOT_CONVERGED every handle is freed, out[] is all NULL and the
+ * status is returned (its message in hss_last_error);
+ * HSS_ERR_NOT_CONVERGED when some matrix did not converge (all handles
+ * valid, as for hss_compress). */
 hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int count, void* stream,
                                 hss_matrix* out);
 

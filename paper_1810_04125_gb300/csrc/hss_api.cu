@@ -247,7 +247,6 @@ struct hss_matrix_s {
   int max_level = 0;
   std::vector<int> bounds;   // sample widths after each growth (Incrementing blocks)
   Arena arena;
-  Scratch scratch;
   double* R = nullptr;     // n x dmax col-major (ld n)
   double* Sg_r = nullptr;  // n x dmax row-major: leaf samples
   double* Sg_c = nullptr;
@@ -256,35 +255,94 @@ struct hss_matrix_s {
   long long* leaf_doff = nullptr; // offset of each leaf's D in the packed leaf blocks (user operator)
   double* leaf_D = nullptr;       // the leaf blocks D, packed (user operator)
   int* iota = nullptr;
-  int* d_flag = nullptr;   // device int scratch
-  int* h_pinned = nullptr; // host pinned readback buffer
-  size_t h_pinned_cap = 0;
   int d_final = 0, n_adapt = 0, converged = 0;
-  int qrcp_cap = -1;       // co-resident CTAs of the QRCP kernel at width qrcp_cap_d
-  int qrcp_cap_d = -1;     // and shape qrcp_cap_w
-  int qrcp_cap_w = -1;
   int pack_decided = -1;   // mixed forms, generated A: packed tiles (1) or not (0)
   bool sym = false;        // symmetric option: the column side mirrors the row side
-  bool trace = false;      // HSS_TRACE=1: one stderr line per QRCP launch
-  cudaEvent_t trace_ev[2] = {nullptr, nullptr};
   void* packA = nullptr;   // packed tensor-core tiles of a dense A (during compress)
   bool usable = false;
   bool partial = false;    // not converged; the uncompressed part kept dense (F12, F21)
   hss_stats st{};
-  long long launches = 0;
-  PhaseTimer timer;
+  // progress of the compression (Algorithm 3's outer loop)
+  int d = 0, d_prev = 0, slot = 0;
+  bool own_R = true, done = false;
   ~hss_matrix_s() {
     if (packA) cudaFree(packA);
-    for (auto& e : trace_ev)
-      if (e) cudaEventDestroy(e);
-    timer.clear();
-    scratch.release();
     arena.release();
-    if (h_pinned) cudaFreeHost(h_pinned);
   }
 };
 
 namespace {
+
+// A device buffer reused launch after launch on one stream: a job list
+// uploaded for the next launch is copied after the previous launch has
+// finished reading it (stream order), so no allocation per launch.
+struct DevBuf {
+  char* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes, cudaStream_t st) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) {
+      cudaError_t e = cudaFreeAsync(p, st);
+      if (e != cudaSuccess) return e;
+    }
+    p = nullptr;
+    cap = 0;
+    const size_t sz = std::max(bytes + bytes / 2, size_t(1) << 20);
+    cudaError_t e = cudaMallocAsync((void**)&p, sz, st);
+    if (e != cudaSuccess) return e;
+    cap = sz;
+    return cudaSuccess;
+  }
+  void release(cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// What the matrices of one compression call share (one matrix for
+// hss_compress, all of them for hss_compress_batched): the stream, per-phase
+// scratch, the job-list buffer, the device flags and the pinned read-back
+// buffer, the phase timer and the counters.
+//   d_flag[0..7]: [1] tensor-core sampling wait, [2] QRCP barrier,
+//   [3] tensor-core tile product wait, [4] Incrementing test barrier;
+//   d_flag[8 + i]: non-finite samples of matrix i.
+struct Ctx {
+  cudaStream_t st = nullptr;
+  Scratch scratch;
+  DevBuf jobs;
+  int* d_flag = nullptr;
+  int nflag = 0;
+  int* h_pinned = nullptr;
+  size_t h_pinned_cap = 0;
+  PhaseTimer timer;
+  long long launches = 0, sample_launches = 0, bytes_h2d = 0, bytes_d2h = 0;
+  bool trace = false;      // HSS_TRACE=1: one stderr line per launch of the batched phases
+  cudaEvent_t trace_ev[2] = {nullptr, nullptr};
+  int qrcp_cap = -1, qrcp_cap_d = -1, qrcp_cap_w = -1;
+  explicit Ctx(cudaStream_t s) : st(s) {
+    const char* tr = getenv("HSS_TRACE");
+    trace = tr && tr[0] == '1';
+    if (trace && (cudaEventCreate(&trace_ev[0]) != cudaSuccess || cudaEventCreate(&trace_ev[1]) != cudaSuccess))
+      trace = false;
+  }
+  ~Ctx() {
+    timer.close_range();
+    timer.clear();
+    for (auto& e : trace_ev)
+      if (e) cudaEventDestroy(e);
+    jobs.release(st);
+    if (d_flag) cudaFreeAsync(d_flag, st);
+    scratch.release();
+    if (h_pinned) cudaFreeHost(h_pinned);
+  }
+  hss_status flags(int nmat) {
+    nflag = 8 + std::max(nmat, 0);
+    CK(cudaMallocAsync((void**)&d_flag, sizeof(int) * nflag, st));
+    CK(cudaMemsetAsync(d_flag, 0, sizeof(int) * nflag, st));
+    return HSS_OK;
+  }
+};
 
 SrcDev make_src(const hss_source& s, const int* leaf_id) {
   SrcDev d;
@@ -352,27 +410,68 @@ void build_tree(int n, int leaf, std::vector<Node>& nodes) {
   for (auto& t : nodes) t.leaf = t.ch[0] < 0;
 }
 
-hss_status upload(hss_matrix_s* H, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+hss_status upload(Ctx& c, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return HSS_OK;
-  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
-  H->st.bytes_h2d += (long long)bytes;
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c.st));
+  c.bytes_h2d += (long long)bytes;
   return HSS_OK;
 }
 
-hss_status readback(hss_matrix_s* H, const void* src, size_t bytes, cudaStream_t st) {
-  if (bytes > H->h_pinned_cap) {
-    if (H->h_pinned) cudaFreeHost(H->h_pinned);
-    H->h_pinned = nullptr;
-    H->h_pinned_cap = 0;
+hss_status readback(Ctx& c, const void* src, size_t bytes) {
+  if (bytes > c.h_pinned_cap) {
+    if (c.h_pinned) cudaFreeHost(c.h_pinned);
+    c.h_pinned = nullptr;
+    c.h_pinned_cap = 0;
     size_t sz = std::max(bytes, size_t(1) << 16);
-    CK(cudaMallocHost((void**)&H->h_pinned, sz));
-    H->h_pinned_cap = sz;
+    CK(cudaMallocHost((void**)&c.h_pinned, sz));
+    c.h_pinned_cap = sz;
   }
-  if (bytes) CK(cudaMemcpyAsync(H->h_pinned, src, bytes, cudaMemcpyDeviceToHost, st));
-  H->st.bytes_d2h += (long long)bytes;
-  CK(cudaStreamSynchronize(st));
+  if (bytes) CK(cudaMemcpyAsync(c.h_pinned, src, bytes, cudaMemcpyDeviceToHost, c.st));
+  c.bytes_d2h += (long long)bytes;
+  CK(cudaStreamSynchronize(c.st));
   return HSS_OK;
 }
+
+// Several device ranges copied into the pinned buffer back to back with one
+// synchronisation; returns the host offset of each range (8-byte aligned).
+hss_status readback_many(Ctx& c, const std::vector<std::pair<const void*, size_t>>& items, std::vector<size_t>& off) {
+  off.clear();
+  size_t tot = 0;
+  for (auto& it : items) {
+    off.push_back(tot);
+    tot += (it.second + 7) & ~size_t(7);
+  }
+  if (tot > c.h_pinned_cap) {
+    if (c.h_pinned) cudaFreeHost(c.h_pinned);
+    c.h_pinned = nullptr;
+    c.h_pinned_cap = 0;
+    size_t sz = std::max(tot, size_t(1) << 16);
+    CK(cudaMallocHost((void**)&c.h_pinned, sz));
+    c.h_pinned_cap = sz;
+  }
+  for (size_t i = 0; i < items.size(); ++i)
+    if (items[i].second)
+      CK(cudaMemcpyAsync((char*)c.h_pinned + off[i], items[i].first, items[i].second, cudaMemcpyDeviceToHost, c.st));
+  c.bytes_d2h += (long long)tot;
+  CK(cudaStreamSynchronize(c.st));
+  return HSS_OK;
+}
+
+// The job lists of one launch, packed into the reused device buffer.
+struct Staging {
+  std::vector<char> host;
+  size_t put(const void* p, size_t bytes) {
+    const size_t off = Scratch::rnd(host.size());
+    host.resize(off + bytes);
+    if (bytes) memcpy(host.data() + off, p, bytes);
+    return off;
+  }
+  hss_status send(Ctx& c, char** dev) {
+    CK(c.jobs.ensure(std::max<size_t>(host.size(), 256), c.st));
+    *dev = c.jobs.p;
+    return upload(c, c.jobs.p, host.data(), host.size());
+  }
+};
 
 Opnd opnd(const double* p, long long rs, long long cs, const int* rows = nullptr,
           const double* p2 = nullptr, int split = 0x7fffffff) {
@@ -392,12 +491,12 @@ GemmJob gemm_job() {
   return j;
 }
 
-// Runs a list of tile-product jobs (one launch).
-// tc: products that only form samples (merge, reduce) go to the tensor-core
-// kernel in the mixed precisions.
-hss_status run_gemms(hss_matrix_s* H, const std::vector<GemmJob>& jobs, cudaStream_t st,
-                     const char* tag = "gemm", bool tc = false) {
-  tc = tc && H->o.precision != HSS_PREC_FP64;
+// Runs a list of tile-product jobs (one launch).  tc_prec: HSS_PREC_FP64 for
+// the FP64 tile kernel; a mixed precision sends the products that only form
+// samples (merge, reduce, test projections) to the tensor-core kernel.
+hss_status run_gemms(Ctx& c, const std::vector<GemmJob>& jobs, const char* tag = "gemm",
+                     int tc_prec = HSS_PREC_FP64) {
+  const bool tc = tc_prec != HSS_PREC_FP64;
   int max_n = 0;
   for (const GemmJob& j : jobs) max_n = std::max(max_n, j.N);
   const int tm = tc ? 128 : 64, tn = tc ? gemm_tc_tile_n(max_n) : 64;
@@ -420,7 +519,7 @@ hss_status run_gemms(hss_matrix_s* H, const std::vector<GemmJob>& jobs, cudaStre
         ntile < 2 * 152) {
       ks = (int)std::min<long long>((2 * 152 + ntile - 1) / ntile, j.K / 256);
       ks = std::max(ks, 1);
-      if (ks > 1 && j.gamma == 0.0) CK(cudaMemsetAsync(j.C, 0, sizeof(double) * (size_t)j.M * j.N, st));
+      if (ks > 1 && j.gamma == 0.0) CK(cudaMemsetAsync(j.C, 0, sizeof(double) * (size_t)j.M * j.N, c.st));
     }
     for (int ti = 0; ti < (j.M + tm - 1) / tm; ++ti)
       for (int tj = 0; tj < (j.N + tn - 1) / tn; ++tj)
@@ -432,66 +531,105 @@ hss_status run_gemms(hss_matrix_s* H, const std::vector<GemmJob>& jobs, cudaStre
         }
   }
   if (tiles.empty()) return HSS_OK;
-  if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
-  size_t bj = jobs.size() * sizeof(GemmJob), bt = tiles.size() * sizeof(GemmTile);
-  void* dj = nullptr;
-  CK(cudaMallocAsync(&dj, Scratch::rnd(bj) + bt, st));
-  GemmTile* dt = (GemmTile*)((char*)dj + Scratch::rnd(bj));
-  CKS(upload(H, dj, jobs.data(), bj, st));
-  CKS(upload(H, dt, tiles.data(), bt, st));
-  if (tc) CK(launch_gemm_tc((const GemmJob*)dj, dt, (int)tiles.size(), tn, H->d_flag + 3, st));
-  else CK(launch_gemm((const GemmJob*)dj, dt, (int)tiles.size(), st));
-  H->launches++;
-  CK(cudaFreeAsync(dj, st));
-  if (H->trace) {
-    CK(cudaEventRecord(H->trace_ev[1], st));
-    CK(cudaEventSynchronize(H->trace_ev[1]));
+  if (c.trace) CK(cudaEventRecord(c.trace_ev[0], c.st));
+  Staging sg;
+  const size_t oj = sg.put(jobs.data(), jobs.size() * sizeof(GemmJob));
+  const size_t ot = sg.put(tiles.data(), tiles.size() * sizeof(GemmTile));
+  char* dev;
+  CKS(sg.send(c, &dev));
+  if (tc) CK(launch_gemm_tc((const GemmJob*)(dev + oj), (const GemmTile*)(dev + ot), (int)tiles.size(), tn,
+                            c.d_flag + 3, c.st));
+  else CK(launch_gemm((const GemmJob*)(dev + oj), (const GemmTile*)(dev + ot), (int)tiles.size(), c.st));
+  c.launches++;
+  if (c.trace) {
+    CK(cudaEventRecord(c.trace_ev[1], c.st));
+    CK(cudaEventSynchronize(c.trace_ev[1]));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, H->trace_ev[0], H->trace_ev[1]);
-    fprintf(stderr, "[hss trace] %s jobs %zu tiles %zu  %.3f ms  %.1f GFLOP/s\n", tag, jobs.size(),
-            tiles.size(), ms, flop / (ms * 1e6));
+    cudaEventElapsedTime(&ms, c.trace_ev[0], c.trace_ev[1]);
+    fprintf(stderr, "[hss trace] %s jobs %zu tiles %zu  %.3f ms  %.1f GFLOP/s\n", tag, jobs.size(), tiles.size(), ms,
+            flop / (ms * 1e6));
   }
   return HSS_OK;
 }
 
-template <class T>
-hss_status upload_jobs(hss_matrix_s* H, const std::vector<T>& jobs, T** dev, cudaStream_t st) {
-  *dev = nullptr;
-  if (jobs.empty()) return HSS_OK;
-  CK(cudaMallocAsync((void**)dev, jobs.size() * sizeof(T), st));
-  return upload(H, *dev, jobs.data(), jobs.size() * sizeof(T), st);
+// One launch over the jobs of every precision present: the FP64 products and
+// the products of each mixed form (tensor cores) separately.
+struct GemmSet {
+  std::vector<GemmJob> by_prec[3];
+  void add(int prec, const GemmJob& j) { by_prec[prec < 0 || prec > 2 ? 0 : prec].push_back(j); }
+  bool empty() const { return by_prec[0].empty() && by_prec[1].empty() && by_prec[2].empty(); }
+};
+hss_status run_gemm_set(Ctx& c, const GemmSet& g, const char* tag) {
+  for (int p = 0; p < 3; ++p) CKS(run_gemms(c, g.by_prec[p], tag, p));
+  return HSS_OK;
 }
 
-// Element extraction out(i, j) = A(I[i], J[j]) for a list of blocks (one
-// tree level, or the leaf blocks): one launch of the gather / generator
-// kernel for a built-in source, one call of the caller's routine for an
-// extraction source (section 3.1: all blocks of a level at once).
-hss_status extract_blocks(hss_matrix_s* H, const std::vector<ExtractJob>& ex, cudaStream_t st) {
-  if (ex.empty()) return HSS_OK;
-  if (H->src.kind == HSS_SRC_EXTRACT) {
-    std::vector<hss_block> blk;
-    blk.reserve(ex.size());
-    for (const ExtractJob& e : ex) {
-      if (e.mi <= 0 || e.nj <= 0) continue;
-      hss_block b;
-      b.nr = e.mi; b.nc = e.nj;
-      b.I = e.I ? e.I : H->iota + e.i0;
-      b.J = e.J ? e.J : H->iota + e.j0;
-      b.out = e.out; b.ldo = e.ldo;
-      blk.push_back(b);
-    }
-    if (blk.empty()) return HSS_OK;
-    const int rc = H->src.extract(H->src.ctx, (int)blk.size(), blk.data(), (void*)st);
-    if (rc != 0) return fail(HSS_ERR_OPERATOR, "user element extraction returned %d (%zu blocks)", rc, blk.size());
-    return HSS_OK;
+// Element extraction out(i, j) = A(I[i], J[j]) for lists of blocks (a tree
+// level of one or several matrices): one launch of the gather / generator
+// kernel for the built-in sources, one call of the caller's routine per
+// matrix with an extraction source (section 3.1: all blocks of a level at
+// once).
+struct ExtractSet {
+  std::vector<std::pair<hss_matrix_s*, std::vector<ExtractJob>>> per;
+  std::vector<ExtractJob>& of(hss_matrix_s* H) {
+    for (auto& e : per)
+      if (e.first == H) return e.second;
+    per.push_back({H, {}});
+    return per.back().second;
   }
+};
+
+hss_status run_extract(Ctx& c, ExtractSet& es) {
+  std::vector<ExtractJob> dev;
   int max_tiles = 1;
-  for (const ExtractJob& e : ex) max_tiles = std::max(max_tiles, ((e.mi + 31) / 32) * ((e.nj + 31) / 32));
-  ExtractJob* dj;
-  CKS(upload_jobs(H, ex, &dj, st));
-  CK(launch_extract(make_src(H->src, H->leaf_id), dj, (int)ex.size(), max_tiles, st));
-  H->launches++;
-  CK(cudaFreeAsync(dj, st));
+  for (auto& pe : es.per) {
+    hss_matrix_s* H = pe.first;
+    if (pe.second.empty()) continue;
+    if (H->src.kind == HSS_SRC_EXTRACT) {
+      std::vector<hss_block> blk;
+      for (const ExtractJob& e : pe.second) {
+        if (e.mi <= 0 || e.nj <= 0) continue;
+        hss_block b;
+        b.nr = e.mi; b.nc = e.nj;
+        b.I = e.I ? e.I : H->iota + e.i0;
+        b.J = e.J ? e.J : H->iota + e.j0;
+        b.out = e.out; b.ldo = e.ldo;
+        blk.push_back(b);
+      }
+      if (blk.empty()) continue;
+      const int rc = H->src.extract(H->src.ctx, (int)blk.size(), blk.data(), (void*)c.st);
+      if (rc != 0) return fail(HSS_ERR_OPERATOR, "user element extraction returned %d (%zu blocks)", rc, blk.size());
+      continue;
+    }
+    const SrcDev s = make_src(H->src, H->leaf_id);
+    for (ExtractJob e : pe.second) {
+      if (e.mi <= 0 || e.nj <= 0) continue;
+      e.src = s;
+      dev.push_back(e);
+      max_tiles = std::max(max_tiles, ((e.mi + 31) / 32) * ((e.nj + 31) / 32));
+    }
+  }
+  es.per.clear();
+  if (dev.empty()) return HSS_OK;
+  Staging sg;
+  const size_t o = sg.put(dev.data(), dev.size() * sizeof(ExtractJob));
+  char* d;
+  CKS(sg.send(c, &d));
+  CK(launch_extract((const ExtractJob*)(d + o), (int)dev.size(), max_tiles, c.st));
+  c.launches++;
+  return HSS_OK;
+}
+
+hss_status run_gathers(Ctx& c, const std::vector<GatherJob>& g) {
+  if (g.empty()) return HSS_OK;
+  int mx = 0;
+  for (const GatherJob& j : g) mx = std::max(mx, j.cnt);
+  Staging sg;
+  const size_t o = sg.put(g.data(), g.size() * sizeof(GatherJob));
+  char* d;
+  CKS(sg.send(c, &d));
+  CK(launch_gather_int((const GatherJob*)(d + o), (int)g.size(), mx, c.st));
+  c.launches++;
   return HSS_OK;
 }
 
@@ -518,25 +656,30 @@ bool use_packed(hss_matrix_s* H) {
   return H->pack_decided == 1;
 }
 
-hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool own_R) {
+// S^r = A R, S^c = A^T R for columns [c0, c1) of matrix H, the leaf diagonal
+// blocks removed (eq. sample_off_diag); the non-finite check writes the
+// matrix's flag.  No read-back here: sample_check reads every matrix's flags
+// at once.
+hss_status sample_columns(Ctx& c, hss_matrix_s* H, int c0, int c1) {
   const int n = H->n, w = c1 - c0;
   if (w <= 0) return HSS_OK;
-  CK(H->timer.mark(PH_RNG, st));
+  cudaStream_t st = c.st;
+  CK(c.timer.mark(PH_RNG, st));
   const int rm = H->o.precision == HSS_PREC_TF32X2 ? 1 : (H->o.precision == HSS_PREC_BF16X3 ? 2 : 0);
-  if (own_R && H->o.R == nullptr) {
+  if (H->own_R && H->o.R == nullptr) {
     CK(launch_random_normal(H->o.seed, n, c0, w, H->R + (long long)c0 * n, n, rm, st));
-    H->launches++;
-  } else if (own_R) {
+    c.launches++;
+  } else if (H->own_R) {
     // caller's R made exactly representable in the tensor format (reading P10)
     CK(launch_round_copy(H->o.R + (long long)c0 * n, n, H->R + (long long)c0 * n, n, n, w, rm, st));
-    H->launches++;
+    c.launches++;
   }
   SrcDev s = make_src(H->src, H->leaf_id);
   const double* Rc = H->R + (long long)c0 * n;
   const int norient = H->sym ? 1 : 2;   // A^T R is A R for a symmetric A
   if (H->o.op) {
     // the user's product A R (and A^T R), then the leaf diagonal blocks off
-    CK(H->timer.mark(PH_SAMPLE, st));
+    CK(c.timer.mark(PH_SAMPLE, st));
     double* T = nullptr;
     CK(cudaMallocAsync(&T, sizeof(double) * (size_t)n * w * norient, st));
     for (int side = 0; side < norient; ++side) {
@@ -551,13 +694,15 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
     if (!H->sym)
       CK(launch_leaf_diag_sub(H->leaf_D, H->leaf_doff, H->leaf_id, H->leaf_lo, n, w, Rc, n, T + (size_t)n * w, n,
                               H->Sg_c + c0, H->dmax, 1, st));
-    H->launches += norient;
+    c.launches += norient;
+    c.sample_launches += norient;
     H->st.sample_launches += norient;
     CK(cudaFreeAsync(T, st));
   } else if (H->o.precision == HSS_PREC_FP64) {
-    CK(H->timer.mark(PH_SAMPLE, st));
+    CK(c.timer.mark(PH_SAMPLE, st));
     CK(launch_sample_fp64(s, w, Rc, n, H->Sg_r + c0, H->sym ? nullptr : H->Sg_c + c0, H->dmax, st));
-    H->launches += norient;
+    c.launches += norient;
+    c.sample_launches += norient;
     H->st.sample_launches += norient;
   } else if (use_packed(H)) {
     // dense A, or generated entries whose split tiles fit comfortably in
@@ -566,57 +711,55 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
     // pass)
     if (!H->packA) {
       const size_t pb = packed_a_bytes(n, H->o.precision);
-      CK(H->timer.mark(PH_SAMPLE, st));
+      CK(c.timer.mark(PH_SAMPLE, st));
       CK(cudaMallocAsync(&H->packA, pb, st));
       CK(launch_pack_a(s, H->o.leaf, H->o.precision, H->packA, st));
-      H->launches++;
+      c.launches++;
       // the split is part of the sampling work: a dense A read once, the
       // packed tiles written once
       H->st.bytes_sample += (H->src.kind == HSS_SRC_DENSE ? 8.0 * n * (double)n : 0.0) + (double)pb;
-      CK(H->timer.mark(PH_RNG, st));
+      CK(c.timer.mark(PH_RNG, st));
     }
     void* packR = nullptr;
     CK(cudaMallocAsync(&packR, packed_r_bytes(n, w, H->o.precision), st));
     CK(launch_pack_r(Rc, n, n, w, H->o.precision, packR, st));
-    H->launches++;
+    c.launches++;
     if (sample_tc_packed_ksplit(n, w, H->o.precision) > 1) {
       CK(cudaMemset2DAsync(H->Sg_r + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
       if (!H->sym) CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
     }
-    CK(cudaMemsetAsync(H->d_flag + 1, 0, sizeof(int), st));
-    CK(H->timer.mark(PH_SAMPLE, st));
-    CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 0, H->Sg_r + c0, H->dmax,
-                               H->d_flag + 1, st));
+    CK(c.timer.mark(PH_SAMPLE, st));
+    CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 0, H->Sg_r + c0, H->dmax, c.d_flag + 1, st));
     if (!H->sym)
-      CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 1, H->Sg_c + c0, H->dmax,
-                                 H->d_flag + 1, st));
-    H->launches += norient;
+      CK(launch_sample_tc_packed(H->packA, packR, n, w, H->o.precision, 1, H->Sg_c + c0, H->dmax, c.d_flag + 1,
+                                 st));
+    c.launches += norient;
+    c.sample_launches += norient;
     H->st.sample_launches += norient;
-    CK(H->timer.mark(PH_RNG, st));
+    CK(c.timer.mark(PH_RNG, st));
     CK(cudaFreeAsync(packR, st));
   } else {
     void* packR = nullptr;
     CK(cudaMallocAsync(&packR, packed_r_bytes(n, w, H->o.precision), st));
     CK(launch_pack_r(Rc, n, n, w, H->o.precision, packR, st));
-    H->launches++;
+    c.launches++;
     if (sample_tc_ksplit(n, w, H->o.precision) > 1) {
       CK(cudaMemset2DAsync(H->Sg_r + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
       if (!H->sym) CK(cudaMemset2DAsync(H->Sg_c + c0, sizeof(double) * H->dmax, 0, sizeof(double) * w, n, st));
     }
-    CK(cudaMemsetAsync(H->d_flag + 1, 0, sizeof(int), st));
-    CK(H->timer.mark(PH_SAMPLE, st));
+    CK(c.timer.mark(PH_SAMPLE, st));
     int at = 0;
-    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 0, w, packR, H->Sg_r + c0, H->dmax,
-                        H->d_flag + 1, &at, st));
+    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 0, w, packR, H->Sg_r + c0, H->dmax, c.d_flag + 1, &at, st));
     if (!H->sym)
-      CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 1, w, packR, H->Sg_c + c0, H->dmax,
-                          H->d_flag + 1, &at, st));
-    H->launches += norient;
+      CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 1, w, packR, H->Sg_c + c0, H->dmax, c.d_flag + 1, &at,
+                          st));
+    c.launches += norient;
+    c.sample_launches += norient;
     H->st.sample_launches += norient;
-    CK(H->timer.mark(PH_RNG, st));
+    CK(c.timer.mark(PH_RNG, st));
     CK(cudaFreeAsync(packR, st));
   }
-  CK(H->timer.mark(PH_RNG, st));
+  CK(c.timer.mark(PH_RNG, st));
   H->st.flop_sample += 2.0 * norient * (double)n * (double)n * (double)w;
   // algorithmic bytes of the sampling kernels: A read once per orientation
   // (FP64: 8 B per entry; packed TF32x2: 8 B; packed BF16x3: 6 B), R read,
@@ -626,22 +769,24 @@ hss_status sample_columns(hss_matrix_s* H, int c0, int c1, cudaStream_t st, bool
   else if (H->src.kind == HSS_SRC_DENSE || (H->o.precision != HSS_PREC_FP64 && H->pack_decided == 1))
     abytes = (H->o.precision == HSS_PREC_BF16X3 ? 6.0 : 8.0) * n * (double)n;
   H->st.bytes_sample += norient * (abytes + 2.0 * 8.0 * n * (double)w);
-  CK(cudaMemsetAsync(H->d_flag, 0, sizeof(int), st));
-  CK(launch_nonfinite(H->Sg_r, H->dmax, n, c0, c1, H->d_flag, st));
-  if (!H->sym) CK(launch_nonfinite(H->Sg_c, H->dmax, n, c0, c1, H->d_flag, st));
-  H->launches += norient;
-  CKS(readback(H, H->d_flag, 2 * sizeof(int), st));
-  if (H->o.precision != HSS_PREC_FP64 && H->h_pinned[1])
-    return fail(HSS_ERR_TIMEOUT, "tensor-core sampling gave up waiting (code %d)", H->h_pinned[1]);
-  if (H->h_pinned[0]) return fail(HSS_ERR_NONFINITE, "NaN or Inf in the random samples (columns %d..%d)", c0, c1);
+  int* flag = c.d_flag + 8 + H->slot;
+  CK(launch_nonfinite(H->Sg_r, H->dmax, n, c0, c1, flag, st));
+  if (!H->sym) CK(launch_nonfinite(H->Sg_c, H->dmax, n, c0, c1, flag, st));
+  c.launches += norient;
+  return HSS_OK;
+}
+
+// One read-back of the sampling flags of every matrix after a sampling round.
+hss_status sample_check(Ctx& c, const std::vector<hss_matrix_s*>& Hs) {
+  CKS(readback(c, c.d_flag, sizeof(int) * c.nflag));
+  if (c.h_pinned[1]) return fail(HSS_ERR_TIMEOUT, "tensor-core sampling gave up waiting (code %d)", c.h_pinned[1]);
+  for (hss_matrix_s* H : Hs)
+    if (c.h_pinned[8 + H->slot])
+      return fail(HSS_ERR_NONFINITE, "NaN or Inf in the random samples (columns up to %d)", H->d);
   return HSS_OK;
 }
 
 // ------------------------------------------------------ one pass of Alg. 3
-struct LevelWork {
-  std::vector<int> cand, upd;   // nodes to test / to update
-};
-
 hss_status alloc_side(hss_matrix_s* H, Side& s, bool leaf, double* Sleaf, int m) {
   s.m = m;
   s.S = leaf ? Sleaf : (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(m, 1) * H->dmax);
@@ -727,15 +872,17 @@ std::mutex& coop_launch_mutex() {
   return m;
 }
 
-// QRCP/ID over all columns [0, d) of the listed node sides.
-struct QrcpReq { int node; int side; int rule; };
+// QRCP/ID over all columns [0, H->d) of the listed node sides (of one or
+// several matrices, each at its own d).
+struct QrcpReq { hss_matrix_s* H; int node; int side; int rule; };
 
-hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cudaStream_t st,
-                    std::vector<double*>& wbuf) {
-  H->scratch.reset();
+hss_status run_qrcp(Ctx& c, const std::vector<QrcpReq>& reqs, std::vector<double*>& wbuf) {
+  c.scratch.reset();
   if (reqs.empty()) return HSS_OK;
-  const long long ldw = ((long long)d + 3) / 4 * 4;   // 32-byte aligned columns
+  cudaStream_t st = c.st;
   const size_t nj = reqs.size();
+  int dmx = 1;
+  for (const QrcpReq& q : reqs) dmx = std::max(dmx, q.H->d);
   // Launch shape.  Every job gets a group of P CTAs, each owning about g of
   // its m columns (g a multiple of 32, at most qrcp_cols_per_cta()), with g
   // the smallest width for which the groups of a batch fit the co-resident
@@ -743,18 +890,16 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   // few node sides (the top levels): the wide shape, whose groups have half
   // as many CTAs; otherwise the narrow one
   const int wide = (int)nj <= tuning_get().qrcp_wide_max_sides ? 1 : 0;
-  if (H->qrcp_cap_d != d || H->qrcp_cap_w != wide) {
-    H->qrcp_cap = qrcp_group_capacity(d, wide);
-    H->qrcp_cap_d = d;
-    H->qrcp_cap_w = wide;
+  if (c.qrcp_cap_d != dmx || c.qrcp_cap_w != wide) {
+    c.qrcp_cap = qrcp_group_capacity(dmx, wide);
+    c.qrcp_cap_d = dmx;
+    c.qrcp_cap_w = wide;
   }
-  const int cap = H->qrcp_cap, NL = qrcp_cols_per_cta();
-  if (cap <= 0) return fail(HSS_ERR_CUDA, "QRCP kernel cannot be resident (d = %d)", d);
+  const int cap = c.qrcp_cap, NL = qrcp_cols_per_cta();
+  if (cap <= 0) return fail(HSS_ERR_CUDA, "QRCP kernel cannot be resident (d = %d)", dmx);
+  auto side_of = [&](const QrcpReq& q) -> Side& { return q.side ? q.H->nodes[q.node].c : q.H->nodes[q.node].r; };
   std::vector<int> mj(nj), P(nj, 1);
-  for (size_t i = 0; i < nj; ++i) {
-    const Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
-    mj[i] = std::max(s.m, 1);
-  }
+  for (size_t i = 0; i < nj; ++i) mj[i] = std::max(side_of(reqs[i]).m, 1);
   struct Batch { size_t b0, b1; bool group; };
   std::vector<Batch> batches;
   bool all_small = nj >= (size_t)cap;
@@ -780,8 +925,8 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     // twice the width) with some growth, else min(m, d)
     std::vector<double> wk(nj, 0.0);
     for (size_t i = b0; i < b1; ++i) {
-      const Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
-      const double m = mj[i], dd = d, kmx = std::min(m, dd);
+      const Side& s = side_of(reqs[i]);
+      const double m = mj[i], dd = reqs[i].H->d, kmx = std::min(m, dd);
       const double k = s.qr_k > 0 ? std::min(kmx, 1.25 * s.qr_k + 16.0) : kmx;
       wk[i] = dd * m * k - 0.5 * (dd + m) * k * k + k * k * k / 3.0 + 1.0;
     }
@@ -803,28 +948,32 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
   }
   size_t need = 0;
   for (size_t i = 0; i < nj; ++i) {
+    const long long ldw = ((long long)reqs[i].H->d + 3) / 4 * 4;
     need += Scratch::rnd(sizeof(double) * (size_t)ldw * mj[i]) + Scratch::rnd(sizeof(double) * mj[i]) +
-            Scratch::rnd(sizeof(double) * (size_t)std::max(1, std::min(mj[i], d))) +
-            Scratch::rnd(sizeof(unsigned)) + Scratch::rnd(sizeof(double) * 4 * P[i]) +
-            Scratch::rnd(sizeof(double) * 2 * P[i]) + Scratch::rnd(sizeof(double) * 8);
+            Scratch::rnd(sizeof(double) * (size_t)std::max(1, std::min(mj[i], reqs[i].H->d))) +
+            Scratch::rnd(sizeof(double) * 4 * P[i]) + Scratch::rnd(sizeof(double) * 2 * P[i]) +
+            Scratch::rnd(sizeof(double) * 8);
   }
-  need += Scratch::rnd(sizeof(int) * 3 * nj);
-  CK(H->scratch.ensure(need, st));
+  need += Scratch::rnd(sizeof(unsigned) * nj) + Scratch::rnd(sizeof(int) * 3 * nj);
+  CK(c.scratch.ensure(need, st));
   std::vector<QrcpJob> jobs;
   wbuf.clear();
-  unsigned* bars = (unsigned*)H->scratch.take(sizeof(unsigned) * nj);
-  int* outs = (int*)H->scratch.take(sizeof(int) * 3 * nj);
+  unsigned* bars = (unsigned*)c.scratch.take(sizeof(unsigned) * nj);
+  int* outs = (int*)c.scratch.take(sizeof(int) * 3 * nj);
   for (size_t i = 0; i < nj; ++i) {
     const QrcpReq& q = reqs[i];
+    hss_matrix_s* H = q.H;
     Node& t = H->nodes[q.node];
     Side& s = q.side ? t.c : t.r;
+    const int d = H->d;
+    const long long ldw = ((long long)d + 3) / 4 * 4;   // 32-byte aligned columns
     QrcpJob j;
     memset(&j, 0, sizeof j);
     j.S = s.S; j.lds = H->dmax; j.m = s.m; j.d = d;
-    j.W = (double*)H->scratch.take(sizeof(double) * (size_t)ldw * mj[i]);
+    j.W = (double*)c.scratch.take(sizeof(double) * (size_t)ldw * mj[i]);
     j.ldw = ldw;
-    j.nrm = (double*)H->scratch.take(sizeof(double) * mj[i]);
-    j.diag = (double*)H->scratch.take(sizeof(double) * std::max(1, std::min(mj[i], d)));
+    j.nrm = (double*)c.scratch.take(sizeof(double) * mj[i]);
+    j.diag = (double*)c.scratch.take(sizeof(double) * std::max(1, std::min(mj[i], d)));
     j.piv = s.piv;
     j.rule = q.rule;
     j.mh = t.size; j.nh = H->n - t.size; j.p = H->o.oversample_p;
@@ -836,92 +985,105 @@ hss_status run_qrcp(hss_matrix_s* H, const std::vector<QrcpReq>& reqs, int d, cu
     j.out = outs + 3 * i;
     j.P = P[i];
     j.bar = bars + i;
-    j.redv = (double*)H->scratch.take(sizeof(double) * 4 * P[i]);   // 2 P (key, index) pairs
-    j.redt = (double*)H->scratch.take(sizeof(double) * 2 * P[i]);
-    j.xfer = (double*)H->scratch.take(sizeof(double) * 8);
+    j.redv = (double*)c.scratch.take(sizeof(double) * 4 * P[i]);   // 2 P (key, index) pairs
+    j.redt = (double*)c.scratch.take(sizeof(double) * 2 * P[i]);
+    j.xfer = (double*)c.scratch.take(sizeof(double) * 8);
     j.wait_ns = wait_limit(H);
     wbuf.push_back(j.W);
     jobs.push_back(j);
   }
-  if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
-  CK(H->timer.mark(PH_ID, st));
+  if (c.scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
+  CK(c.timer.mark(PH_ID, st));
   CK(cudaMemsetAsync(bars, 0, sizeof(unsigned) * nj, st));
-  CK(cudaMemsetAsync(H->d_flag + 2, 0, sizeof(int), st));
-  if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
-  QrcpJob* dj;
-  CKS(upload_jobs(H, jobs, &dj, st));
+  CK(cudaMemsetAsync(c.d_flag + 2, 0, sizeof(int), st));
+  if (c.trace) CK(cudaEventRecord(c.trace_ev[0], st));
+  // job list and every batch's (job, rank) map in one upload
+  Staging sg;
+  const size_t oj = sg.put(jobs.data(), jobs.size() * sizeof(QrcpJob));
+  std::vector<size_t> omap(batches.size(), 0);
+  std::vector<int> nmap(batches.size(), 0);
+  for (size_t bi = 0; bi < batches.size(); ++bi) {
+    const Batch& b = batches[bi];
+    if (!b.group) continue;
+    std::vector<int2> map;
+    for (size_t i = b.b0; i < b.b1; ++i)
+      for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
+    omap[bi] = sg.put(map.data(), map.size() * sizeof(int2));
+    nmap[bi] = (int)map.size();
+  }
+  char* dev;
+  CKS(sg.send(c, &dev));
+  const QrcpJob* dj = (const QrcpJob*)(dev + oj);
   // A cooperative launch needs all of its CTAs resident at once: compressions
-  // running side by side (hss_compress_batched) take turns with them, the
+  // running side by side on other host threads take turns with them, the
   // lock held until the launch has finished (the flag read-back below).
   bool any_group = false;
   for (const Batch& b : batches) any_group = any_group || b.group;
   std::unique_lock<std::mutex> coop(coop_launch_mutex(), std::defer_lock);
   if (any_group) coop.lock();
   int ctas_total = 0;
-  for (const Batch& b : batches) {
+  for (size_t bi = 0; bi < batches.size(); ++bi) {
+    const Batch& b = batches[bi];
     if (b.group) {
-      std::vector<int2> map;
-      for (size_t i = b.b0; i < b.b1; ++i)
-        for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
-      int2* dm;
-      CKS(upload_jobs(H, map, &dm, st));
-      CK(launch_qrcp(dj, dm, (int)map.size(), d, wide, H->d_flag + 2, st));
-      CK(cudaFreeAsync(dm, st));
-      ctas_total += (int)map.size();
+      CK(launch_qrcp(dj, (const int2*)(dev + omap[bi]), nmap[bi], dmx, wide, c.d_flag + 2, st));
+      ctas_total += nmap[bi];
     } else {
-      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), d, wide, H->d_flag + 2, st));
+      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), dmx, wide, c.d_flag + 2, st));
       ctas_total += (int)(b.b1 - b.b0);
     }
-    H->launches++;
+    c.launches++;
   }
   const int nbatch = (int)batches.size();
-  CK(cudaFreeAsync(dj, st));
-  if (H->trace) CK(cudaEventRecord(H->trace_ev[1], st));
-  CKS(readback(H, H->d_flag + 2, 2 * sizeof(int), st));
+  if (c.trace) CK(cudaEventRecord(c.trace_ev[1], st));
+  // the flags and the (k, stopped, accepted) triples in one read-back
+  std::vector<size_t> off;
+  CKS(readback_many(c, {{c.d_flag, sizeof(int) * 8}, {outs, sizeof(int) * 3 * jobs.size()}}, off));
+  const int* hf = (const int*)((char*)c.h_pinned + off[0]);
+  const int* ho = (const int*)((char*)c.h_pinned + off[1]);
+  const int f2 = hf[2], f3 = hf[3];
   if (coop.owns_lock()) coop.unlock();
-  if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "group QRCP barrier gave up (code %d)", H->h_pinned[0]);
-  if (H->h_pinned[1]) return fail(HSS_ERR_TIMEOUT, "tensor-core tile product gave up waiting (code %d)", H->h_pinned[1]);
-  CKS(readback(H, outs, sizeof(int) * 3 * jobs.size(), st));
+  if (f2) return fail(HSS_ERR_TIMEOUT, "group QRCP barrier gave up (code %d)", f2);
+  if (f3) return fail(HSS_ERR_TIMEOUT, "tensor-core tile product gave up waiting (code %d)", f3);
   double tr_flop = 0.0;
   int tr_m = 0, tr_k = 0;
   double tr_wmax = 0.0;
   for (size_t i = 0; i < reqs.size(); ++i) {
-    Side& s = reqs[i].side ? H->nodes[reqs[i].node].c : H->nodes[reqs[i].node].r;
-    s.qr_k = H->h_pinned[3 * i];
-    s.qr_acc = H->h_pinned[3 * i + 2];
+    Side& s = side_of(reqs[i]);
+    s.qr_k = ho[3 * i];
+    s.qr_acc = ho[3 * i + 2];
     // algorithmic flops: norms, k Householder steps (reflector + trailing
     // dot and update of m-j-1 columns), back substitution for X
     const double m = jobs[i].m, dd = jobs[i].d, k = s.qr_k;
     double f = 2.0 * m * dd;
     for (int j = 0; j < s.qr_k; ++j) f += 4.0 * (dd - j) * (m - j - 1) + 3.0 * (dd - j);
     if (s.qr_acc && k > 0 && m > k) f += k * k * (m - k);
-    H->st.flop_id += f;
+    reqs[i].H->st.flop_id += f;
     tr_flop += f;
     tr_m = std::max(tr_m, jobs[i].m);
     tr_k = std::max(tr_k, s.qr_k);
     tr_wmax = std::max(tr_wmax, f / P[i]);
   }
-  if (H->trace) {
+  if (c.trace) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, H->trace_ev[0], H->trace_ev[1]);
+    cudaEventElapsedTime(&ms, c.trace_ev[0], c.trace_ev[1]);
     // balance: the work per CTA of the busiest group against the mean
     fprintf(stderr,
             "[hss trace] qrcp level %d jobs %zu batches %d ctas %d max_m %d d %d max_k %d  %.3f ms  %.1f GFLOP/s"
             "  balance %.2f\n",
-            H->nodes[reqs[0].node].level, nj, nbatch, ctas_total, tr_m, d, tr_k, ms, tr_flop / (ms * 1e6),
-            tr_flop / std::max(1.0, tr_wmax * ctas_total));
+            reqs[0].H->nodes[reqs[0].node].level, nj, nbatch, ctas_total, tr_m, dmx, tr_k, ms,
+            tr_flop / (ms * 1e6), tr_flop / std::max(1.0, tr_wmax * ctas_total));
   }
   return HSS_OK;
 }
 
 // After an accepted QRCP: permanent X (compacted out of the workspace) and
 // the global skeleton indices tau.I = base(J).
-hss_status finalize_id(hss_matrix_s* H, int node, int side, const double* W, int d,
-                       std::vector<GemmJob>& copies, cudaStream_t st) {
+hss_status finalize_id(hss_matrix_s* H, int node, int side, const double* W, std::vector<GemmJob>& copies,
+                       std::vector<GatherJob>& gathers) {
   Node& t = H->nodes[node];
   Side& s = side ? t.c : t.r;
   s.k = s.qr_k;
-  const int k = s.k, m = s.m;
+  const int k = s.k, m = s.m, d = H->d;
   s.X = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(k, 1) * std::max(m - k, 1));
   s.I = (int*)H->arena.alloc(sizeof(int) * (size_t)std::max(k, 1));
   if (!s.X || !s.I) return fail(HSS_ERR_NOMEM, "device arena allocation failed (ID)");
@@ -935,330 +1097,399 @@ hss_status finalize_id(hss_matrix_s* H, int node, int side, const double* W, int
     copies.push_back(j);
   }
   if (k > 0) {
+    GatherJob g;
     if (t.leaf) {
-      CK(launch_gather_int(H->iota + t.lo, s.piv, s.I, k, nullptr, 0x7fffffff, st));
+      g = {H->iota + t.lo, nullptr, s.piv, s.I, k, 0x7fffffff};
     } else {
       Side& a = side ? H->nodes[t.ch[0]].c : H->nodes[t.ch[0]].r;
       Side& b = side ? H->nodes[t.ch[1]].c : H->nodes[t.ch[1]].r;
-      CK(launch_gather_int(a.I, s.piv, s.I, k, b.I, a.k, st));
+      g = {a.I, b.I, s.piv, s.I, k, a.k};
     }
-    H->launches++;
+    gathers.push_back(g);
   }
   return HSS_OK;
 }
 
-hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
-  const bool dbl = H->o.strategy == HSS_DOUBLING;
-  for (int lev = H->max_level; lev >= 1; --lev) {
-    LevelWork lw;
-    for (int id : H->by_level[lev]) {
-      Node& t = H->nodes[id];
-      if (!t.leaf && (H->nodes[t.ch[0]].state != HSS_COMPRESSED ||
-                      H->nodes[t.ch[1]].state != HSS_COMPRESSED))
-        continue;
-      (t.state == HSS_COMPRESSED ? lw.upd : lw.cand).push_back(id);
-    }
-    if (lw.cand.empty() && lw.upd.empty()) continue;
-    CK(H->timer.mark(PH_MERGE, st));
-    // --- extraction of D (new leaves) and B12/B21 (new non-leaves)
-    std::vector<ExtractJob> ex;
-    auto add_ex = [&](const int* I, int i0, int mi, const int* J, int j0, int nj, double* out, long long ldo) {
-      if (mi <= 0 || nj <= 0) return;
-      ExtractJob e{I, i0, mi, J, j0, nj, out, ldo};
-      ex.push_back(e);
-    };
-    for (int id : lw.cand) {
-      Node& t = H->nodes[id];
-      if (t.state != HSS_UNTOUCHED) continue;
-      if (t.leaf) {
-        if (!t.D) {   // (already there with a user operator)
-          t.D = (double*)H->arena.alloc(sizeof(double) * (size_t)t.size * t.size);
-          if (!t.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
-          add_ex(nullptr, t.lo, t.size, nullptr, t.lo, t.size, t.D, t.size);
+// The Incrementing test (Algorithm 5) of the candidate sides of one level of
+// every listed matrix: all their untested blocks, one round per block, until
+// each side passes or runs out of columns (P18).
+hss_status incrementing_tests(Ctx& c, const std::vector<std::pair<hss_matrix_s*, std::vector<int>>>& cands) {
+  cudaStream_t st = c.st;
+  struct Sd { hss_matrix_s* H; int node, side; };
+  auto block_end = [&](hss_matrix_s* H, int tested) {
+    for (int bnd : H->bounds)
+      if (bnd > tested) return std::min(bnd, H->d);
+    return H->d;
+  };
+  for (;;) {
+    std::vector<Sd> sides;
+    for (auto& hc : cands) {
+      hss_matrix_s* H = hc.first;
+      for (int id : hc.second) {
+        Node& t = H->nodes[id];
+        for (int sd = 0; sd < (H->sym ? 1 : 2); ++sd) {
+          Side& s = sd ? t.c : t.r;
+          if (s.done) s.tested = H->d;
+          else if (H->d > s.tested) sides.push_back({H, id, sd});
         }
-        CKS(alloc_side(H, t.r, true, H->Sg_r + (long long)t.lo * H->dmax, t.size));
         if (H->sym) t.c = t.r;
-        else CKS(alloc_side(H, t.c, true, H->Sg_c + (long long)t.lo * H->dmax, t.size));
-      } else {
-        Node& a = H->nodes[t.ch[0]];
-        Node& b = H->nodes[t.ch[1]];
-        t.B12 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(a.r.k, 1) * std::max(b.c.k, 1));
-        t.B21 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(b.r.k, 1) * std::max(a.c.k, 1));
-        if (!t.B12 || !t.B21) return fail(HSS_ERR_NOMEM, "device arena allocation failed (B)");
-        add_ex(a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, t.B12, std::max(a.r.k, 1));
-        add_ex(b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, t.B21, std::max(b.r.k, 1));
-        CKS(alloc_side(H, t.r, false, nullptr, a.r.k + b.r.k));
-        if (H->sym) t.c = t.r;
-        else CKS(alloc_side(H, t.c, false, nullptr, a.c.k + b.c.k));
       }
     }
-    CKS(extract_blocks(H, ex, st));
-    // --- local samples of non-leaf nodes (upward merge)
-    std::vector<GemmJob> mj;
-    for (int id : lw.cand) {
-      Node& t = H->nodes[id];
-      if (!t.leaf) merge_jobs(H, t, t.state == HSS_UNTOUCHED ? 0 : d_prev, d, mj);
+    if (sides.empty()) return HSS_OK;
+    CK(c.timer.mark(PH_TEST, st));
+    c.scratch.reset();
+    size_t need = 0;
+    for (auto& x : sides) {
+      Side& s = x.side ? x.H->nodes[x.node].c : x.H->nodes[x.node].r;
+      size_t b = block_end(x.H, s.tested) - s.tested, m = std::max(s.m, 1);
+      const size_t pg = (m + inc_group_rows((int)b) - 1) / inc_group_rows((int)b);   // group size bound
+      need += Scratch::rnd(8 * m * b) + Scratch::rnd(8 * std::max<size_t>(std::max(s.q, s.m), 1) * b) +
+              Scratch::rnd(8 * b) + Scratch::rnd(8 * 4) + Scratch::rnd(8) + Scratch::rnd(sizeof(unsigned)) +
+              Scratch::rnd(8 * 2 * std::max<size_t>(pg, 1) * (b + 2));
     }
-    for (int id : lw.upd) {
-      Node& t = H->nodes[id];
-      if (!t.leaf) merge_jobs(H, t, d_prev, d, mj);
+    CK(c.scratch.ensure(need, st));
+    std::vector<IncJob> ij;
+    GemmSet g1, g2, g3;
+    int bmax = 0;
+    for (auto& x : sides) {
+      hss_matrix_s* H = x.H;
+      Node& t = H->nodes[x.node];
+      Side& s = x.side ? t.c : t.r;
+      IncJob j;
+      memset(&j, 0, sizeof j);
+      const int b = block_end(H, s.tested) - s.tested, m = s.m;
+      bmax = std::max(bmax, b);
+      j.S = s.S; j.lds = H->dmax; j.m = m; j.c0 = s.tested; j.b = b;
+      j.Q = s.Q; j.q = s.q;
+      j.Sh = (double*)c.scratch.take(8 * (size_t)std::max(m, 1) * b);
+      j.T = (double*)c.scratch.take(8 * (size_t)std::max(std::max(s.q, m), 1) * b);
+      j.tau = (double*)c.scratch.take(8 * (size_t)b);
+      double sc = tol_scale(H, t.level);
+      j.er = H->o.rtol * sc; j.ea = H->o.atol * sc;
+      j.rho = s.rho;
+      j.hmt = H->o.criterion == HSS_CRIT_HMT;
+      j.hmt_c = j.hmt ? H->o.hmt_alpha * std::sqrt(2.0 / std::acos(-1.0)) : 0.0;
+      j.wait_ns = wait_limit(H);
+      ij.push_back(j);
+      // Sh = S(:, tested:tested+b)
+      GemmJob cp = gemm_job();
+      cp.M = m; cp.N = b; cp.K = 0;
+      cp.C0 = opnd(s.S + s.tested, H->dmax, 1);
+      cp.beta = 1.0;
+      cp.C = j.Sh; cp.c_rs = 1; cp.c_cs = m;
+      g1.add(HSS_PREC_FP64, cp);
+      if (s.q > 0) {
+        GemmJob t1 = gemm_job();   // T = Q^T Sh
+        t1.M = s.q; t1.N = b; t1.K = m;
+        t1.A = opnd(s.Q, 1, H->dmax);
+        t1.B = opnd(j.Sh, 1, m);
+        t1.C = j.T; t1.c_rs = 1; t1.c_cs = s.q;
+        g2.add(H->o.precision, t1);
+        GemmJob t2 = gemm_job();   // Sh -= Q T
+        t2.M = m; t2.N = b; t2.K = s.q;
+        t2.A = opnd(s.Q, H->dmax, 1);
+        t2.B = opnd(j.T, 1, s.q);
+        t2.alpha = -1.0; t2.gamma = 1.0;
+        t2.C = j.Sh; t2.c_rs = 1; t2.c_cs = m;
+        g3.add(H->o.precision, t2);
+      }
     }
-    CKS(run_gemms(H, mj, st, "merge", true));
-
-    // --- strategy test on the candidates
-    std::vector<int> accepted;
-    std::vector<QrcpReq> reqs;
-    if (dbl) {
-      for (int id : lw.cand) {
-        reqs.push_back({id, 0, 1});
-        if (!H->sym) reqs.push_back({id, 1, 1});
+    double* res0 = (double*)c.scratch.take(sizeof(double) * 4 * ij.size());
+    int* flag0 = (int*)c.scratch.take(sizeof(int) * 2 * ij.size());
+    for (size_t i = 0; i < ij.size(); ++i) { ij[i].res = res0 + 4 * i; ij[i].flag = flag0 + 2 * i; }
+    CKS(run_gemm_set(c, g1, "test-copy"));
+    // (I - Q Q^T)^2; in the mixed forms both products take the tensor
+    // cores with the three-term split of the merges (error below 2^-32
+    // of |Q||S| per product, under the samples' own noise); the norms,
+    // the QR and every decision stay FP64
+    for (int rep = 0; rep < 2; ++rep) {
+      CKS(run_gemm_set(c, g2, "test-QtS"));
+      CKS(run_gemm_set(c, g3, "test-S-QT"));
+    }
+    // the rows of each side over a group of CTAs (one cooperative launch
+    // per batch of sides that fits the co-resident slots); blocks wider
+    // than the group kernel takes go to one CTA per side
+    // (only when one CTA per side would leave SMs idle and all groups fit
+    // one launch; a level with many sides keeps one CTA per side)
+    int nsm = 0, cur = 0;
+    CK(cudaGetDevice(&cur));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, cur));
+    bool grouped = bmax <= inc_group_bmax() && (int)ij.size() < nsm;
+    const int gcap = grouped ? inc_group_capacity(bmax) : 0;
+    long long gsum = 0;
+    for (const IncJob& j : ij) {   // the groups at their row widths fit the resident slots
+      const int rows = inc_group_rows(j.b);
+      gsum += (j.m + rows - 1) / rows;
+    }
+    if (gsum > gcap) grouped = false;
+    std::vector<int> P(ij.size(), 1);
+    std::vector<std::pair<size_t, size_t>> gbatches;
+    if (grouped) {
+      for (size_t i = 0; i < ij.size(); ++i) {
+        const int rows = inc_group_rows(ij[i].b);
+        P[i] = std::max(1, (ij[i].m + rows - 1) / rows);
+        ij[i].P = P[i];
+        ij[i].bar = (unsigned*)c.scratch.take(sizeof(unsigned));
+        ij[i].part = (double*)c.scratch.take(sizeof(double) * 2 * (size_t)P[i] * (ij[i].b + 2));
+      }
+      for (size_t b0 = 0; b0 < ij.size();) {
+        size_t b1 = b0;
+        int used = 0;
+        while (b1 < ij.size() && (b1 == b0 || used + P[b1] <= gcap)) used += P[b1++];
+        gbatches.push_back({b0, b1});
+        b0 = b1;
+      }
+    }
+    if (c.scratch.overflow) return fail(HSS_ERR_NOMEM, "test scratch sized too small");
+    Staging sg;
+    const size_t oj = sg.put(ij.data(), ij.size() * sizeof(IncJob));
+    std::vector<size_t> omap;
+    std::vector<int> nmap;
+    for (auto& gb : gbatches) {
+      std::vector<int2> map;
+      for (size_t i = gb.first; i < gb.second; ++i)
+        for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
+      omap.push_back(sg.put(map.data(), map.size() * sizeof(int2)));
+      nmap.push_back((int)map.size());
+    }
+    char* dev;
+    CKS(sg.send(c, &dev));
+    const IncJob* dj = (const IncJob*)(dev + oj);
+    if (c.trace) CK(cudaEventRecord(c.trace_ev[0], st));
+    std::unique_lock<std::mutex> coop(coop_launch_mutex(), std::defer_lock);
+    if (grouped) {
+      CK(cudaMemsetAsync(c.d_flag + 4, 0, sizeof(int), st));
+      for (size_t i = 0; i < ij.size(); ++i) CK(cudaMemsetAsync(ij[i].bar, 0, sizeof(unsigned), st));
+      coop.lock();
+      for (size_t b = 0; b < gbatches.size(); ++b) {
+        CK(launch_inc_group(dj, (const int2*)(dev + omap[b]), nmap[b], bmax, c.d_flag + 4, st));
+        c.launches++;
       }
     } else {
-      // Incrementing: test the untested columns of every side block by block
-      // as they were drawn (d0, then each growth), all sides of the level
-      // together, one round per block, until each side passes or runs out
-      struct Sd { int node, side; };
-      for (;;) {
-        std::vector<Sd> sides;
-        for (int id : lw.cand) {
-          Node& t = H->nodes[id];
-          for (int sd = 0; sd < (H->sym ? 1 : 2); ++sd) {
-            Side& s = sd ? t.c : t.r;
-            if (s.done) s.tested = d;
-            else if (d > s.tested) sides.push_back({id, sd});
+      CK(launch_inc_qr(dj, (int)ij.size(), st));
+      c.launches++;
+    }
+    if (c.trace) {
+      CK(cudaEventRecord(c.trace_ev[1], st));
+      CK(cudaEventSynchronize(c.trace_ev[1]));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c.trace_ev[0], c.trace_ev[1]);
+      int mm = 0, qq = 0;
+      for (auto& x : sides) {
+        const Side& s = x.side ? x.H->nodes[x.node].c : x.H->nodes[x.node].r;
+        mm = std::max(mm, s.m);
+        qq = std::max(qq, s.q);
+      }
+      fprintf(stderr, "[hss trace] inc_qr sides %zu max_m %d max_q %d b %d  %.3f ms\n", sides.size(), mm, qq, bmax, ms);
+    }
+    // the barrier flag, the test flags and the norms in one read-back
+    std::vector<size_t> off;
+    CKS(readback_many(c, {{c.d_flag + 4, sizeof(int)}, {flag0, sizeof(int) * 2 * ij.size()},
+                          {res0, sizeof(double) * 4 * ij.size()}}, off));
+    if (coop.owns_lock()) coop.unlock();
+    const int bar_err = *(const int*)((char*)c.h_pinned + off[0]);
+    if (grouped && bar_err)
+      return fail(HSS_ERR_TIMEOUT, "Incrementing test group barrier gave up (code %d)", bar_err);
+    const int* flags = (const int*)((char*)c.h_pinned + off[1]);
+    const double* res = (const double*)((char*)c.h_pinned + off[2]);
+    for (size_t i = 0; i < sides.size(); ++i) {
+      hss_matrix_s* H = sides[i].H;
+      Side& s = sides[i].side ? H->nodes[sides[i].node].c : H->nodes[sides[i].node].r;
+      s.tested = block_end(H, s.tested);
+      s.q = flags[2 * i + 1];
+      if (s.rho < 0.0 && res[4 * i + 3] >= 0.0) s.rho = res[4 * i + 3];
+      s.done = flags[2 * i] != 0;
+    }
+  }
+}
+
+// One pass of Algorithm 3 (the sweep of CompressNodeAdaptive over the tree)
+// for every listed matrix, in lockstep: step s takes level max_level - s of
+// each matrix (the leaves of all of them first), and every phase of a step
+// is one launch over the nodes of all matrices at that step.
+hss_status run_pass(Ctx& c, const std::vector<hss_matrix_s*>& act) {
+  cudaStream_t st = c.st;
+  int depth = 0;
+  for (hss_matrix_s* H : act) depth = std::max(depth, H->max_level);
+  for (int sstep = 0; sstep < depth; ++sstep) {
+    struct Lv { hss_matrix_s* H; int lev; std::vector<int> cand, upd; };
+    std::vector<Lv> L;
+    for (hss_matrix_s* H : act) {
+      const int lev = H->max_level - sstep;
+      if (lev < 1) continue;
+      Lv lv{H, lev, {}, {}};
+      for (int id : H->by_level[lev]) {
+        Node& t = H->nodes[id];
+        if (!t.leaf && (H->nodes[t.ch[0]].state != HSS_COMPRESSED || H->nodes[t.ch[1]].state != HSS_COMPRESSED))
+          continue;
+        (t.state == HSS_COMPRESSED ? lv.upd : lv.cand).push_back(id);
+      }
+      if (!lv.cand.empty() || !lv.upd.empty()) L.push_back(std::move(lv));
+    }
+    if (L.empty()) continue;
+    CK(c.timer.mark(PH_MERGE, st));
+    // --- extraction of D (new leaves) and B12/B21 (new non-leaves)
+    ExtractSet ex;
+    for (Lv& lv : L) {
+      hss_matrix_s* H = lv.H;
+      auto add_ex = [&](const int* I, int i0, int mi, const int* J, int j0, int nj, double* out, long long ldo) {
+        if (mi <= 0 || nj <= 0) return;
+        ExtractJob e;
+        memset(&e, 0, sizeof e);
+        e.I = I; e.i0 = i0; e.mi = mi; e.J = J; e.j0 = j0; e.nj = nj; e.out = out; e.ldo = ldo;
+        ex.of(H).push_back(e);
+      };
+      for (int id : lv.cand) {
+        Node& t = H->nodes[id];
+        if (t.state != HSS_UNTOUCHED) continue;
+        if (t.leaf) {
+          if (!t.D) {   // (already there with a user operator)
+            t.D = (double*)H->arena.alloc(sizeof(double) * (size_t)t.size * t.size);
+            if (!t.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
+            add_ex(nullptr, t.lo, t.size, nullptr, t.lo, t.size, t.D, t.size);
           }
+          CKS(alloc_side(H, t.r, true, H->Sg_r + (long long)t.lo * H->dmax, t.size));
           if (H->sym) t.c = t.r;
-        }
-        if (sides.empty()) break;
-        CK(H->timer.mark(PH_TEST, st));
-        H->scratch.reset();
-        auto block_end = [&](int tested) {
-          for (int bnd : H->bounds)
-            if (bnd > tested) return std::min(bnd, d);
-          return d;
-        };
-        size_t need = 0;
-        for (auto& x : sides) {
-          Side& s = x.side ? H->nodes[x.node].c : H->nodes[x.node].r;
-          size_t b = block_end(s.tested) - s.tested, m = std::max(s.m, 1);
-          const size_t pg = (m + inc_group_rows((int)b) - 1) / inc_group_rows((int)b);   // group size bound
-          need += Scratch::rnd(8 * m * b) + Scratch::rnd(8 * std::max<size_t>(std::max(s.q, s.m), 1) * b) +
-                  Scratch::rnd(8 * b) + Scratch::rnd(8 * 4) + Scratch::rnd(8) + Scratch::rnd(sizeof(unsigned)) +
-                  Scratch::rnd(8 * 2 * std::max<size_t>(pg, 1) * (b + 2));
-        }
-        CK(H->scratch.ensure(need, st));
-        std::vector<IncJob> ij;
-        std::vector<GemmJob> g1, g2, g3;
-        double* res0 = nullptr;
-        int* flag0 = nullptr;
-        int bmax = 0;
-        for (auto& x : sides) {
-          Node& t = H->nodes[x.node];
-          Side& s = x.side ? t.c : t.r;
-          IncJob j;
-          memset(&j, 0, sizeof j);
-          const int b = block_end(s.tested) - s.tested, m = s.m;
-          bmax = std::max(bmax, b);
-          j.S = s.S; j.lds = H->dmax; j.m = m; j.c0 = s.tested; j.b = b;
-          j.Q = s.Q; j.q = s.q;
-          j.Sh = (double*)H->scratch.take(8 * (size_t)std::max(m, 1) * b);
-          j.T = (double*)H->scratch.take(8 * (size_t)std::max(std::max(s.q, m), 1) * b);
-          j.tau = (double*)H->scratch.take(8 * (size_t)b);
-          double sc = tol_scale(H, t.level);
-          j.er = H->o.rtol * sc; j.ea = H->o.atol * sc;
-          j.rho = s.rho;
-          j.hmt = H->o.criterion == HSS_CRIT_HMT;
-          j.hmt_c = j.hmt ? H->o.hmt_alpha * std::sqrt(2.0 / std::acos(-1.0)) : 0.0;
-          j.wait_ns = wait_limit(H);
-          ij.push_back(j);
-          // Sh = S(:, tested:tested+b)
-          GemmJob c = gemm_job();
-          c.M = m; c.N = b; c.K = 0;
-          c.C0 = opnd(s.S + s.tested, H->dmax, 1);
-          c.beta = 1.0;
-          c.C = j.Sh; c.c_rs = 1; c.c_cs = m;
-          g1.push_back(c);
-          if (s.q > 0) {
-            GemmJob t1 = gemm_job();   // T = Q^T Sh
-            t1.M = s.q; t1.N = b; t1.K = m;
-            t1.A = opnd(s.Q, 1, H->dmax);
-            t1.B = opnd(j.Sh, 1, m);
-            t1.C = j.T; t1.c_rs = 1; t1.c_cs = s.q;
-            g2.push_back(t1);
-            GemmJob t2 = gemm_job();   // Sh -= Q T
-            t2.M = m; t2.N = b; t2.K = s.q;
-            t2.A = opnd(s.Q, H->dmax, 1);
-            t2.B = opnd(j.T, 1, s.q);
-            t2.alpha = -1.0; t2.gamma = 1.0;
-            t2.C = j.Sh; t2.c_rs = 1; t2.c_cs = m;
-            g3.push_back(t2);
-          }
-        }
-        res0 = (double*)H->scratch.take(sizeof(double) * 4 * ij.size());
-        flag0 = (int*)H->scratch.take(sizeof(int) * 2 * ij.size());
-        for (size_t i = 0; i < ij.size(); ++i) { ij[i].res = res0 + 4 * i; ij[i].flag = flag0 + 2 * i; }
-        CKS(run_gemms(H, g1, st, "test-copy"));
-        // (I - Q Q^T)^2; in the mixed forms both products take the tensor
-        // cores with the three-term split of the merges (error below 2^-32
-        // of |Q||S| per product, under the samples' own noise); the norms,
-        // the QR and every decision stay FP64
-        for (int rep = 0; rep < 2; ++rep) {
-          CKS(run_gemms(H, g2, st, "test-QtS", true));
-          CKS(run_gemms(H, g3, st, "test-S-QT", true));
-        }
-        // the rows of each side over a group of CTAs (one cooperative launch
-        // per batch of sides that fits the co-resident slots); blocks wider
-        // than the group kernel takes go to one CTA per side
-        // (only when one CTA per side would leave SMs idle and all groups fit
-        // one launch; a level with many sides keeps one CTA per side)
-        int nsm = 0, cur = 0;
-        CK(cudaGetDevice(&cur));
-        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, cur));
-        bool grouped = bmax <= inc_group_bmax() && (int)ij.size() < nsm;
-        const int gcap = grouped ? inc_group_capacity(bmax) : 0;
-        long long gsum = 0;
-        for (const IncJob& j : ij) {   // the groups at their row widths fit the resident slots
-          const int rows = inc_group_rows(j.b);
-          gsum += (j.m + rows - 1) / rows;
-        }
-        if (gsum > gcap) grouped = false;
-        std::vector<int> P(ij.size(), 1);
-        std::vector<std::pair<size_t, size_t>> gbatches;
-        if (grouped) {
-          const int cap = gcap;
-          for (size_t i = 0; i < ij.size(); ++i) {
-            const int rows = inc_group_rows(ij[i].b);
-            P[i] = std::max(1, (ij[i].m + rows - 1) / rows);
-            ij[i].P = P[i];
-            ij[i].bar = (unsigned*)H->scratch.take(sizeof(unsigned));
-            ij[i].part = (double*)H->scratch.take(sizeof(double) * 2 * (size_t)P[i] * (ij[i].b + 2));
-          }
-          for (size_t b0 = 0; b0 < ij.size();) {
-            size_t b1 = b0;
-            int used = 0;
-            while (b1 < ij.size() && (b1 == b0 || used + P[b1] <= cap)) used += P[b1++];
-            gbatches.push_back({b0, b1});
-            b0 = b1;
-          }
-        }
-        IncJob* dj;
-        CKS(upload_jobs(H, ij, &dj, st));
-        if (H->scratch.overflow) return fail(HSS_ERR_NOMEM, "test scratch sized too small");
-        if (H->trace) CK(cudaEventRecord(H->trace_ev[0], st));
-        if (grouped) {
-          CK(cudaMemsetAsync(H->d_flag + 4, 0, sizeof(int), st));
-          std::unique_lock<std::mutex> coop(coop_launch_mutex());
-          for (auto& gb : gbatches) {
-            std::vector<int2> map;
-            for (size_t i = gb.first; i < gb.second; ++i) {
-              CK(cudaMemsetAsync(ij[i].bar, 0, sizeof(unsigned), st));
-              for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
-            }
-            int2* dm;
-            CKS(upload_jobs(H, map, &dm, st));
-            CK(launch_inc_group(dj, dm, (int)map.size(), bmax, H->d_flag + 4, st));
-            CK(cudaFreeAsync(dm, st));
-            H->launches++;
-          }
-          CKS(readback(H, H->d_flag + 4, sizeof(int), st));
-          coop.unlock();
-          if (H->h_pinned[0])
-            return fail(HSS_ERR_TIMEOUT, "Incrementing test group barrier gave up (code %d)", H->h_pinned[0]);
+          else CKS(alloc_side(H, t.c, true, H->Sg_c + (long long)t.lo * H->dmax, t.size));
         } else {
-          CK(launch_inc_qr(dj, (int)ij.size(), st));
-          H->launches++;
-        }
-        if (H->trace) {
-          CK(cudaEventRecord(H->trace_ev[1], st));
-          CK(cudaEventSynchronize(H->trace_ev[1]));
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, H->trace_ev[0], H->trace_ev[1]);
-          int mm = 0, qq = 0;
-          for (auto& x : sides) {
-            const Side& s = x.side ? H->nodes[x.node].c : H->nodes[x.node].r;
-            mm = std::max(mm, s.m);
-            qq = std::max(qq, s.q);
-          }
-          fprintf(stderr, "[hss trace] inc_qr level %d sides %zu max_m %d max_q %d b %d  %.3f ms\n", lev,
-                  sides.size(), mm, qq, bmax, ms);
-        }
-        CK(cudaFreeAsync(dj, st));
-        // read flags and res together
-        std::vector<int> flags(2 * ij.size());
-        std::vector<double> res(4 * ij.size());
-        CK(cudaMemcpyAsync(flags.data(), flag0, sizeof(int) * flags.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(res.data(), res0, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        H->st.bytes_d2h += (long long)(sizeof(int) * flags.size() + sizeof(double) * res.size());
-        for (size_t i = 0; i < sides.size(); ++i) {
-          Side& s = sides[i].side ? H->nodes[sides[i].node].c : H->nodes[sides[i].node].r;
-          s.tested = block_end(s.tested);
-          s.q = flags[2 * i + 1];
-          if (s.rho < 0.0 && res[4 * i + 3] >= 0.0) s.rho = res[4 * i + 3];
-          s.done = flags[2 * i] != 0;
+          Node& a = H->nodes[t.ch[0]];
+          Node& b = H->nodes[t.ch[1]];
+          t.B12 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(a.r.k, 1) * std::max(b.c.k, 1));
+          t.B21 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(b.r.k, 1) * std::max(a.c.k, 1));
+          if (!t.B12 || !t.B21) return fail(HSS_ERR_NOMEM, "device arena allocation failed (B)");
+          add_ex(a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, t.B12, std::max(a.r.k, 1));
+          add_ex(b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, t.B21, std::max(b.r.k, 1));
+          CKS(alloc_side(H, t.r, false, nullptr, a.r.k + b.r.k));
+          if (H->sym) t.c = t.r;
+          else CKS(alloc_side(H, t.c, false, nullptr, a.c.k + b.c.k));
         }
       }
-      for (int id : lw.cand) {
+    }
+    CKS(run_extract(c, ex));
+    // --- local samples of non-leaf nodes (upward merge)
+    GemmSet mj;
+    for (Lv& lv : L) {
+      hss_matrix_s* H = lv.H;
+      std::vector<GemmJob> j;
+      for (int id : lv.cand) {
         Node& t = H->nodes[id];
-        if (H->sym) t.c = t.r;
-        if (t.r.done && t.c.done) {
-          reqs.push_back({id, 0, 0});
-          if (!H->sym) reqs.push_back({id, 1, 0});
-        } else {
-          t.state = HSS_PARTIALLY_COMPRESSED;
+        if (!t.leaf) merge_jobs(H, t, t.state == HSS_UNTOUCHED ? 0 : H->d_prev, H->d, j);
+      }
+      for (int id : lv.upd) {
+        Node& t = H->nodes[id];
+        if (!t.leaf) merge_jobs(H, t, H->d_prev, H->d, j);
+      }
+      for (auto& g : j) mj.add(H->o.precision, g);
+    }
+    CKS(run_gemm_set(c, mj, "merge"));
+
+    // --- strategy test on the candidates
+    std::vector<QrcpReq> reqs;
+    std::vector<std::pair<hss_matrix_s*, std::vector<int>>> inc;
+    for (Lv& lv : L) {
+      hss_matrix_s* H = lv.H;
+      if (H->o.strategy == HSS_DOUBLING) {
+        for (int id : lv.cand) {
+          reqs.push_back({H, id, 0, 1});
+          if (!H->sym) reqs.push_back({H, id, 1, 1});
+        }
+      } else if (!lv.cand.empty()) {
+        inc.push_back({H, lv.cand});
+      }
+    }
+    if (!inc.empty()) {
+      CKS(incrementing_tests(c, inc));
+      for (auto& hc : inc) {
+        hss_matrix_s* H = hc.first;
+        for (int id : hc.second) {
+          Node& t = H->nodes[id];
+          if (H->sym) t.c = t.r;
+          if (t.r.done && t.c.done) {
+            reqs.push_back({H, id, 0, 0});
+            if (!H->sym) reqs.push_back({H, id, 1, 0});
+          } else {
+            t.state = HSS_PARTIALLY_COMPRESSED;
+          }
         }
       }
     }
     std::vector<double*> wbuf;
-    CKS(run_qrcp(H, reqs, d, st, wbuf));
-    CK(H->timer.mark(PH_MERGE, st));
-    std::vector<GemmJob> copies, rj;
+    CKS(run_qrcp(c, reqs, wbuf));
+    CK(c.timer.mark(PH_MERGE, st));
+    std::vector<GemmJob> copies;
+    std::vector<GatherJob> gathers;
+    std::vector<std::pair<hss_matrix_s*, int>> accepted;
     // the requests come as (row side, column side) pairs, or one row-side
     // request per node with the symmetric option (the column side copies it)
-    const size_t per = H->sym ? 1 : 2;
-    for (size_t i = 0; i + per - 1 < reqs.size(); i += per) {
+    for (size_t i = 0; i < reqs.size();) {
+      hss_matrix_s* H = reqs[i].H;
+      const size_t per = H->sym ? 1 : 2;
       Node& t = H->nodes[reqs[i].node];
       if (H->sym) t.c = t.r;
       if (t.r.qr_acc && t.c.qr_acc) {
-        CKS(finalize_id(H, reqs[i].node, 0, wbuf[i], d, copies, st));
+        CKS(finalize_id(H, reqs[i].node, 0, wbuf[i], copies, gathers));
         if (H->sym) t.c = t.r;
-        else CKS(finalize_id(H, reqs[i].node, 1, wbuf[i + 1], d, copies, st));
+        else CKS(finalize_id(H, reqs[i].node, 1, wbuf[i + 1], copies, gathers));
         t.state = HSS_COMPRESSED;
         t.Rr = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(t.c.k, 1) * H->dmax);
         t.Rc = H->sym ? t.Rr : (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(t.r.k, 1) * H->dmax);
         if (!t.Rr || !t.Rc) return fail(HSS_ERR_NOMEM, "device arena allocation failed (reduced R)");
-        accepted.push_back(reqs[i].node);
+        accepted.push_back({H, reqs[i].node});
       } else {
         t.state = HSS_PARTIALLY_COMPRESSED;
       }
+      i += per;
     }
-    CKS(run_gemms(H, copies, st, "x-copy"));
-    for (int id : accepted) reduce_jobs(H, H->nodes[id], 0, d, rj);
-    for (int id : lw.upd) reduce_jobs(H, H->nodes[id], d_prev, d, rj);
-    CKS(run_gemms(H, rj, st, "reduce", true));
+    CKS(run_gathers(c, gathers));
+    CKS(run_gemms(c, copies, "x-copy"));
+    GemmSet rj;
+    for (auto& a : accepted) {
+      std::vector<GemmJob> j;
+      reduce_jobs(a.first, a.first->nodes[a.second], 0, a.first->d, j);
+      for (auto& g : j) rj.add(a.first->o.precision, g);
+    }
+    for (Lv& lv : L) {
+      std::vector<GemmJob> j;
+      for (int id : lv.upd) reduce_jobs(lv.H, lv.H->nodes[id], lv.H->d_prev, lv.H->d, j);
+      for (auto& g : j) rj.add(lv.H->o.precision, g);
+    }
+    CKS(run_gemm_set(c, rj, "reduce"));
   }
-  Node& root = H->nodes[0];
-  if (root.leaf || (H->nodes[root.ch[0]].state == HSS_COMPRESSED &&
-                    H->nodes[root.ch[1]].state == HSS_COMPRESSED)) {
-    if (root.leaf && root.state == HSS_UNTOUCHED && !root.D) {
-      root.D = (double*)H->arena.alloc(sizeof(double) * (size_t)root.size * root.size);
-      if (!root.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
-      CKS(extract_blocks(H, {{nullptr, 0, root.size, nullptr, 0, root.size, root.D, root.size}}, st));
-    }
-    if (!root.leaf && root.state == HSS_UNTOUCHED) {
-      // the root keeps B12 = A(nu1.I^r, nu2.I^c) and B21 = A(nu2.I^r, nu1.I^c)
-      Node& a = H->nodes[root.ch[0]];
-      Node& b = H->nodes[root.ch[1]];
-      root.B12 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(a.r.k, 1) * std::max(b.c.k, 1));
-      root.B21 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(b.r.k, 1) * std::max(a.c.k, 1));
-      if (!root.B12 || !root.B21) return fail(HSS_ERR_NOMEM, "device arena allocation failed (B)");
-      std::vector<ExtractJob> ex;
-      if (a.r.k > 0 && b.c.k > 0) ex.push_back({a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, root.B12, std::max(a.r.k, 1)});
-      if (b.r.k > 0 && a.c.k > 0) ex.push_back({b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, root.B21, std::max(b.r.k, 1)});
-      CKS(extract_blocks(H, ex, st));
+  // the roots: COMPRESSED once both children are (Algorithm 3), keeping
+  // B12 = A(nu1.I^r, nu2.I^c), B21 = A(nu2.I^r, nu1.I^c), or D for a root leaf
+  ExtractSet ex;
+  for (hss_matrix_s* H : act) {
+    Node& root = H->nodes[0];
+    if (!(root.leaf || (H->nodes[root.ch[0]].state == HSS_COMPRESSED &&
+                        H->nodes[root.ch[1]].state == HSS_COMPRESSED)))
+      continue;
+    if (root.state == HSS_UNTOUCHED) {
+      auto add = [&](const int* I, int i0, int mi, const int* J, int j0, int nj, double* out, long long ldo) {
+        if (mi <= 0 || nj <= 0) return;
+        ExtractJob e;
+        memset(&e, 0, sizeof e);
+        e.I = I; e.i0 = i0; e.mi = mi; e.J = J; e.j0 = j0; e.nj = nj; e.out = out; e.ldo = ldo;
+        ex.of(H).push_back(e);
+      };
+      if (root.leaf) {
+        if (!root.D) {
+          root.D = (double*)H->arena.alloc(sizeof(double) * (size_t)root.size * root.size);
+          if (!root.D) return fail(HSS_ERR_NOMEM, "device arena allocation failed (D)");
+          add(nullptr, 0, root.size, nullptr, 0, root.size, root.D, root.size);
+        }
+      } else {
+        Node& a = H->nodes[root.ch[0]];
+        Node& b = H->nodes[root.ch[1]];
+        root.B12 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(a.r.k, 1) * std::max(b.c.k, 1));
+        root.B21 = (double*)H->arena.alloc(sizeof(double) * (size_t)std::max(b.r.k, 1) * std::max(a.c.k, 1));
+        if (!root.B12 || !root.B21) return fail(HSS_ERR_NOMEM, "device arena allocation failed (B)");
+        add(a.r.I, 0, a.r.k, b.c.I, 0, b.c.k, root.B12, std::max(a.r.k, 1));
+        add(b.r.I, 0, b.r.k, a.c.I, 0, a.c.k, root.B21, std::max(b.r.k, 1));
+      }
     }
     root.state = HSS_COMPRESSED;
   }
+  CKS(run_extract(c, ex));
   return HSS_OK;
 }
 
@@ -1270,7 +1501,7 @@ hss_status run_pass(hss_matrix_s* H, int d_prev, int d, cudaStream_t st) {
 // reproduce A exactly outside the compressed subtrees.  The blocks take
 // sum 2 |nu1| |nu2| doubles; when that exceeds half of the free device
 // memory they are not kept and the handle holds no usable generators.
-hss_status keep_dense_blocks(hss_matrix_s* H, cudaStream_t st) {
+hss_status keep_dense_blocks(Ctx& c, hss_matrix_s* H) {
   double need = 0.0;
   for (auto& t : H->nodes)
     if (!t.leaf && t.state != HSS_COMPRESSED)
@@ -1278,7 +1509,7 @@ hss_status keep_dense_blocks(hss_matrix_s* H, cudaStream_t st) {
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
   if (need > 0.5 * (double)fr) return HSS_OK;
-  std::vector<ExtractJob> ex;
+  ExtractSet ex;
   for (auto& t : H->nodes) {
     if (t.leaf || t.state == HSS_COMPRESSED) continue;
     const Node& a = H->nodes[t.ch[0]];
@@ -1286,30 +1517,28 @@ hss_status keep_dense_blocks(hss_matrix_s* H, cudaStream_t st) {
     t.F12 = (double*)H->arena.alloc(sizeof(double) * (size_t)a.size * b.size);
     t.F21 = (double*)H->arena.alloc(sizeof(double) * (size_t)b.size * a.size);
     if (!t.F12 || !t.F21) return fail(HSS_ERR_NOMEM, "device allocation of the uncompressed blocks failed");
-    ex.push_back({nullptr, a.lo, a.size, nullptr, b.lo, b.size, t.F12, a.size});
-    ex.push_back({nullptr, b.lo, b.size, nullptr, a.lo, a.size, t.F21, b.size});
+    ExtractJob e;
+    memset(&e, 0, sizeof e);
+    e.i0 = a.lo; e.mi = a.size; e.j0 = b.lo; e.nj = b.size; e.out = t.F12; e.ldo = a.size;
+    ex.of(H).push_back(e);
+    e.i0 = b.lo; e.mi = b.size; e.j0 = a.lo; e.nj = a.size; e.out = t.F21; e.ldo = b.size;
+    ex.of(H).push_back(e);
   }
-  CK(H->timer.mark(PH_MERGE, st));
-  CKS(extract_blocks(H, ex, st));
+  CK(c.timer.mark(PH_MERGE, c.st));
+  CKS(run_extract(c, ex));
   H->partial = true;
   return HSS_OK;
 }
 
-hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st, hss_matrix_s* H) {
+// Everything a compression needs before its first pass: tree, leaf labels,
+// sample and R buffers, and (with a user operator) the packed leaf blocks D.
+hss_status setup(Ctx& c, const hss_source* A, const hss_opts* o, hss_matrix_s* H, ExtractSet& leafD) {
   const int n = A->n;
   H->n = n;
   H->o = *o;
   H->src = *A;
   H->dmax = std::min(o->d_max, n);
   CK(cudaGetDevice(&H->device));
-  {
-    const char* tr = getenv("HSS_TRACE");
-    H->trace = tr && tr[0] == '1';
-    if (H->trace) {
-      CK(cudaEventCreate(&H->trace_ev[0]));
-      CK(cudaEventCreate(&H->trace_ev[1]));
-    }
-  }
   build_tree(n, o->leaf, H->nodes);
   H->max_level = 0;
   for (auto& t : H->nodes) H->max_level = std::max(H->max_level, t.level);
@@ -1329,17 +1558,17 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
   const size_t nd = (size_t)n * H->dmax;
   H->leaf_id = (int*)H->arena.alloc(sizeof(int) * n);
   H->iota = (int*)H->arena.alloc(sizeof(int) * n);
-  H->d_flag = (int*)H->arena.alloc(256);
   H->Sg_r = (double*)H->arena.alloc(sizeof(double) * nd);
   H->sym = o->symmetric != 0;
   H->Sg_c = H->sym ? H->Sg_r : (double*)H->arena.alloc(sizeof(double) * nd);
   const bool mixed = o->precision != HSS_PREC_FP64;
-  const bool own_R = (o->R == nullptr) || mixed;
-  if (own_R) H->R = (double*)H->arena.alloc(sizeof(double) * nd);
+  H->own_R = (o->R == nullptr) || mixed;
+  if (H->own_R) H->R = (double*)H->arena.alloc(sizeof(double) * nd);
   else H->R = const_cast<double*>(o->R);
-  if (!H->leaf_id || !H->iota || !H->d_flag || !H->Sg_r || !H->Sg_c || !H->R)
+  if (!H->leaf_id || !H->iota || !H->Sg_r || !H->Sg_c || !H->R)
     return fail(HSS_ERR_NOMEM, "device allocation of %zu bytes for samples failed", 3 * nd * 8);
-  CKS(upload(H, H->leaf_id, lid.data(), sizeof(int) * n, st));
+  CKS(upload(c, H->leaf_id, lid.data(), sizeof(int) * n));
+  CKS(upload(c, H->iota, io.data(), sizeof(int) * n));
   if (o->op) {
     std::vector<int> lb;
     for (auto& t : H->nodes)
@@ -1347,10 +1576,7 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     lb.push_back(n);
     H->leaf_lo = (int*)H->arena.alloc(sizeof(int) * lb.size());
     if (!H->leaf_lo) return fail(HSS_ERR_NOMEM, "device allocation of the leaf bounds failed");
-    CKS(upload(H, H->leaf_lo, lb.data(), sizeof(int) * lb.size(), st));
-  }
-  CKS(upload(H, H->iota, io.data(), sizeof(int) * n, st));
-  if (o->op) {
+    CKS(upload(c, H->leaf_lo, lb.data(), sizeof(int) * lb.size()));
     // the leaf blocks D_tau = A(I_tau, I_tau) first, packed: every sampling
     // pass removes D_tau R(I_tau) from the operator's product (Algorithm 2)
     std::vector<long long> off;
@@ -1363,55 +1589,129 @@ hss_status compress_impl(const hss_source* A, const hss_opts* o, cudaStream_t st
     H->leaf_D = (double*)H->arena.alloc(sizeof(double) * (size_t)tot);
     H->leaf_doff = (long long*)H->arena.alloc(sizeof(long long) * off.size());
     if (!H->leaf_D || !H->leaf_doff) return fail(HSS_ERR_NOMEM, "device allocation of the leaf blocks failed");
-    CKS(upload(H, H->leaf_doff, off.data(), sizeof(long long) * off.size(), st));
-    std::vector<ExtractJob> ex;
+    CKS(upload(c, H->leaf_doff, off.data(), sizeof(long long) * off.size()));
     size_t q = 0;
     for (auto& t : H->nodes)
       if (t.leaf) {
         t.D = H->leaf_D + off[q++];
-        ex.push_back({nullptr, t.lo, t.size, nullptr, t.lo, t.size, t.D, t.size});
+        ExtractJob e;
+        memset(&e, 0, sizeof e);
+        e.i0 = t.lo; e.mi = t.size; e.j0 = t.lo; e.nj = t.size; e.out = t.D; e.ldo = t.size;
+        leafD.of(H).push_back(e);
       }
-    CK(H->timer.mark(PH_MERGE, st));
-    CKS(extract_blocks(H, ex, st));
   }
-  CK(cudaMemsetAsync(H->d_flag, 0, 256, st));
+  H->d = std::min(o->d0, H->dmax);
+  H->d_prev = 0;
+  H->bounds.assign(1, H->d);
+  return HSS_OK;
+}
 
-  CK(H->timer.mark(PH_OTHER, st));
-  int d = std::min(o->d0, H->dmax), d_prev = 0;
-  H->bounds.assign(1, d);
-  CKS(sample_columns(H, 0, d, st, own_R));
-  for (;;) {
-    CKS(run_pass(H, d_prev, d, st));
-    if (H->nodes[0].state == HSS_COMPRESSED) { H->converged = 1; break; }
-    if (d >= H->dmax) break;
-    int dd = (o->strategy == HSS_DOUBLING) ? d : o->dd;
-    dd = std::min(dd, H->dmax - d);
-    CKS(sample_columns(H, d, d + dd, st, own_R));
-    d_prev = d;
-    d += dd;
-    H->bounds.push_back(d);
-    H->n_adapt++;
+// HSSCompressAdaptive (Algorithm 3) for a list of matrices in lockstep: all
+// first samples, then passes of the tree sweep (run_pass) over the matrices
+// that are not done, each followed by the growth of the sample of those
+// whose root is not COMPRESSED (Doubling: d more columns; Incrementing: dd),
+// until every root is COMPRESSED or at d_max.  One read-back of the sampling
+// flags per round of sampling.
+hss_status compress_all(Ctx& c, const std::vector<const hss_source*>& A, const std::vector<const hss_opts*>& O,
+                        std::vector<hss_matrix_s*>& Hs) {
+  CKS(c.flags((int)Hs.size()));
+  CK(c.timer.mark(PH_OTHER, c.st));
+  ExtractSet leafD;
+  for (size_t i = 0; i < Hs.size(); ++i) {
+    Hs[i]->slot = (int)i;
+    CKS(setup(c, A[i], O[i], Hs[i], leafD));
   }
-  CK(H->timer.mark(PH_OTHER, st));
-  if (H->packA) {
-    CK(cudaFreeAsync(H->packA, st));
-    H->packA = nullptr;
+  if (!leafD.per.empty()) {
+    CK(c.timer.mark(PH_MERGE, c.st));
+    CKS(run_extract(c, leafD));
   }
-  if (!H->converged) CKS(keep_dense_blocks(H, st));
-  CKS(readback(H, H->d_flag + 3, sizeof(int), st));
-  if (H->h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "tensor-core tile product gave up waiting (code %d)", H->h_pinned[0]);
-  H->d_final = d;
-  H->usable = H->converged != 0 || H->partial;
+  for (hss_matrix_s* H : Hs) CKS(sample_columns(c, H, 0, H->d));
+  CKS(sample_check(c, Hs));
+  std::vector<hss_matrix_s*> act = Hs;
+  while (!act.empty()) {
+    CKS(run_pass(c, act));
+    std::vector<hss_matrix_s*> next;
+    for (hss_matrix_s* H : act) {
+      if (H->nodes[0].state == HSS_COMPRESSED) { H->converged = 1; H->done = true; continue; }
+      if (H->d >= H->dmax) { H->done = true; continue; }
+      int dd = (H->o.strategy == HSS_DOUBLING) ? H->d : H->o.dd;
+      dd = std::min(dd, H->dmax - H->d);
+      CKS(sample_columns(c, H, H->d, H->d + dd));
+      H->d_prev = H->d;
+      H->d += dd;
+      H->bounds.push_back(H->d);
+      H->n_adapt++;
+      next.push_back(H);
+    }
+    if (!next.empty()) CKS(sample_check(c, next));
+    act.swap(next);
+  }
+  CK(c.timer.mark(PH_OTHER, c.st));
+  for (hss_matrix_s* H : Hs) {
+    if (H->packA) {
+      CK(cudaFreeAsync(H->packA, c.st));
+      H->packA = nullptr;
+    }
+    if (!H->converged) CKS(keep_dense_blocks(c, H));
+  }
+  CKS(readback(c, c.d_flag + 3, sizeof(int)));
+  if (c.h_pinned[0]) return fail(HSS_ERR_TIMEOUT, "tensor-core tile product gave up waiting (code %d)", c.h_pinned[0]);
   double ph[PH_N];
-  H->timer.sum(ph, PH_N);
-  H->st.ms_sample = ph[PH_SAMPLE];
-  H->st.ms_rng = ph[PH_RNG];
-  H->st.ms_id = ph[PH_ID];
-  H->st.ms_test = ph[PH_TEST];
-  H->st.ms_merge = ph[PH_MERGE] + ph[PH_OTHER];
-  H->st.ms_total = ph[PH_N - 1];
-  H->timer.clear();
-  H->scratch.release();
+  c.timer.sum(ph, PH_N);
+  for (size_t i = 0; i < Hs.size(); ++i) {
+    hss_matrix_s* H = Hs[i];
+    H->d_final = H->d;
+    H->usable = H->converged != 0 || H->partial;
+    // the phases of a batched call are shared by its matrices; the launch and
+    // byte counts are the call's, reported with its first matrix
+    H->st.ms_sample = ph[PH_SAMPLE];
+    H->st.ms_rng = ph[PH_RNG];
+    H->st.ms_id = ph[PH_ID];
+    H->st.ms_test = ph[PH_TEST];
+    H->st.ms_merge = ph[PH_MERGE] + ph[PH_OTHER];
+    H->st.ms_total = ph[PH_N - 1];
+    H->st.launches = i == 0 ? c.launches : 0;
+    H->st.bytes_h2d = i == 0 ? c.bytes_h2d : 0;
+    H->st.bytes_d2h = i == 0 ? c.bytes_d2h : 0;
+    H->st.n = H->n;
+    H->st.n_nodes = (int)H->nodes.size();
+    H->st.levels = H->max_level + 1;
+    H->st.d_final = H->d_final;
+    H->st.n_adapt = H->n_adapt;
+    H->st.converged = H->converged;
+    for (size_t q = 1; q < H->nodes.size(); ++q) {
+      H->st.max_rank_r = std::max(H->st.max_rank_r, H->nodes[q].r.k);
+      H->st.max_rank_c = std::max(H->st.max_rank_c, H->nodes[q].c.k);
+    }
+  }
+  return HSS_OK;
+}
+
+hss_status check_opts(const hss_source* A, const hss_opts* o) {
+  CKS(check_source(A));
+  if (!o) return fail(HSS_ERR_ARG, "opts is NULL");
+  if (o->leaf < 1) return fail(HSS_ERR_ARG, "leaf must be >= 1 (got %d)", o->leaf);
+  if (o->d0 < 1 || o->d_max < 1) return fail(HSS_ERR_ARG, "d0 and d_max must be >= 1");
+  if (o->strategy != HSS_DOUBLING && o->strategy != HSS_INCREMENTING)
+    return fail(HSS_ERR_ARG, "unknown strategy %d", o->strategy);
+  if (o->strategy == HSS_INCREMENTING && o->dd < 1) return fail(HSS_ERR_ARG, "dd must be >= 1");
+  if (o->precision < HSS_PREC_FP64 || o->precision > HSS_PREC_BF16X3)
+    return fail(HSS_ERR_ARG, "unknown precision %d", o->precision);
+  if (!(o->rtol >= 0.0) || !(o->atol >= 0.0)) return fail(HSS_ERR_ARG, "tolerances must be >= 0");
+  if (o->wait_limit_ns < 0) return fail(HSS_ERR_ARG, "wait_limit_ns must be >= 0");
+  if (o->oversample_p < 0) return fail(HSS_ERR_ARG, "oversample_p must be >= 0");
+  if (o->op && (!o->op->apply || o->precision != HSS_PREC_FP64))
+    return fail(HSS_ERR_ARG, "a user operator needs an apply function and HSS_PREC_FP64");
+  if (A->kind == HSS_SRC_EXTRACT && !o->op)
+    return fail(HSS_ERR_ARG, "an extraction source is sampled through a user operator (opts->op)");
+  if (o->criterion != HSS_CRIT_NEW && o->criterion != HSS_CRIT_HMT)
+    return fail(HSS_ERR_ARG, "unknown criterion %d", o->criterion);
+  if (o->criterion == HSS_CRIT_HMT) {
+    if (o->strategy != HSS_INCREMENTING)
+      return fail(HSS_ERR_ARG, "the HMT criterion is a test of the Incrementing strategy");
+    if (!(o->hmt_alpha > 1.0) || !std::isfinite(o->hmt_alpha))
+      return fail(HSS_ERR_ARG, "hmt_alpha must be finite and > 1 (got %g)", o->hmt_alpha);
+  }
   return HSS_OK;
 }
 
@@ -1486,50 +1786,20 @@ const char* hss_last_error(void) { return g_err.c_str(); }
 hss_status hss_compress(const hss_source* A, const hss_opts* o, void* stream, hss_matrix* out) {
   if (!out) return fail(HSS_ERR_ARG, "out is NULL");
   *out = nullptr;
-  CKS(check_source(A));
-  if (!o) return fail(HSS_ERR_ARG, "opts is NULL");
-  if (o->leaf < 1) return fail(HSS_ERR_ARG, "leaf must be >= 1 (got %d)", o->leaf);
-  if (o->d0 < 1 || o->d_max < 1) return fail(HSS_ERR_ARG, "d0 and d_max must be >= 1");
-  if (o->strategy != HSS_DOUBLING && o->strategy != HSS_INCREMENTING)
-    return fail(HSS_ERR_ARG, "unknown strategy %d", o->strategy);
-  if (o->strategy == HSS_INCREMENTING && o->dd < 1) return fail(HSS_ERR_ARG, "dd must be >= 1");
-  if (o->precision < HSS_PREC_FP64 || o->precision > HSS_PREC_BF16X3)
-    return fail(HSS_ERR_ARG, "unknown precision %d", o->precision);
-  if (!(o->rtol >= 0.0) || !(o->atol >= 0.0)) return fail(HSS_ERR_ARG, "tolerances must be >= 0");
-  if (o->wait_limit_ns < 0) return fail(HSS_ERR_ARG, "wait_limit_ns must be >= 0");
-  if (o->oversample_p < 0) return fail(HSS_ERR_ARG, "oversample_p must be >= 0");
-  if (o->op && (!o->op->apply || o->precision != HSS_PREC_FP64))
-    return fail(HSS_ERR_ARG, "a user operator needs an apply function and HSS_PREC_FP64");
-  if (A->kind == HSS_SRC_EXTRACT && !o->op)
-    return fail(HSS_ERR_ARG, "an extraction source is sampled through a user operator (opts->op)");
-  if (o->criterion != HSS_CRIT_NEW && o->criterion != HSS_CRIT_HMT)
-    return fail(HSS_ERR_ARG, "unknown criterion %d", o->criterion);
-  if (o->criterion == HSS_CRIT_HMT) {
-    if (o->strategy != HSS_INCREMENTING)
-      return fail(HSS_ERR_ARG, "the HMT criterion is a test of the Incrementing strategy");
-    if (!(o->hmt_alpha > 1.0) || !std::isfinite(o->hmt_alpha))
-      return fail(HSS_ERR_ARG, "hmt_alpha must be finite and > 1 (got %g)", o->hmt_alpha);
-  }
+  CKS(check_opts(A, o));
   cudaStream_t st = (cudaStream_t)stream;
   hss_matrix_s* H = new (std::nothrow) hss_matrix_s();
   if (!H) return fail(HSS_ERR_NOMEM, "host allocation failed");
-  hss_status s = compress_impl(A, o, st, H);
-  H->timer.close_range();
+  hss_status s;
+  {
+    Ctx c(st);
+    std::vector<hss_matrix_s*> Hs{H};
+    s = compress_all(c, {A}, {o}, Hs);
+  }
   if (s != HSS_OK) {
     cudaStreamSynchronize(st);
     delete H;
     return s;
-  }
-  H->st.n = H->n;
-  H->st.n_nodes = (int)H->nodes.size();
-  H->st.levels = H->max_level + 1;
-  H->st.d_final = H->d_final;
-  H->st.n_adapt = H->n_adapt;
-  H->st.converged = H->converged;
-  H->st.launches = H->launches;
-  for (size_t i = 1; i < H->nodes.size(); ++i) {
-    H->st.max_rank_r = std::max(H->st.max_rank_r, H->nodes[i].r.k);
-    H->st.max_rank_c = std::max(H->st.max_rank_c, H->nodes[i].c.k);
   }
   *out = H;
   if (!H->converged)
@@ -1566,66 +1836,62 @@ hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int c
   if (count == 0) return HSS_OK;
   if (!A || !opts || !out) return fail(HSS_ERR_ARG, "NULL argument");
   for (int i = 0; i < count; ++i) out[i] = nullptr;
+  for (int i = 0; i < count; ++i) {
+    hss_status s = check_opts(&A[i], &opts[i]);
+    if (s != HSS_OK) return fail(s, "matrix %d: %s", i, g_err.c_str());
+  }
   cudaStream_t st = (cudaStream_t)stream;
-  cudaEvent_t ready;
-  CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-  CK(cudaEventRecord(ready, st));
-  // largest problems first, handed out to the workers one at a time
+  // Groups of matrices compressed in lockstep, each group's estimated device
+  // memory (samples, R, bases, packed tensor-core operand) within 60 % of
+  // the free memory; largest first.
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return A[a].n > A[b].n; });
-  const int T = std::min(count, 4);
-  std::atomic<int> next(0);
-  std::vector<hss_status> status(count, HSS_OK);
-  std::vector<std::string> msg(count);
-  std::vector<cudaEvent_t> done(T, nullptr);
-  std::vector<hss_status> wstat(T, HSS_OK);
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  auto worker = [&](int w) {
-    cudaSetDevice(dev);
-    cudaStream_t ws;
-    if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamWaitEvent(ws, ready, 0) != cudaSuccess) {
-      wstat[w] = HSS_ERR_CUDA;
-      return;
-    }
-    for (int q = next++; q < count; q = next++) {
-      const int i = order[q];
-      status[i] = hss_compress(&A[i], &opts[i], ws, &out[i]);
-      if (status[i] != HSS_OK) msg[i] = g_err;
-    }
-    if (cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventRecord(done[w], ws) != cudaSuccess)
-      wstat[w] = HSS_ERR_CUDA;
-    cudaStreamDestroy(ws);
+  auto footprint = [&](int i) {
+    const double n = A[i].n, dm = std::min(opts[i].d_max, A[i].n);
+    double b = 8.0 * n * dm * (opts[i].symmetric ? 3.0 : 4.0);      // R, S^r, S^c, node samples
+    if (opts[i].strategy == HSS_INCREMENTING) b += 8.0 * n * dm * 2.0;   // bases Q
+    if (opts[i].precision != HSS_PREC_FP64 && A[i].kind == HSS_SRC_DENSE)
+      b += (double)packed_a_bytes(A[i].n, opts[i].precision);
+    return b;
   };
-  std::vector<std::thread> th;
-  for (int w = 0; w < T; ++w) th.emplace_back(worker, w);
-  for (auto& t : th) t.join();
-  for (int w = 0; w < T; ++w)
-    if (done[w]) {
-      cudaStreamWaitEvent(st, done[w], 0);
-      cudaEventDestroy(done[w]);
-    }
-  cudaEventDestroy(ready);
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  const double budget = 0.6 * (double)fr;
   hss_status first = HSS_OK;
   int at = -1;
-  for (int w = 0; w < T; ++w)
-    if (wstat[w] != HSS_OK) { first = wstat[w]; break; }
-  for (int i = 0; i < count && first == HSS_OK; ++i)
-    if (status[i] != HSS_OK && status[i] != HSS_ERR_NOT_CONVERGED) { first = status[i]; at = i; }
+  for (size_t g0 = 0; g0 < order.size() && first == HSS_OK;) {
+    size_t g1 = g0;
+    double used = 0.0;
+    while (g1 < order.size() && (g1 == g0 || used + footprint(order[g1]) <= budget)) used += footprint(order[g1++]);
+    std::vector<hss_matrix_s*> Hs;
+    std::vector<const hss_source*> As;
+    std::vector<const hss_opts*> Os;
+    for (size_t q = g0; q < g1; ++q) {
+      hss_matrix_s* H = new (std::nothrow) hss_matrix_s();
+      if (!H) { first = fail(HSS_ERR_NOMEM, "host allocation failed"); break; }
+      out[order[q]] = H;
+      Hs.push_back(H);
+      As.push_back(&A[order[q]]);
+      Os.push_back(&opts[order[q]]);
+    }
+    if (first != HSS_OK) break;
+    Ctx c(st);
+    first = compress_all(c, As, Os, Hs);
+    if (first != HSS_OK) at = order[g0];
+    g0 = g1;
+  }
   if (first != HSS_OK) {
+    const std::string msg = g_err;
+    cudaStreamSynchronize(st);
     for (int i = 0; i < count; ++i) {
       hss_free(out[i]);
       out[i] = nullptr;
     }
-    if (at >= 0) return fail(first, "matrix %d: %s", at, msg[at].c_str());
-    return fail(first, "worker stream setup failed");
+    return fail(first, "batch group starting at matrix %d: %s", at, msg.c_str());
   }
   for (int i = 0; i < count; ++i)
-    if (status[i] == HSS_ERR_NOT_CONVERGED)
-      return fail(HSS_ERR_NOT_CONVERGED, "matrix %d: %s", i, msg[i].c_str());
+    if (!out[i]->converged) return fail(HSS_ERR_NOT_CONVERGED, "matrix %d: root not compressed at d_max", i);
   return HSS_OK;
 }
 
@@ -1904,6 +2170,7 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
   if (transpose != 0 && transpose != 1) return fail(HSS_ERR_ARG, "transpose must be 0 or 1");
   if (nrhs == 0) return HSS_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  Ctx c(st);
   const bool tr = transpose != 0;
   const int nn = (int)H->nodes.size();
   // H^T has the roles of U and V exchanged, D^T at the leaves and
@@ -1940,7 +2207,7 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
       j.C = xh(id); j.c_rs = R_; j.c_cs = 1;
       jobs.push_back(j);
     }
-    hss_status e = run_gemms(H, jobs, st);
+    hss_status e = run_gemms(c, jobs);
     if (e != HSS_OK) { cudaFreeAsync(buf, st); return e; }
   }
   // down-sweep; nodes that are not COMPRESSED (a partial result) couple
@@ -2020,8 +2287,8 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
       g2.C = yh(b); g2.c_rs = R_; g2.c_cs = 1;
       p1.push_back(g2);
     }
-    hss_status e = run_gemms(H, p0, st);
-    if (e == HSS_OK) e = run_gemms(H, p1, st);
+    hss_status e = run_gemms(c, p0);
+    if (e == HSS_OK) e = run_gemms(c, p1);
     if (e != HSS_OK) { cudaFreeAsync(buf, st); return e; }
   }
   // leaves: Y(I) = D X(I) + U y^  (D^T and V y^ transposed)
@@ -2052,11 +2319,11 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
       l1.push_back(e2);
     }
   }
-  hss_status e = run_gemms(H, l0, st);
-  if (e == HSS_OK) e = run_gemms(H, l1, st);
+  hss_status e = run_gemms(c, l0);
+  if (e == HSS_OK) e = run_gemms(c, l1);
   // dense couplings of a partial result, one launch per level (the blocks
   // of one level write disjoint rows of Y)
-  for (int lev = 0; lev <= H->max_level && e == HSS_OK; ++lev) e = run_gemms(H, dense[lev], st);
+  for (int lev = 0; lev <= H->max_level && e == HSS_OK; ++lev) e = run_gemms(c, dense[lev]);
   cudaFreeAsync(buf, st);
   return e;
 }
@@ -2113,11 +2380,12 @@ hss_status hss_get_entries(hss_matrix H, int nr, const int* I, int nc, const int
     }
   }
   hss_status s = HSS_OK;
+  Ctx c(st);
   auto run = [&]() -> hss_status {
     CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     CK(cudaMemsetAsync(inv, 0xff, sizeof(int) * std::max<size_t>(ninv, 1), st));   // -1: no position
-    CKS(upload(H, dn, hn.data(), sizeof(EntryNode) * nn, st));
-    CKS(upload(H, dleaf, leaf_of.data(), sizeof(int) * n, st));
+    CKS(upload(c, dn, hn.data(), sizeof(EntryNode) * nn));
+    CKS(upload(c, dleaf, leaf_of.data(), sizeof(int) * n));
     CK(launch_inv_piv(dn, nn, err, st));
     for (int c0 = 0; c0 < nc; c0 += chunk) {
       const int w = std::min(chunk, nc - c0);

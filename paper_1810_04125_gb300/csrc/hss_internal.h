@@ -133,11 +133,23 @@ struct IncJob {
 };
 
 // Gather of sub-blocks of A: out(i, j) = A(I[i], J[j]) (col-major, ld ldo);
-// I or J may be NULL meaning i0 + i / j0 + j.
+// I or J may be NULL meaning i0 + i / j0 + j.  src: the source of the
+// entries (one launch serves the blocks of several matrices).
 struct ExtractJob {
   const int* I; int i0, mi;
   const int* J; int j0, nj;
   double* out; long long ldo;
+  SrcDev src;
+};
+
+// dst[t] = (idx[t] < split ? src[idx[t]] : src2[idx[t] - split]) for t < cnt:
+// the skeleton index composition tau.I = [nu1.I nu2.I](tau.J) of Algorithm 2
+struct GatherJob {
+  const int* src;
+  const int* src2;
+  const int* idx;
+  int* dst;
+  int cnt, split;
 };
 
 // One node of a compressed handle as the entry kernels read it
@@ -186,8 +198,7 @@ cudaError_t launch_sample_tc_packed(const void* A, const void* Rp, int n, int nc
 // bits, TF32; mode 2: 8 bits, BF16)
 cudaError_t launch_round_copy(const double* in, long long ldin, double* out, long long ldout, int n,
                               int ncols, int mode, cudaStream_t st);
-cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int njobs,
-                           int max_tiles, cudaStream_t st);
+cudaError_t launch_extract(const ExtractJob* jobs_dev, int njobs, int max_tiles, cudaStream_t st);
 cudaError_t launch_gemm(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles,
                         cudaStream_t st);
 // The same contract with the product on tcgen05 tensor cores, operands split
@@ -228,8 +239,7 @@ cudaError_t launch_inc_group(const IncJob* jobs_dev, const int2* map_dev, int nc
 cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int c1,
                              int* flag, cudaStream_t st);
 cudaError_t launch_identity_block(double* X, int n, int c0, int w, cudaStream_t st);
-cudaError_t launch_gather_int(const int* src, const int* idx, int* dst, int cnt,
-                              const int* src2, int split, cudaStream_t st);
+cudaError_t launch_gather_int(const GatherJob* jobs_dev, int njobs, int max_cnt, cudaStream_t st);
 // entries of a compressed handle (k_entries.cu); err: 1 = index out of
 // range, 2 = pivot out of range
 cudaError_t launch_inv_piv(const EntryNode* nodes, int nn, int* err, cudaStream_t st);

@@ -10,8 +10,9 @@ namespace {
 
 // grid: (tile, job); each CTA fills 32 x 32 tiles of its job, striding
 // over the job's tiles.
-__global__ void k_extract(SrcDev src, const ExtractJob* __restrict__ jobs) {
+__global__ void k_extract(const ExtractJob* __restrict__ jobs) {
   const ExtractJob jb = jobs[blockIdx.y];
+  const SrcDev& src = jb.src;
   const int tiles_i = (jb.mi + 31) / 32, tiles_j = (jb.nj + 31) / 32;
   const int ntiles = tiles_i * tiles_j;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -82,12 +83,13 @@ __global__ void k_nonfinite(const double* __restrict__ S, long long lds, int n, 
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
-__global__ void k_gather_int(const int* __restrict__ src, const int* __restrict__ idx, int* dst,
-                             int cnt, const int* __restrict__ src2, int split) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  int r = idx[t];
-  dst[t] = (r < split) ? src[r] : src2[r - split];
+// grid: (chunk, job)
+__global__ void k_gather_int(const GatherJob* __restrict__ jobs) {
+  const GatherJob jb = jobs[blockIdx.y];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < jb.cnt; t += gridDim.x * blockDim.x) {
+    const int r = jb.idx[t];
+    jb.dst[t] = (r < jb.split) ? jb.src[r] : jb.src2[r - jb.split];
+  }
 }
 
 // X(i, j) = (i == c0 + j): columns c0 .. c0 + w - 1 of the identity (n x w,
@@ -108,12 +110,15 @@ cudaError_t launch_identity_block(double* X, int n, int c0, int w, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_extract(const SrcDev& src, const ExtractJob* jobs_dev, int njobs, int max_tiles,
-                           cudaStream_t st) {
+// Every job's source must have its entries on the device (kinds DENSE ..
+// LAPLACE); the host checks that before it builds the list.
+cudaError_t launch_extract(const ExtractJob* jobs_dev, int njobs, int max_tiles, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  if (src.kind < HSS_SRC_DENSE || src.kind > HSS_SRC_LAPLACE) return cudaErrorInvalidValue;   // no entries on the device
   int gx = max_tiles < 1 ? 1 : (max_tiles > 64 ? 64 : max_tiles);
-  k_extract<<<dim3(gx, njobs), 256, 0, st>>>(src, jobs_dev);
+  for (int j0 = 0; j0 < njobs; j0 += 65535) {
+    const int nj = njobs - j0 < 65535 ? njobs - j0 : 65535;
+    k_extract<<<dim3(gx, nj), 256, 0, st>>>(jobs_dev + j0);
+  }
   return cudaGetLastError();
 }
 
@@ -133,10 +138,13 @@ cudaError_t launch_nonfinite(const double* S, long long lds, int n, int c0, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_int(const int* src, const int* idx, int* dst, int cnt, const int* src2,
-                              int split, cudaStream_t st) {
-  if (cnt <= 0) return cudaSuccess;
-  k_gather_int<<<(cnt + 127) / 128, 128, 0, st>>>(src, idx, dst, cnt, src2, split);
+cudaError_t launch_gather_int(const GatherJob* jobs_dev, int njobs, int max_cnt, cudaStream_t st) {
+  if (njobs <= 0 || max_cnt <= 0) return cudaSuccess;
+  const int gx = (max_cnt + 127) / 128 < 8 ? (max_cnt + 127) / 128 : 8;
+  for (int j0 = 0; j0 < njobs; j0 += 65535) {
+    const int nj = njobs - j0 < 65535 ? njobs - j0 : 65535;
+    k_gather_int<<<dim3(gx, nj), 128, 0, st>>>(jobs_dev + j0);
+  }
   return cudaGetLastError();
 }
 

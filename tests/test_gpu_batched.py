@@ -85,3 +85,29 @@ def test_batched_error_frees_everything(hss, torch):
     with pytest.raises(hss.HSSError) as e:
         hss.hss_compress_batched([good, bad, good], [o, o, o])
     assert "matrix 1" in str(e.value)
+
+
+def test_batched_levels_share_launches(hss, torch):
+    """Lockstep batching: every phase of a tree level is one launch over the
+    nodes of all matrices, so eight equal matrices take far fewer launches
+    than eight single calls (only the sampling launches are per matrix), with
+    the same ranks and an error within 1.1x the oracle's."""
+    src = w.toeplitz_power(1024, 1.5)
+    o = Options(leaf=64, rtol=1e-6, atol=1e-12, d0=16, dd=16, d_max=512)
+    R = w.gaussian_matrix(3, src.n, 0, o.d_max)
+    ref = compress(src, R, o)
+    s = gu.device_source(src)
+    Rd = gu.col_major(R)
+    opt = hss.make_opts(o.leaf, o.rtol, o.atol, o.d0, o.dd, o.d_max, gu.STRAT[o.strategy], R=Rd)
+    single = hss.hss_compress(s, opt)
+    Hs = hss.hss_compress_batched([s] * 8, [opt] * 8)
+    launches_batch = sum(H.stats().launches for H in Hs)
+    launches_single = single.stats().launches
+    assert launches_batch <= 0.5 * 8 * launches_single, (launches_batch, launches_single)
+    A = src.to_dense()
+    for H in Hs:
+        st = H.stats()
+        assert (st.d_final, st.n_adapt) == (ref.d_final, ref.n_adapt)
+        assert H.ranks() == single.ranks()
+        assert not gu.compare_with_oracle(H, ref, o, src.n)
+        assert gu.rel_err(A, gu.gpu_dense(H, src.n)) <= 1.1 * apply.rel_error(ref, A) + 1e-15
