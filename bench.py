@@ -59,17 +59,37 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
+def kernel_source_hash(kernel: str) -> str | None:
+    """sha1 of the source file that defines `kernel` (csrc/<kernel>.cu), so a
+    profile can tell which version of the kernel its counters came from."""
+    import hashlib
+    base = kernel.split("_gauss8")[0]
+    for name in (base, base.rsplit("_", 1)[0]):
+        p = os.path.join(ROOT, "paper_1810_04125_gb300", "csrc", f"{name}.cu")
+        if os.path.exists(p):
+            return hashlib.sha1(open(p, "rb").read()).hexdigest()
+    return None
+
+
 def traffic_from_profiles(kernel: str):
-    """Per-launch DRAM bytes of `kernel` on this workload, recorded from an
-    ncu capture in profiles/ (line 'traffic_bytes_per_launch: <int>')."""
+    """Per-launch DRAM bytes of `kernel` on this workload from an ncu capture
+    summarised in profiles/<kernel>.md ('traffic_bytes_per_launch: <int>'),
+    with the profile's name; None when there is none, or when the summary's
+    'kernel_source_sha1' does not match the kernel's current source (the
+    counters were taken on another version of the kernel)."""
     p = os.path.join(ROOT, "profiles", f"{kernel}.md")
     if not os.path.exists(p):
-        return None
+        return None, None
+    val, sha = None, None
     for line in open(p):
         if line.startswith("traffic_bytes_per_launch:"):
             v = line.split(":", 1)[1].strip()
-            return None if v in ("null", "") else float(v)
-    return None
+            val = None if v in ("null", "") else float(v)
+        elif line.startswith("kernel_source_sha1:"):
+            sha = line.split(":", 1)[1].strip()
+    if sha is None or sha != kernel_source_hash(kernel):
+        return None, f"profiles/{kernel}.md (stale: taken on another version of the kernel)"
+    return val, f"profiles/{kernel}.md"
 
 
 class Clocks:
@@ -272,17 +292,17 @@ def run_gpu(args):
         ach = s0.flop_sample / (s0.ms_sample / 1e3) / 1e12
         r_sample = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach / FP64_PEAK_TFLOPS, "kernel": "k_sample_fp64", "peak_source": fp64_src,
-                    "traffic": traffic_from_profiles("k_sample_fp64_gauss8_n16384")}
+                    **dict(zip(("traffic", "traffic_profile"), traffic_from_profiles("k_sample_fp64_gauss8_n16384")))}
     else:
         ach = s0.bytes_sample / (s0.ms_sample / 1e3) / 1e9
         r_sample = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / pk["hbm_gbs"], "kernel": "k_sample_tc",
                     "peak_source": f"{pk_kind} hbm_gbs (burst)",
-                    "traffic": traffic_from_profiles("k_sample_tc_gauss8_n16384")}
+                    **dict(zip(("traffic", "traffic_profile"), traffic_from_profiles("k_sample_tc_gauss8_n16384")))}
     ach_id = s0.flop_id / max(s0.ms_id / 1e3, 1e-12) / 1e12
     r_id = {"bound": "alu", "achieved": ach_id, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach_id / FP64_PEAK_TFLOPS, "kernel": "k_qrcp", "peak_source": fp64_src,
-            "traffic": traffic_from_profiles("k_qrcp_gauss8_n16384")}
+            **dict(zip(("traffic", "traffic_profile"), traffic_from_profiles("k_qrcp_gauss8_n16384")))}
     roof, roof_other = (r_id, r_sample) if s0.ms_id > s0.ms_sample else (r_sample, r_id)
 
     # --- the FP64 plain form on the same matrix, for the mixed / plain ratio
