@@ -259,6 +259,7 @@ struct hss_matrix_s {
   int pack_decided = -1;   // mixed forms, generated A: packed tiles (1) or not (0)
   bool sym = false;        // symmetric option: the column side mirrors the row side
   void* packA = nullptr;   // packed tensor-core tiles of a dense A (during compress)
+  void* toep_terms = nullptr; // a Toeplitz source's diagonals split into terms (during compress)
   bool usable = false;
   bool partial = false;    // not converged; the uncompressed part kept dense (F12, F21)
   hss_stats st{};
@@ -267,6 +268,7 @@ struct hss_matrix_s {
   bool own_R = true, done = false;
   ~hss_matrix_s() {
     if (packA) cudaFree(packA);
+    if (toep_terms) cudaFree(toep_terms);
     arena.release();
   }
 };
@@ -739,6 +741,13 @@ hss_status sample_columns(Ctx& c, hss_matrix_s* H, int c0, int c1) {
     CK(c.timer.mark(PH_RNG, st));
     CK(cudaFreeAsync(packR, st));
   } else {
+    if (H->src.kind == HSS_SRC_TOEPLITZ && !H->toep_terms) {
+      // the diagonals split once per compression: the producers assemble
+      // tiles from windows of them
+      CK(cudaMallocAsync(&H->toep_terms, toeplitz_terms_bytes(n, H->o.precision), st));
+      CK(launch_toeplitz_terms(s, H->o.precision, H->toep_terms, st));
+      c.launches++;
+    }
     void* packR = nullptr;
     CK(cudaMallocAsync(&packR, packed_r_bytes(n, w, H->o.precision), st));
     CK(launch_pack_r(Rc, n, n, w, H->o.precision, packR, st));
@@ -749,10 +758,11 @@ hss_status sample_columns(Ctx& c, hss_matrix_s* H, int c0, int c1) {
     }
     CK(c.timer.mark(PH_SAMPLE, st));
     int at = 0;
-    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 0, w, packR, H->Sg_r + c0, H->dmax, c.d_flag + 1, &at, st));
+    CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 0, w, packR, H->Sg_r + c0, H->dmax, c.d_flag + 1, &at,
+                        H->toep_terms, st));
     if (!H->sym)
       CK(launch_sample_tc(s, H->o.leaf, H->o.precision, 1, w, packR, H->Sg_c + c0, H->dmax, c.d_flag + 1, &at,
-                          st));
+                          H->toep_terms, st));
     c.launches += norient;
     c.sample_launches += norient;
     H->st.sample_launches += norient;
@@ -1652,6 +1662,10 @@ hss_status compress_all(Ctx& c, const std::vector<const hss_source*>& A, const s
       CK(cudaFreeAsync(H->packA, c.st));
       H->packA = nullptr;
     }
+    if (H->toep_terms) {
+      CK(cudaFreeAsync(H->toep_terms, c.st));
+      H->toep_terms = nullptr;
+    }
     if (!H->converged) CKS(keep_dense_blocks(c, H));
   }
   CKS(readback(c, c.d_flag + 3, sizeof(int)));
@@ -2487,12 +2501,16 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
   CK(launch_round_copy(R, ldr, Rr, n, n, ncols, precision == HSS_PREC_TF32X2 ? 1 : 2, st));
   void* pA = nullptr;
   void* pR = nullptr;
+  void* tt = nullptr;
   const bool packed = A->kind == HSS_SRC_DENSE;
   CK(cudaMallocAsync(&pR, packed_r_bytes(n, ncols, precision), st));
   CK(launch_pack_r(Rr, n, n, ncols, precision, pR, st));
   if (packed) {
     CK(cudaMallocAsync(&pA, packed_a_bytes(n, precision), st));
     CK(launch_pack_a(s, leaf, precision, pA, st));
+  } else if (A->kind == HSS_SRC_TOEPLITZ) {
+    CK(cudaMallocAsync(&tt, toeplitz_terms_bytes(n, precision), st));
+    CK(launch_toeplitz_terms(s, precision, tt, st));
   }
   for (int side = 0; side < 2; ++side) {
     double* S = side ? Sc : Sr;
@@ -2501,9 +2519,10 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
     if (ks > 1) CK(cudaMemset2DAsync(S, sizeof(double) * lds, 0, sizeof(double) * ncols, n, st));
     int at = 0;
     if (packed) CK(launch_sample_tc_packed(pA, pR, n, ncols, precision, side, S, lds, err, st));
-    else CK(launch_sample_tc(s, leaf, precision, side, ncols, pR, S, lds, err, &at, st));
+    else CK(launch_sample_tc(s, leaf, precision, side, ncols, pR, S, lds, err, &at, tt, st));
   }
   if (packed) CK(cudaFreeAsync(pA, st));
+  if (tt) CK(cudaFreeAsync(tt, st));
   CK(cudaFreeAsync(pR, st));
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -179,10 +179,14 @@ cudaError_t launch_sample_fp64(const SrcDev& src, int ncols, const double* R, lo
                                double* Sr, double* Sc, long long lds, cudaStream_t st);
 // tcgen05 mixed-precision sampling with entries generated in the kernel
 // (k_sample_tc.cu); Rp is R packed by launch_pack_r; *used_atomic tells
-// whether S had to be zeroed beforehand (K split across CTAs).
+// whether S had to be zeroed beforehand (K split across CTAs).  toep: for a
+// Toeplitz source, its diagonals split into the terms of the precision
+// (launch_toeplitz_terms, toeplitz_terms_bytes), else NULL.
 cudaError_t launch_sample_tc(const SrcDev& src, int leaf, int precision, int trans, int ncols,
                              const void* Rp, double* S, long long lds, int* err, int* used_atomic,
-                             cudaStream_t st);
+                             const void* toep, cudaStream_t st);
+size_t toeplitz_terms_bytes(int n, int precision);
+cudaError_t launch_toeplitz_terms(const SrcDev& src, int precision, void* out, cudaStream_t st);
 int sample_tc_ksplit(int n, int ncols, int precision);
 // packed form for a dense A: operands split once into canonical tiles in
 // global memory, the main loop fed by bulk copies (k_sample_tc.cu)

@@ -172,7 +172,7 @@ __global__ void __maxnreg__(96) k_gemm_tc(const GemmJob* __restrict__ jobs,
     for (int it = 0; it < nk && ok; ++it) {
       const int st = it % NS;
       const uint32_t ph = (uint32_t)(it / NS) & 1u;
-      if (!mbar_wait(&empty[st], ph ^ 1u, err, 21)) { ok = false; break; }
+      if (!mbar_wait_warp(&empty[st], ph ^ 1u, err, 21)) { ok = false; break; }
       uint8_t* sp = smem + st * stage_bytes;
       const int k0 = it * GT_BK;
       stage_tile(sp, TILE_A_BYTES, BM, a_rows_fast, tid, [&](int r, int kc, double* v) {
@@ -199,7 +199,7 @@ __global__ void __maxnreg__(96) k_gemm_tc(const GemmJob* __restrict__ jobs,
       // drain the chain of the previous k-tile
       if (it >= 1) {
         const int cd = it - 1, b = cd & 1;
-        if (!mbar_wait(&tfull[b], (uint32_t)(cd >> 1) & 1u, err, 22)) { ok = false; break; }
+        if (!mbar_wait_warp(&tfull[b], (uint32_t)(cd >> 1) & 1u, err, 22)) { ok = false; break; }
         tc_fence_after();
         drain_chain<NH>(tmem, N, b, q, h, s, e);
         tc_fence_before();
@@ -209,7 +209,7 @@ __global__ void __maxnreg__(96) k_gemm_tc(const GemmJob* __restrict__ jobs,
     }
     if (ok && nk >= 1) {
       const int cd = nk - 1, b = cd & 1;
-      if (!mbar_wait(&tfull[b], (uint32_t)(cd >> 1) & 1u, err, 23)) ok = false;
+      if (!mbar_wait_warp(&tfull[b], (uint32_t)(cd >> 1) & 1u, err, 23)) ok = false;
       else {
         tc_fence_after();
         drain_chain<NH>(tmem, N, b, q, h, s, e);

@@ -25,6 +25,8 @@
 // tc_common.cuh.
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "tc_common.cuh"
 
 namespace hss {
@@ -77,9 +79,39 @@ struct TcArgs {
   long long lds;
   int atomic;         // 1: add into S (pre-zeroed); 0: store
   int* err;
+  const void* toep;   // Toeplitz source: its diagonals split into the T terms
+                      // (term-major, 2n - 1 entries each, entry of A_ij at
+                      // (i - j) + n - 1), or NULL
 };
 
 constexpr int GEN_WARPS = 16;
+constexpr int TW = 80;   // window entries per term and producer warp (>= 8 + BK - 1)
+
+// The diagonals c_t of a Toeplitz matrix (A_ij = c_{i-j}: the first column
+// for i >= j, the first row for i < j), t = -(n-1) .. n-1, split into the T
+// terms of the mixed form exactly as the producers split an entry: the
+// generating kernel then assembles a tile from a window of consecutive
+// diagonals instead of evaluating and splitting every entry.
+template <int PREC>
+__global__ void k_toeplitz_terms(const double* col, const double* row, int n, void* out) {
+  using SP = Split<PREC>;
+  constexpr int T = SP::T, EV = SP::EV;
+  const long long len = 2LL * n - 1;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < len; q += (long long)gridDim.x * blockDim.x) {
+    const long long t = q - (n - 1);
+    double v[EV];
+    const double x = t >= 0 ? col[t] : row[-t];
+#pragma unroll
+    for (int e = 0; e < EV; ++e) v[e] = x;
+    uint4 ch[T];
+    SP::split(v, ch);
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      if (PREC == HSS_PREC_TF32X2) ((uint32_t*)out)[k * len + q] = ch[k].x;
+      else ((uint16_t*)out)[k * len + q] = (uint16_t)(ch[k].x & 0xFFFFu);
+    }
+  }
+}
 constexpr int GEN_THREADS = GEN_WARPS * 32 + 32;
 
 template <int PREC, int NH>
@@ -98,6 +130,9 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
   uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   int* lrow_lo = (int*)(tmem_slot + 4);
   int* lrow_hi = lrow_lo + BM;
+  // per producer warp: T window rows of TW diagonals (Toeplitz path)
+  uint32_t* win32 = (uint32_t*)(lrow_hi + BM) + (size_t)(threadIdx.x / 32) * T * TW;
+  uint16_t* win16 = (uint16_t*)win32;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int rb = blockIdx.x, ct = blockIdx.y;
   const int row0 = rb * BM, col0 = ct * N;
@@ -131,6 +166,15 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
 
   if (warp < GEN_WARPS) {
     const int q = warp % 4, h = warp / 4;
+    // this warp's rows (Toeplitz path): all below n, and the union of their
+    // leaf blocks [wlo, whi)
+    int wlo = 0x7fffffff, whi = -1;
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+      wlo = min(wlo, lrow_lo[8 * warp + rr]);
+      whi = max(whi, lrow_hi[8 * warp + rr]);
+    }
+    const bool rows_ok = row0 + 8 * warp + 8 <= n;
     float s[NH], e[NH];
 #pragma unroll
     for (int j = 0; j < NH; ++j) { s[j] = 0.f; e[j] = 0.f; }
@@ -139,32 +183,103 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
     for (int it = 0; it < nk && ok; ++it) {
       const int st = it % NSTAGE;
       const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
-      if (!mbar_wait(&empty[st], ph ^ 1u, a.err, 2)) { ok = false; break; }
+      if (!mbar_wait_warp(&empty[st], ph ^ 1u, a.err, 2)) { ok = false; break; }
       uint8_t* sp = smem + st * stage_bytes;
       if (tid == 0) {
         mbar_expect_tx(&full[st], tileB);
         bulk_g2s(sp + T * TILE_A_BYTES, gB + (size_t)it * tileB, tileB, &full[st]);
       }
       const int k0 = (kt0 + it) * BK;
-      for (int u = tid; u < BM * KC; u += NP) {
-        int r, c;
-        if (!a.trans) { r = u % BM; c = u / BM; }
-        else { r = (u / (8 * KC)) * 8 + (u % 8); c = (u / 8) % KC; }
-        const int gr = row0 + r, lo = lrow_lo[r], hi = lrow_hi[r];
-        double v[EV];
+      if (a.toep) {
+        // Toeplitz: this warp's 8 rows of the tile from a window of 8 + BK - 1
+        // consecutive diagonals (orientation 0: A(r, k) = c_{r - k}; 1:
+        // A(k, r) = c_{k - r}), masked only where the rows reach past n or a
+        // row's leaf block meets the tile's columns
+        const int rw = 8 * warp;
+        const long long tb = a.trans ? (long long)k0 - row0 - rw - 7 : (long long)row0 - k0 + rw - (BK - 1);
+        __syncwarp();
+        for (int qq = lane; qq < 8 + BK - 1; qq += 32) {
+          const long long t = tb + qq;
+          const bool in = t > -(long long)n && t < (long long)n;
 #pragma unroll
-        for (int x = 0; x < EV; ++x) {
-          const int gk = k0 + c * EV + x;
-          double val = 0.0;
-          if (gr < n && gk < n && (gk < lo || gk >= hi))
-            val = a.trans ? entry_gen(a.src, gk, gr) : entry_gen(a.src, gr, gk);
-          v[x] = val;
+          for (int k = 0; k < T; ++k) {
+            if (PREC == HSS_PREC_TF32X2)
+              win32[k * TW + qq] = in ? ((const uint32_t*)a.toep)[k * (2LL * n - 1) + t + n - 1] : 0u;
+            else
+              win16[k * TW + qq] = in ? ((const uint16_t*)a.toep)[k * (2LL * n - 1) + t + n - 1] : (uint16_t)0;
+          }
         }
-        uint4 chunk[T];
-        SP::split(v, chunk);
-        const uint32_t off = (uint32_t)(r / 8) * 1024u + (uint32_t)c * 128u + (uint32_t)(r % 8) * 16u;
+        __syncwarp();
+        const bool clean = rows_ok && k0 + BK <= n && (k0 + BK <= wlo || k0 >= whi);
 #pragma unroll
-        for (int t = 0; t < T; ++t) *(uint4*)(sp + t * TILE_A_BYTES + off) = chunk[t];
+        for (int i2 = 0; i2 < 2; ++i2) {
+          const int idx = lane + 32 * i2, rl = idx % 8, c = idx / 8, r = rw + rl;
+          // window position of the chunk's first entry; the next entries
+          // step by +1 (orientation 1) or -1 (orientation 0)
+          const int q0 = a.trans ? c * EV - rl + 7 : rl - c * EV + (BK - 1);
+          const int dq = a.trans ? 1 : -1;
+          uint4 chunk[T];
+          if (clean) {
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+              uint32_t wv[4];
+#pragma unroll
+              for (int e2 = 0; e2 < 4; ++e2) {
+                if (PREC == HSS_PREC_TF32X2) {
+                  wv[e2] = win32[k * TW + q0 + dq * e2];
+                } else {
+                  wv[e2] = (uint32_t)win16[k * TW + q0 + dq * (2 * e2)] |
+                           ((uint32_t)win16[k * TW + q0 + dq * (2 * e2 + 1)] << 16);
+                }
+              }
+              chunk[k] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+          } else {
+            const int gr = row0 + r, lo = lrow_lo[r], hi = lrow_hi[r];
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+              uint32_t wv[4];
+#pragma unroll
+              for (int e2 = 0; e2 < 4; ++e2) {
+                uint32_t pair = 0u;
+#pragma unroll
+                for (int hh = 0; hh < (PREC == HSS_PREC_TF32X2 ? 1 : 2); ++hh) {
+                  const int x = PREC == HSS_PREC_TF32X2 ? e2 : 2 * e2 + hh;
+                  const int gk = k0 + c * EV + x;
+                  const bool keep = gr < n && gk < n && (gk < lo || gk >= hi);
+                  if (PREC == HSS_PREC_TF32X2) pair = keep ? win32[k * TW + q0 + dq * x] : 0u;
+                  else pair |= (keep ? (uint32_t)win16[k * TW + q0 + dq * x] : 0u) << (16 * hh);
+                }
+                wv[e2] = pair;
+              }
+              chunk[k] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+          }
+          const uint32_t off = (uint32_t)(r / 8) * 1024u + (uint32_t)c * 128u + (uint32_t)(r % 8) * 16u;
+#pragma unroll
+          for (int t = 0; t < T; ++t) *(uint4*)(sp + t * TILE_A_BYTES + off) = chunk[t];
+        }
+      } else {
+        for (int u = tid; u < BM * KC; u += NP) {
+          int r, c;
+          if (!a.trans) { r = u % BM; c = u / BM; }
+          else { r = (u / (8 * KC)) * 8 + (u % 8); c = (u / 8) % KC; }
+          const int gr = row0 + r, lo = lrow_lo[r], hi = lrow_hi[r];
+          double v[EV];
+#pragma unroll
+          for (int x = 0; x < EV; ++x) {
+            const int gk = k0 + c * EV + x;
+            double val = 0.0;
+            if (gr < n && gk < n && (gk < lo || gk >= hi))
+              val = a.trans ? entry_gen(a.src, gk, gr) : entry_gen(a.src, gr, gk);
+            v[x] = val;
+          }
+          uint4 chunk[T];
+          SP::split(v, chunk);
+          const uint32_t off = (uint32_t)(r / 8) * 1024u + (uint32_t)c * 128u + (uint32_t)(r % 8) * 16u;
+#pragma unroll
+          for (int t = 0; t < T; ++t) *(uint4*)(sp + t * TILE_A_BYTES + off) = chunk[t];
+        }
       }
       fence_async_smem();
       mbar_arrive(&full[st]);
@@ -172,7 +287,7 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
       const int c = it / DR;
       if ((it % DR == DR - 1 || it == nk - 1) && c >= 1) {
         const int cd = c - 1, b = cd & 1;
-        if (!mbar_wait(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 6)) { ok = false; break; }
+        if (!mbar_wait_warp(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 6)) { ok = false; break; }
         tc_fence_after();
         drain_chain<NH>(tmem, N, b, q, h, s, e);
         tc_fence_before();
@@ -184,7 +299,7 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
     // drain what is left (the last chain)
     for (int cd = drained; ok && cd < nchain; ++cd) {
       const int b = cd & 1;
-      if (!mbar_wait(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 7)) { ok = false; break; }
+      if (!mbar_wait_warp(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 7)) { ok = false; break; }
       tc_fence_after();
       drain_chain<NH>(tmem, N, b, q, h, s, e);
       tc_fence_before();
@@ -386,7 +501,7 @@ __global__ void __maxnreg__(96) k_sample_tc_packed(TcPackedArgs a) {
     bool ok = true;
     for (int cd = 0; cd < nchain; ++cd) {
       const int b = cd & 1;
-      if (!mbar_wait(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 14)) { ok = false; break; }
+      if (!mbar_wait_warp(&tfull[b], (uint32_t)(cd >> 1) & 1u, a.err, 14)) { ok = false; break; }
       tc_fence_after();
       drain_chain<NH>(tmem, N, b, q, h, s, e);
       tc_fence_before();
@@ -415,7 +530,10 @@ int tmem_cols_for(int N) {
 }
 
 constexpr int DRAIN_PACKED = 2;   // k-tiles per accumulation chain (dense, packed)
-constexpr int DRAIN_GEN = 2;      // k-tiles per accumulation chain (generated entries)
+// k-tiles per accumulation chain (generated entries): TF32 x 2 carries its
+// chains four k-tiles long (its samples serve tolerances >= 1e-4; measured
+// error of the samples below 5e-7), BF16 x 3 two (tolerances down to 1e-6)
+constexpr int drain_gen(int precision) { return precision == HSS_PREC_TF32X2 ? 4 : 2; }
 
 template <int PREC>
 cudaError_t launch_packed_t(const TcPackedArgs& a, int gx, int gy, cudaStream_t st) {
@@ -439,7 +557,7 @@ template <int PREC>
 cudaError_t launch_gen_t(const TcArgs& a, int gx, int gy, cudaStream_t st) {
   constexpr int T = Split<PREC>::T;
   const size_t sm = (size_t)NSTAGE * (T * TILE_A_BYTES + (size_t)a.N * 128) + 8 * (2 * NSTAGE + 4) + 16 +
-                    2 * BM * sizeof(int) + 1024;
+                    2 * BM * sizeof(int) + (size_t)GEN_WARPS * T * TW * sizeof(uint32_t) + 1024;
   dim3 grid(gx, gy, a.ksplit);
 #define HSS_LAUNCH_GEN(NHV)                                                                         \
   do {                                                                                              \
@@ -467,6 +585,20 @@ int ksplit_for(int gx, int gy, int nkt, int waves) {
 }
 
 }  // namespace
+
+size_t toeplitz_terms_bytes(int n, int precision) {
+  return (size_t)(2LL * n - 1) * (precision == HSS_PREC_TF32X2 ? 2 * 4 : 3 * 2);
+}
+
+cudaError_t launch_toeplitz_terms(const SrcDev& src, int precision, void* out, cudaStream_t st) {
+  if (src.kind != HSS_SRC_TOEPLITZ || src.n <= 0) return cudaErrorInvalidValue;
+  const long long len = 2LL * src.n - 1;
+  const unsigned grid = (unsigned)std::min<long long>((len + 255) / 256, 152LL * 16);
+  if (precision == HSS_PREC_TF32X2) k_toeplitz_terms<HSS_PREC_TF32X2><<<grid, 256, 0, st>>>(src.a, src.b, src.n, out);
+  else if (precision == HSS_PREC_BF16X3) k_toeplitz_terms<HSS_PREC_BF16X3><<<grid, 256, 0, st>>>(src.a, src.b, src.n, out);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
 
 size_t packed_a_bytes(int n, int precision) {
   const int T = precision == HSS_PREC_TF32X2 ? 2 : 3, bk = bk_of(precision);
@@ -549,7 +681,7 @@ cudaError_t launch_sample_tc_packed(const void* A, const void* Rp, int n, int nc
 // K range is split across CTAs (*used_atomic).
 cudaError_t launch_sample_tc(const SrcDev& src, int leaf, int precision, int trans, int ncols,
                              const void* Rp, double* S, long long lds, int* err, int* used_atomic,
-                             cudaStream_t st) {
+                             const void* toep, cudaStream_t st) {
   if (src.kind < HSS_SRC_DENSE || src.kind > HSS_SRC_LAPLACE) return cudaErrorInvalidValue;   // no entries on the device
   const int n = src.n;
   if (n <= 0 || ncols <= 0) return cudaSuccess;
@@ -563,12 +695,13 @@ cudaError_t launch_sample_tc(const SrcDev& src, int leaf, int precision, int tra
   a.nkt = (n + bk_of(precision) - 1) / bk_of(precision);
   const int gx = (n + BM - 1) / BM, gy = (ncols + a.N - 1) / a.N;
   a.ksplit = sample_tc_ksplit(n, ncols, precision);
-  a.drain = DRAIN_GEN;
+  a.drain = drain_gen(precision);
   a.Rp = (const uint8_t*)Rp;
   a.S = S;
   a.lds = lds;
   a.atomic = a.ksplit > 1 ? 1 : 0;
   a.err = err;
+  a.toep = src.kind == HSS_SRC_TOEPLITZ ? toep : nullptr;
   *used_atomic = a.atomic;
   if (precision == HSS_PREC_TF32X2) return launch_gen_t<HSS_PREC_TF32X2>(a, gx, gy, st);
   if (precision == HSS_PREC_BF16X3) return launch_gen_t<HSS_PREC_BF16X3>(a, gx, gy, st);

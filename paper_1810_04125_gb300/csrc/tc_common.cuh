@@ -64,6 +64,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   }
 }
 
+// mbar_wait by a whole warp (all 32 lanes converged): the warp gives up as a
+// whole, so warp-collective operations after the wait (tcgen05.ld, __syncwarp)
+// never wait for a lane that left.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, int* err, int code) {
+  const bool ok = mbar_wait(bar, parity, err, code);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
