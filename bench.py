@@ -502,8 +502,9 @@ def run_config(args):
             members.append((hss.dense_source(A.t()), n, A))    # symmetric: the buffer is A column-major
         leaf, rtol, atol, strat, d0, dd, prec = 128, 1e-5, 1e-8, "doubling", 64, 64, "tf32x2"
     else:
-        W = {"c1": wl.workload_toeplitz_1024, "c3": wl.workload_laplace_sphere,
-             "c5": wl.workload_toeplitz_cos, "c5op": wl.workload_toeplitz_cos}[c]()
+        mk = {"c1": wl.workload_toeplitz_1024, "c3": wl.workload_laplace_sphere,
+              "c5": wl.workload_toeplitz_cos, "c5op": wl.workload_toeplitz_cos}[c]
+        W = mk(n=args.n) if args.n and c != "c1" else mk()
         src = W.source
         if W.needs_rcb:
             src = src.permuted(hss.hss_rcb_order(src.points, W.leaf))
@@ -568,6 +569,43 @@ def run_config(args):
                 den += float((Ab ** 2).sum())
         return (num / den) ** 0.5
 
+    pk, pk_kind = peaks()
+    # tensor-pipe peak of the mixed form's dtype: the measured BF16 burst
+    # figure, times the nominal TF32 / BF16 ratio (1.1 / 2.25) for TF32
+    tc_peak = pk["bf16_tflops"] * (1.1 / 2.25 if prec == "tf32x2" else 1.0)
+    tc_src = f"{pk_kind} bf16_tflops (burst)" + (" x 1.1/2.25 (nominal TF32/BF16)" if prec == "tf32x2" else "")
+    terms = {"tf32x2": 2, "bf16x3": 3}.get(prec, 1)
+    if args.sampling_only:
+        # the sampling kernel alone: S^r, S^c = (A - D^(L)) R for one pass of
+        # d0 columns through hss_sample_offdiag (entries generated in the
+        # kernel for these sources)
+        ds, n = members[0][0], members[0][1]
+        Rd = torch.randn((d0, n), dtype=torch.float64, device=dev).t()
+        Sr = torch.empty((n, d0), dtype=torch.float64, device=dev)
+        Sc = torch.empty((n, d0), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            hss.hss_sample_offdiag(ds, leaf, PREC[prec], Rd, Sr, Sc, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = Clocks(dev.index or 0)
+        with clocks:
+            e0.record(stream)
+            for _ in range(args.steps):
+                hss.hss_sample_offdiag(ds, leaf, PREC[prec], Rd, Sr, Sc, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        useful = 4.0 * n * n * d0
+        ach = useful * terms / (ms / 1e3) / 1e12
+        out = {"metric": "sampling kernel alone: S^r, S^c of one pass (generated entries)", "value": useful / (ms / 1e3) / 1e12,
+               "unit": "TFLOP/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+               "config": {"workload": CONFIG_WORKLOADS[c], "n": n, "columns": d0, "precision": prec, "leaf": leaf},
+               "roofline": {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
+                            "kernel": "k_sample_tc_gen", "peak_source": tc_src,
+                            "note": f"tensor work = {terms} term products x 4 n^2 d0"},
+               "clocks": clocks.summary()}
+        print(json.dumps(out), flush=True)
+        return
     clocks = Clocks(dev.index or 0)
     with clocks:
         ms, st = timed(prec, args.steps, args.warmup)
@@ -584,6 +622,14 @@ def run_config(args):
                       "strategy": strat, "d0": d0, "dd": dd, "precision": prec, "members": len(members),
                       "sampling": "user FFT operator" if op is not None else "entries"},
            "compress_s": ms / 1e3, "rel_error": err,
+           # the sampling kernels over the sampling phase (CUDA events): the
+           # tensor-core products of the mixed forms against the tensor peak of
+           # their dtype, the FP64 kernel against the FP64 pipe
+           "roofline_sampling": ({"bound": "tensor", "kernel": "k_sample_tc_gen" if c in ("c3", "c5") else "k_sample_tc_packed",
+                                  "achieved": sum(s.flop_sample for s in st) * terms / (max(1e-9, sum(s.ms_sample for s in st if s.launches)) / 1e3) / 1e12,
+                                  "peak": tc_peak, "unit": "TFLOP/s", "peak_source": tc_src,
+                                  "note": f"tensor work = {terms} term products x the sampled flops"}
+                                 if prec != "fp64" else None),
            "result": {"d_final": max(s.d_final for s in st), "n_adapt": max(s.n_adapt for s in st),
                       "max_rank": max(max(s.max_rank_r, s.max_rank_c) for s in st),
                       "converged": min(s.converged for s in st)},
@@ -593,6 +639,8 @@ def run_config(args):
                          "test": sum(s.ms_test for s in st if s.launches),
                          "merge_reduce": sum(s.ms_merge for s in st if s.launches)},
            "clocks": clocks.summary()}
+    if out.get("roofline_sampling"):
+        out["roofline_sampling"]["frac"] = out["roofline_sampling"]["achieved"] / out["roofline_sampling"]["peak"]
     if c == "c4":
         t0 = time.perf_counter()
         for m in members:
@@ -849,6 +897,8 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=2048)
     ap.add_argument("--ref-n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sampling-only", action="store_true",
+                    help="with --config c3 / c5: time the generated-entry sampling kernel alone (one pass)")
     ap.add_argument("--n", type=int, default=0, help="diagnostic override of the matrix order")
     ap.add_argument("--tol", type=float, default=0.0, help="rtol = atol of --config table4 (default 1e-12)")
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5op", "table3", "table4"],

@@ -340,6 +340,9 @@ typedef struct hss_tuning {
                                  (default 4; at least 64 k-tiles per CTA)      */
   int sample_waves_generated; /* the same for the generated-entry kernel
                                  (default 2)                                   */
+  int qrcp_min_cols;          /* a node side's QRCP group takes extra CTAs
+                                 (beyond one per 256 columns) only while each
+                                 keeps at least this many columns (default 4) */
 } hss_tuning;
 hss_status hss_set_tuning(const hss_tuning* t);   /* NULL: back to the defaults;
                                                      HSS_ERR_ARG on values < 1  */

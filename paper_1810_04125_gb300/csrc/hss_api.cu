@@ -873,7 +873,7 @@ std::mutex& tuning_mutex() {
   return m;
 }
 hss_tuning& tuning_ref() {
-  static hss_tuning t{8, 4, 2};
+  static hss_tuning t{8, 4, 2, 4};
   return t;
 }
 
@@ -946,7 +946,7 @@ hss_status run_qrcp(Ctx& c, const std::vector<QrcpReq>& reqs, std::vector<double
       auto top = pq.top();
       pq.pop();
       const size_t i = top.second;
-      if (mj[i] / (P[i] + 1) < 4) continue;   // keep at least four columns per CTA
+      if (mj[i] / (P[i] + 1) < tuning_get().qrcp_min_cols) continue;   // keep enough columns per CTA
       P[i]++;
       used++;
       pq.push({wk[i] / P[i], i});
@@ -1912,8 +1912,9 @@ hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int c
 void hss_free(hss_matrix H) { delete H; }
 
 hss_status hss_set_tuning(const hss_tuning* t) {
-  const hss_tuning def{8, 4, 2};
-  if (t && (t->qrcp_wide_max_sides < 1 || t->sample_waves_packed < 1 || t->sample_waves_generated < 1))
+  const hss_tuning def{8, 4, 2, 4};
+  if (t && (t->qrcp_wide_max_sides < 1 || t->sample_waves_packed < 1 || t->sample_waves_generated < 1 ||
+            t->qrcp_min_cols < 1))
     return fail(HSS_ERR_ARG, "tuning values must be >= 1");
   std::lock_guard<std::mutex> lock(tuning_mutex());
   tuning_ref() = t ? *t : def;

@@ -79,6 +79,13 @@ def main():
     meas["qrcp_wide_max_sides_ms_id"] = cand
     hss.set_tuning(qrcp_wide_max_sides=best_q)
     cand = {}
+    for c in (4, 16, 32, 64, 128):
+        hss.set_tuning(qrcp_min_cols=c)
+        cand[c] = _phase_ms(hss, torch, src, opts, args.reps)[0]
+    best_mc = min(cand, key=cand.get)
+    meas["qrcp_min_cols_ms_id"] = cand
+    hss.set_tuning(qrcp_min_cols=best_mc)
+    cand = {}
     for c in (1, 2, 4, 8):
         hss.set_tuning(sample_waves_packed=c)
         cand[c] = _phase_ms(hss, torch, src, opts, args.reps)[1]
@@ -99,6 +106,7 @@ def main():
     best_g = min(cand, key=cand.get)
     meas["sample_waves_generated_ms_sample"] = cand
     out = {"qrcp_wide_max_sides": best_q, "sample_waves_packed": best_p, "sample_waves_generated": best_g,
+           "qrcp_min_cols": best_mc,
            "device": torch.cuda.get_device_name(), "measured_ms": meas}
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)
