@@ -343,9 +343,14 @@ typedef struct hss_tuning {
   int qrcp_min_cols;          /* a node side's QRCP group takes extra CTAs
                                  (beyond one per 256 columns) only while each
                                  keeps at least this many columns (default 4) */
+  int qrcp_sm_ctas;           /* CTAs per SM of the QRCP group launches: 1
+                                 (512 threads), 2 (256) or 4 (128); 0 = by
+                                 qrcp_wide_max_sides (default 0)              */
 } hss_tuning;
 hss_status hss_set_tuning(const hss_tuning* t);   /* NULL: back to the defaults;
-                                                     HSS_ERR_ARG on values < 1  */
+                                                     HSS_ERR_ARG on values < 1
+                                                     (qrcp_sm_ctas: not 0, 1, 2
+                                                     or 4)                    */
 hss_status hss_get_tuning(hss_tuning* t);
 
 /* Checkpoint of a compressed handle (no counterpart in the paper, which

@@ -321,7 +321,7 @@ struct Ctx {
   long long launches = 0, sample_launches = 0, bytes_h2d = 0, bytes_d2h = 0;
   bool trace = false;      // HSS_TRACE=1: one stderr line per launch of the batched phases
   cudaEvent_t trace_ev[2] = {nullptr, nullptr};
-  int qrcp_cap = -1, qrcp_cap_d = -1, qrcp_cap_w = -1;
+  int qrcp_cap = -1, qrcp_cap_d = -1, qrcp_cap_w = -1, qrcp_nsm = 0, qrcp_per = 0;
   explicit Ctx(cudaStream_t s) : st(s) {
     const char* tr = getenv("HSS_TRACE");
     trace = tr && tr[0] == '1';
@@ -898,10 +898,14 @@ hss_status run_qrcp(Ctx& c, const std::vector<QrcpReq>& reqs, std::vector<double
   // the smallest width for which the groups of a batch fit the co-resident
   // CTAs; one cooperative launch per batch (plain launch when every P is 1).
   // few node sides (the top levels): the wide shape, whose groups have half
-  // as many CTAs; otherwise the narrow one
-  const int wide = (int)nj <= tuning_get().qrcp_wide_max_sides ? 1 : 0;
+  // as many CTAs; otherwise the narrow one (or the number of CTAs per SM the
+  // tuning fixes).  Shapes: 0 = 128 threads, four CTAs per SM; 1 = 256, two;
+  // 2 = 512, one.
+  const hss_tuning tun = tuning_get();
+  int wide = (int)nj <= tun.qrcp_wide_max_sides ? 1 : 0;
+  if (tun.qrcp_sm_ctas) wide = tun.qrcp_sm_ctas == 4 ? 0 : (tun.qrcp_sm_ctas == 2 ? 1 : 2);
   if (c.qrcp_cap_d != dmx || c.qrcp_cap_w != wide) {
-    c.qrcp_cap = qrcp_group_capacity(dmx, wide);
+    c.qrcp_cap = qrcp_group_capacity(dmx, wide, &c.qrcp_nsm, &c.qrcp_per);
     c.qrcp_cap_d = dmx;
     c.qrcp_cap_w = wide;
   }
@@ -946,7 +950,7 @@ hss_status run_qrcp(Ctx& c, const std::vector<QrcpReq>& reqs, std::vector<double
       auto top = pq.top();
       pq.pop();
       const size_t i = top.second;
-      if (mj[i] / (P[i] + 1) < tuning_get().qrcp_min_cols) continue;   // keep enough columns per CTA
+      if (mj[i] / (P[i] + 1) < tun.qrcp_min_cols) continue;   // keep enough columns per CTA
       P[i]++;
       used++;
       pq.push({wk[i] / P[i], i});
@@ -965,11 +969,14 @@ hss_status run_qrcp(Ctx& c, const std::vector<QrcpReq>& reqs, std::vector<double
             Scratch::rnd(sizeof(double) * 8);
   }
   need += Scratch::rnd(sizeof(unsigned) * nj) + Scratch::rnd(sizeof(int) * 3 * nj);
+  need += Scratch::rnd(sizeof(unsigned) * QRCP_PLACE_WORDS * batches.size());
   CK(c.scratch.ensure(need, st));
   std::vector<QrcpJob> jobs;
   wbuf.clear();
   unsigned* bars = (unsigned*)c.scratch.take(sizeof(unsigned) * nj);
   int* outs = (int*)c.scratch.take(sizeof(int) * 3 * nj);
+  // per batch: the placement counters of its cooperative launch
+  unsigned* places = (unsigned*)c.scratch.take(sizeof(unsigned) * QRCP_PLACE_WORDS * batches.size());
   for (size_t i = 0; i < nj; ++i) {
     const QrcpReq& q = reqs[i];
     hss_matrix_s* H = q.H;
@@ -1005,6 +1012,7 @@ hss_status run_qrcp(Ctx& c, const std::vector<QrcpReq>& reqs, std::vector<double
   if (c.scratch.overflow) return fail(HSS_ERR_NOMEM, "QRCP scratch sized too small");
   CK(c.timer.mark(PH_ID, st));
   CK(cudaMemsetAsync(bars, 0, sizeof(unsigned) * nj, st));
+  CK(cudaMemsetAsync(places, 0, sizeof(unsigned) * QRCP_PLACE_WORDS * batches.size(), st));
   CK(cudaMemsetAsync(c.d_flag + 2, 0, sizeof(int), st));
   if (c.trace) CK(cudaEventRecord(c.trace_ev[0], st));
   // job list and every batch's (job, rank) map in one upload
@@ -1015,9 +1023,14 @@ hss_status run_qrcp(Ctx& c, const std::vector<QrcpReq>& reqs, std::vector<double
   for (size_t bi = 0; bi < batches.size(); ++bi) {
     const Batch& b = batches[bi];
     if (!b.group) continue;
+    // every co-resident slot, positions slot x nsm + SM index: the groups'
+    // ranks in order, so that the CTAs of a group run on different SMs and
+    // each SM hosts ranks of several groups; the rest idle
     std::vector<int2> map;
     for (size_t i = b.b0; i < b.b1; ++i)
       for (int r = 0; r < P[i]; ++r) map.push_back(make_int2((int)i, r));
+    if ((int)map.size() > cap) return fail(HSS_ERR_CUDA, "QRCP groups exceed the co-resident CTAs");
+    map.resize((size_t)cap, make_int2(-1, -1));
     omap[bi] = sg.put(map.data(), map.size() * sizeof(int2));
     nmap[bi] = (int)map.size();
   }
@@ -1035,10 +1048,12 @@ hss_status run_qrcp(Ctx& c, const std::vector<QrcpReq>& reqs, std::vector<double
   for (size_t bi = 0; bi < batches.size(); ++bi) {
     const Batch& b = batches[bi];
     if (b.group) {
-      CK(launch_qrcp(dj, (const int2*)(dev + omap[bi]), nmap[bi], dmx, wide, c.d_flag + 2, st));
+      const bool place = c.qrcp_nsm * c.qrcp_per == nmap[bi];
+      CK(launch_qrcp(dj, (const int2*)(dev + omap[bi]), nmap[bi], dmx, wide, c.d_flag + 2,
+                     place ? places + QRCP_PLACE_WORDS * bi : nullptr, c.qrcp_nsm, c.qrcp_per, st));
       ctas_total += nmap[bi];
     } else {
-      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), dmx, wide, c.d_flag + 2, st));
+      CK(launch_qrcp(dj + b.b0, nullptr, (int)(b.b1 - b.b0), dmx, wide, c.d_flag + 2, nullptr, 0, 0, st));
       ctas_total += (int)(b.b1 - b.b0);
     }
     c.launches++;
@@ -1912,10 +1927,12 @@ hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int c
 void hss_free(hss_matrix H) { delete H; }
 
 hss_status hss_set_tuning(const hss_tuning* t) {
-  const hss_tuning def{8, 4, 2, 4};
+  const hss_tuning def{8, 4, 2, 4, 0};
   if (t && (t->qrcp_wide_max_sides < 1 || t->sample_waves_packed < 1 || t->sample_waves_generated < 1 ||
             t->qrcp_min_cols < 1))
     return fail(HSS_ERR_ARG, "tuning values must be >= 1");
+  if (t && t->qrcp_sm_ctas != 0 && t->qrcp_sm_ctas != 1 && t->qrcp_sm_ctas != 2 && t->qrcp_sm_ctas != 4)
+    return fail(HSS_ERR_ARG, "qrcp_sm_ctas must be 0, 1, 2 or 4");
   std::lock_guard<std::mutex> lock(tuning_mutex());
   tuning_ref() = t ? *t : def;
   return HSS_OK;

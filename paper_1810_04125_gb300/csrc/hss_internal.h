@@ -211,17 +211,25 @@ cudaError_t launch_gemm(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int 
 int gemm_tc_tile_n(int max_n);
 cudaError_t launch_gemm_tc(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles, int tile_n,
                            int* err, cudaStream_t st);
-// map == nullptr: one CTA per job; otherwise map[cta] = (job, rank within
-// the job's group) and the launch is cooperative.  d_max: largest d.  A CTA
-// owns at most qrcp_cols_per_cta() columns (m / P); W is col-major with
-// ldw a multiple of 4; nrm holds m doubles.
+// map == nullptr: one CTA per job; otherwise the launch is cooperative and
+// map holds the (job, rank within the job's group) of every position, (-1,
+// -1) for an idle one.  With place == nullptr CTA b takes map[b]; with
+// place (QRCP_PLACE_WORDS zeroed words) the launch fills every co-resident
+// slot (nctas = nsm x per) and CTA takes map[slot x nsm + its SM's index], so
+// that the ranks of one group that sit at consecutive positions run on
+// different SMs (it falls back to map[b] when the SMs do not hold exactly
+// per CTAs each).  d_max: largest d.  A CTA owns at most qrcp_cols_per_cta()
+// columns (m / P); W is col-major with ldw a multiple of 4; nrm holds m
+// doubles.
 // The process-wide launch-shape parameters (hss_set_tuning).
 hss_tuning tuning_get();
-// wide: 256 threads and two CTAs per SM (else 128 threads, four per SM).
+// wide: 2 = 512 threads and one CTA per SM, 1 = 256 threads and two, 0 = 128
+// threads and four.
+constexpr int QRCP_PLACE_WORDS = 1024 + 32 + 4;
 int qrcp_cols_per_cta();
-int qrcp_group_capacity(int d_max, int wide);
+int qrcp_group_capacity(int d_max, int wide, int* nsm = nullptr, int* per = nullptr);
 cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int d_max, int wide, int* err,
-                        cudaStream_t st);
+                        unsigned* place, int nsm, int per, cudaStream_t st);
 // With a user sampling operator: S(i, c0 + q) = T(i, q) - sum_{j in leaf(i)}
 // A(i, j) R(j, q) (trans = 0) or A(j, i) (trans = 1) for i < n, q < w: the
 // leaf diagonal blocks removed from the user's product T (col-major, ld ldt)

@@ -33,6 +33,15 @@
 // live column (a quad of 4 rows each, 16-byte loads) and the warps split
 // the rows; the partial dot products meet in shared memory.
 //
+// Placement.  The CTAs of a group run their pivot steps in lockstep, so two
+// of them on one SM are idle in the serial part of a step at the same time
+// and the SM's FP64 pipe with them; the block scheduler is free to put
+// consecutive blocks on one SM.  A cooperative launch therefore fills every
+// co-resident slot and each CTA takes its (job, rank) by the SM it runs on:
+// position slot x nsm + (index of its SM), where the host lays the ranks of
+// a group out at consecutive positions, i.e. on different SMs, and every SM
+// hosts CTAs of several groups whose serial parts need not coincide.
+//
 // Pivot = largest down-dated squared column norm (lowest index on ties),
 // recomputed from the column when cancellation has left less than
 // sqrt(eps) of its last exact value; the stop test uses the exact norm of
@@ -45,11 +54,12 @@
 namespace hss {
 namespace {
 
-// Two launch shapes: 256 threads and two CTAs per SM for levels with few
-// node sides, 128 threads and four CTAs per SM otherwise (more co-resident
-// groups, so that one group's serial phases overlap others' passes).  The
-// registers are budgeted for 512 threads per SM either way.
-constexpr int NT_WIDE = 256, NT_NARROW = 128;
+// Three launch shapes: 128 threads and four CTAs per SM (more co-resident
+// groups, so that one group's serial phases overlap others' passes), 256
+// threads and two, 512 threads and one (no other group's CTA competing for
+// the SM's FP64 pipe).  The registers are budgeted for 512 threads per SM
+// in every shape.
+constexpr int NT_XWIDE = 512, NT_WIDE = 256, NT_NARROW = 128;
 constexpr int NLMAX = 256;   // own columns per CTA (host sizes the groups)
 constexpr int PCU = 8;       // loads in flight per thread when the pivot column is read
 constexpr int EB = 16;       // rows per block of the back substitution X = R1^{-1} R2
@@ -169,12 +179,74 @@ __device__ __forceinline__ Carve carve(double* base, int dmax) {
   return c;
 }
 
+// The position of this CTA in a launch that fills every co-resident slot:
+// slot x nsm + the index of its SM among the SMs present, when every SM
+// present holds exactly per CTAs of the launch (else blockIdx.x).  place:
+// per-SM counters [0, 1024), the bitmap of SMs present [1024, 1056), the
+// launch barrier and a flag for an SM id out of range.  Called by every
+// thread; false when the launch barrier gave up.
+__device__ bool placed_position(unsigned* place, int nsm, int per, int* err, unsigned long long wait_ns, int* pos_out) {
+  __shared__ unsigned s_smid, s_slot;
+  __shared__ int s_pos, s_ok0;
+  unsigned* cnt = place;
+  unsigned* bits = place + 1024;
+  unsigned* bar = place + 1056;
+  unsigned* bad = place + 1057;
+  if (threadIdx.x == 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    s_smid = smid;
+    if (smid < 1024u) {
+      s_slot = atomicAdd(cnt + smid, 1u);
+      atomicOr(bits + (smid >> 5), 1u << (smid & 31u));
+    } else {
+      s_slot = 0u;
+      atomicOr(bad, 1u);
+    }
+  }
+  unsigned ep = 0;
+  if (!group_barrier(bar, (int)gridDim.x, ep, err, &s_ok0, wait_ns)) return false;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const unsigned w = __ldcg(bits + lane);
+    const unsigned me = s_smid;
+    // SMs present, those below this one, and whether each holds per CTAs
+    int total = __popc(w), below = 0, even = 1;
+    if (me < 1024u) {
+      const unsigned mw = me >> 5;
+      if ((unsigned)lane < mw) below = __popc(w);
+      else if ((unsigned)lane == mw) below = __popc(w & ((1u << (me & 31u)) - 1u));
+    }
+    for (unsigned r = w; r; r &= r - 1) {
+      const int b = __ffs(r) - 1;
+      if (__ldcg(cnt + 32 * lane + b) != (unsigned)per) even = 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      total += __shfl_xor_sync(0xffffffffu, total, o);
+      below += __shfl_xor_sync(0xffffffffu, below, o);
+    }
+    even = __all_sync(0xffffffffu, even);
+    if (lane == 0) {
+      const bool ok = even && total == nsm && __ldcg(bad) == 0u && s_slot < (unsigned)per;
+      s_pos = ok ? (int)s_slot * nsm + below : (int)blockIdx.x;
+    }
+  }
+  __syncthreads();
+  *pos_out = s_pos;
+  return true;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k_qrcp(const QrcpJob* __restrict__ jobs,
-                                                   const int2* __restrict__ map, int* err, int dmax) {
+                                                   const int2* __restrict__ map, int* err, int dmax,
+                                                   unsigned* place, int nsm, int per) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) double smem_d[];
-  const int2 me = map ? map[blockIdx.x] : make_int2(blockIdx.x, 0);
+  int pos = (int)blockIdx.x;
+  if (map && place && !placed_position(place, nsm, per, err, jobs[0].wait_ns, &pos)) return;
+  const int2 me = map ? map[pos] : make_int2(blockIdx.x, 0);
+  if (me.x < 0) return;   // an idle slot
   const QrcpJob jb = jobs[me.x];
   const int rank = me.y, P = map ? jb.P : 1;
   const int m = jb.m, d = jb.d, tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -644,7 +716,7 @@ size_t smem_for(int dmax, int nt) {
 }
 
 template <int NT>
-int group_capacity(int dmax) {
+int group_capacity(int dmax, int* nsm_out, int* per_out) {
   int dev = 0, sms = 0, per = 0;
   const size_t sm = smem_for(dmax, NT);
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -652,19 +724,24 @@ int group_capacity(int dmax) {
   if (cudaFuncSetAttribute(k_qrcp<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_qrcp<NT>, NT, sm) != cudaSuccess) return 0;
+  if (nsm_out) *nsm_out = sms;
+  if (per_out) *per_out = per;
   return sms * per;
 }
 
 template <int NT>
-cudaError_t launch(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int dmax, int* err, cudaStream_t st) {
+cudaError_t launch(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int dmax, int* err, unsigned* place,
+                   int nsm, int per, cudaStream_t st) {
   const size_t sm = smem_for(dmax, NT);
   cudaError_t e = cudaFuncSetAttribute(k_qrcp<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   if (!map_dev) {
-    k_qrcp<NT><<<nctas, NT, sm, st>>>(jobs_dev, nullptr, err, dmax);
+    k_qrcp<NT><<<nctas, NT, sm, st>>>(jobs_dev, nullptr, err, dmax, nullptr, 0, 0);
     return cudaGetLastError();
   }
-  void* args[] = {(void*)&jobs_dev, (void*)&map_dev, (void*)&err, (void*)&dmax};
+  if (place && nctas != nsm * per) return cudaErrorInvalidValue;   // placement needs every slot filled
+  void* args[] = {(void*)&jobs_dev, (void*)&map_dev, (void*)&err, (void*)&dmax, (void*)&place, (void*)&nsm,
+                  (void*)&per};
   return cudaLaunchCooperativeKernel((const void*)k_qrcp<NT>, dim3(nctas), dim3(NT), args, sm, st);
 }
 
@@ -672,19 +749,21 @@ cudaError_t launch(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int 
 
 int qrcp_cols_per_cta() { return NLMAX; }
 
-// Co-resident CTAs of k_qrcp on this device for sample width dmax, in the
-// wide (256 threads) or narrow (128 threads) shape.
-int qrcp_group_capacity(int dmax, int wide) {
-  return wide ? group_capacity<NT_WIDE>(dmax) : group_capacity<NT_NARROW>(dmax);
+// Co-resident CTAs of k_qrcp on this device for sample width dmax, in shape
+// 2 (512 threads), 1 (256) or 0 (128).
+int qrcp_group_capacity(int dmax, int wide, int* nsm, int* per) {
+  if (wide == 2) return group_capacity<NT_XWIDE>(dmax, nsm, per);
+  return wide ? group_capacity<NT_WIDE>(dmax, nsm, per) : group_capacity<NT_NARROW>(dmax, nsm, per);
 }
 
 // map == nullptr: one CTA per job (ordinary launch); otherwise map[cta] =
 // (job, rank) and the launch is cooperative.  dmax: largest d of the jobs.
 cudaError_t launch_qrcp(const QrcpJob* jobs_dev, const int2* map_dev, int nctas, int dmax, int wide, int* err,
-                        cudaStream_t st) {
+                        unsigned* place, int nsm, int per, cudaStream_t st) {
   if (nctas <= 0) return cudaSuccess;
-  return wide ? launch<NT_WIDE>(jobs_dev, map_dev, nctas, dmax, err, st)
-              : launch<NT_NARROW>(jobs_dev, map_dev, nctas, dmax, err, st);
+  if (wide == 2) return launch<NT_XWIDE>(jobs_dev, map_dev, nctas, dmax, err, place, nsm, per, st);
+  return wide ? launch<NT_WIDE>(jobs_dev, map_dev, nctas, dmax, err, place, nsm, per, st)
+              : launch<NT_NARROW>(jobs_dev, map_dev, nctas, dmax, err, place, nsm, per, st);
 }
 
 }  // namespace hss

@@ -76,7 +76,7 @@ class hss_stats(C.Structure):
 
 class hss_tuning(C.Structure):
     _fields_ = [("qrcp_wide_max_sides", C.c_int), ("sample_waves_packed", C.c_int),
-                ("sample_waves_generated", C.c_int), ("qrcp_min_cols", C.c_int)]
+                ("sample_waves_generated", C.c_int), ("qrcp_min_cols", C.c_int), ("qrcp_sm_ctas", C.c_int)]
 
 
 class hss_node_info(C.Structure):
@@ -137,7 +137,7 @@ def _apply_tuning_table():
     import json
     t = json.load(open(TUNING_PATH))
     set_tuning(**{k: int(t[k]) for k in ("qrcp_wide_max_sides", "sample_waves_packed",
-                                         "sample_waves_generated", "qrcp_min_cols") if k in t})
+                                         "sample_waves_generated", "qrcp_min_cols", "qrcp_sm_ctas") if k in t})
 
 
 def get_tuning() -> dict:

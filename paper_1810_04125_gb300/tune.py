@@ -11,8 +11,8 @@ same method (rounding aside).
 Workloads (synthetic, seeded):
   * dense Gaussian kernel exp(-|x - y|^2 / 2) + I on 16384 points uniform in
     [0, 1]^8 (seed 0), recursive-coordinate-bisection order, leaf 128,
-    TF32x2 sampling, Doubling from 128 at rtol 1e-4: the QRCP shape threshold
-    (ID phase time) and the K split of the packed sampling kernel (sampling
+    TF32x2 sampling, Doubling from 128 at rtol 1e-4: the QRCP shapes (CTAs
+    per SM, ID phase time) and the K split of the packed sampling kernel (sampling
     phase time);
   * Toeplitz cos(0.3 k) / (1 + k), n = 131072, generated entries, leaf 256,
     TF32x2 sampling, Incrementing from 256 by 128 at rtol 1e-4: the K split
@@ -79,6 +79,13 @@ def main():
     meas["qrcp_wide_max_sides_ms_id"] = cand
     hss.set_tuning(qrcp_wide_max_sides=best_q)
     cand = {}
+    for c in (0, 1, 2, 4):
+        hss.set_tuning(qrcp_sm_ctas=c)
+        cand[c] = _phase_ms(hss, torch, src, opts, args.reps)[0]
+    best_s = min(cand, key=cand.get)
+    meas["qrcp_sm_ctas_ms_id"] = cand
+    hss.set_tuning(qrcp_sm_ctas=best_s)
+    cand = {}
     for c in (4, 16, 32, 64, 128):
         hss.set_tuning(qrcp_min_cols=c)
         cand[c] = _phase_ms(hss, torch, src, opts, args.reps)[0]
@@ -106,7 +113,7 @@ def main():
     best_g = min(cand, key=cand.get)
     meas["sample_waves_generated_ms_sample"] = cand
     out = {"qrcp_wide_max_sides": best_q, "sample_waves_packed": best_p, "sample_waves_generated": best_g,
-           "qrcp_min_cols": best_mc,
+           "qrcp_min_cols": best_mc, "qrcp_sm_ctas": best_s,
            "device": torch.cuda.get_device_name(), "measured_ms": meas}
     with open(args.out, "w") as f:
         json.dump(out, f, indent=1)

@@ -93,11 +93,15 @@ def test_argument_validation_without_gpu(hss):
         os.unlink(tf.name)
     # launch-shape parameters: validated, settable, restorable
     saved = hss.get_tuning()
-    bad_t = hss.hss_tuning(0, 4, 2, 4)
+    bad_t = hss.hss_tuning(0, 4, 2, 4, 0)
+    assert L.hss_set_tuning(C.byref(bad_t)) == hss.HSS_ERR_ARG
+    bad_t = hss.hss_tuning(8, 4, 2, 4, 3)    # CTAs per SM: 0, 1, 2 or 4
     assert L.hss_set_tuning(C.byref(bad_t)) == hss.HSS_ERR_ARG
     hss.set_tuning()
     assert hss.get_tuning() == {"qrcp_wide_max_sides": 8, "sample_waves_packed": 4, "sample_waves_generated": 2,
-                                "qrcp_min_cols": 4}
+                                "qrcp_min_cols": 4, "qrcp_sm_ctas": 0}
+    hss.set_tuning(qrcp_sm_ctas=1)
+    assert hss.get_tuning()["qrcp_sm_ctas"] == 1
     hss.set_tuning(qrcp_wide_max_sides=16)
     assert hss.get_tuning()["qrcp_wide_max_sides"] == 16
     hss.set_tuning(**saved)
