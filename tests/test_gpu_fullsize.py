@@ -62,15 +62,19 @@ def test_benchmark_configuration_against_oracle(name, prec):
     assert st.converged == int(kv["converged"]) == 1
     assert (st.d_final, st.n_adapt) == (int(kv["d_final"]), int(kv["n_adapt"]))
     key = "near_mixed" if prec != "fp64" else "near"
-    bad = []
+    bad, diffs = [], []
     for i, (kr, kc) in H.ranks().items():
         ref = nodes[i]
         for k_g, k_o, band in ((kr, ref["kr"], ref[key][0]), (kc, ref["kc"], ref[key][1])):
+            diffs.append(abs(k_g - k_o))
             if abs(k_g - k_o) > band:
                 bad.append((i, k_g, k_o, band))
+    print(f"{name}: {len(diffs)} node sides, rank differences: max {max(diffs)}, "
+          f"sum {sum(diffs)}, nonzero {sum(1 for x in diffs if x)}")
     assert not bad, bad
     # the error on the whole matrix, from the expansion on the GPU
     D = torch.empty((n, n), dtype=torch.float64, device=gu.dev()).t()
     hss.hss_to_dense(H, D)
     err = float(torch.linalg.norm(D - Ad) / torch.linalg.norm(Ad))
+    print(f"{name}: error {err:.4e}, oracle {float(kv['rel_error']):.4e}")
     assert err <= 1.1 * float(kv["rel_error"]), (err, kv["rel_error"])
