@@ -877,6 +877,10 @@ hss_tuning& tuning_ref() {
   return t;
 }
 
+// Most CTAs of one side's group in the Incrementing test (every value of a
+// column step adds this many partial sums).
+constexpr int INC_GROUP_PMAX = 32;
+
 std::mutex& coop_launch_mutex() {
   static std::mutex m;
   return m;
@@ -1167,10 +1171,10 @@ hss_status incrementing_tests(Ctx& c, const std::vector<std::pair<hss_matrix_s*,
     for (auto& x : sides) {
       Side& s = x.side ? x.H->nodes[x.node].c : x.H->nodes[x.node].r;
       size_t b = block_end(x.H, s.tested) - s.tested, m = std::max(s.m, 1);
-      const size_t pg = (m + inc_group_rows((int)b) - 1) / inc_group_rows((int)b);   // group size bound
+      const int pg = (int)((m + inc_group_rows((int)b) - 1) / inc_group_rows((int)b));   // fewest CTAs of a group
       need += Scratch::rnd(8 * m * b) + Scratch::rnd(8 * std::max<size_t>(std::max(s.q, s.m), 1) * b) +
               Scratch::rnd(8 * b) + Scratch::rnd(8 * 4) + Scratch::rnd(8) + Scratch::rnd(sizeof(unsigned)) +
-              Scratch::rnd(8 * 2 * std::max<size_t>(pg, 1) * (b + 2));
+              Scratch::rnd(8 * inc_group_part(std::max(pg, INC_GROUP_PMAX), (int)b));
     }
     CK(c.scratch.ensure(need, st));
     std::vector<IncJob> ij;
@@ -1235,27 +1239,47 @@ hss_status incrementing_tests(Ctx& c, const std::vector<std::pair<hss_matrix_s*,
     // per batch of sides that fits the co-resident slots); blocks wider
     // than the group kernel takes go to one CTA per side
     // (only when one CTA per side would leave SMs idle and all groups fit
-    // one launch; a level with many sides keeps one CTA per side)
+    // two launches; a level with many sides keeps one CTA per side)
     int nsm = 0, cur = 0;
     CK(cudaGetDevice(&cur));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, cur));
     bool grouped = bmax <= inc_group_bmax() && (int)ij.size() < nsm;
     const int gcap = grouped ? inc_group_capacity(bmax) : 0;
     long long gsum = 0;
-    for (const IncJob& j : ij) {   // the groups at their row widths fit the resident slots
+    for (const IncJob& j : ij) {   // the groups at their row widths fit two launches
       const int rows = inc_group_rows(j.b);
-      gsum += (j.m + rows - 1) / rows;
+      const int pmin = (j.m + rows - 1) / rows;
+      if (pmin > gcap) grouped = false;
+      gsum += pmin;
     }
-    if (gsum > gcap) grouped = false;
+    if (gsum > 2LL * gcap) grouped = false;
     std::vector<int> P(ij.size(), 1);
     std::vector<std::pair<size_t, size_t>> gbatches;
     if (grouped) {
+      // the fewest CTAs whose rows fit shared memory, then the remaining
+      // resident slots to the sides with the most rows per CTA (at most
+      // INC_GROUP_PMAX CTAs and at least 8 rows each): a group's cost is its
+      // barriers and its rows per CTA
+      long long used = 0;
+      std::priority_queue<std::pair<double, size_t>> pq;
       for (size_t i = 0; i < ij.size(); ++i) {
         const int rows = inc_group_rows(ij[i].b);
         P[i] = std::max(1, (ij[i].m + rows - 1) / rows);
+        used += P[i];
+        pq.push({(double)ij[i].m / P[i], i});
+      }
+      while (gsum <= gcap && used < gcap && !pq.empty()) {   // one launch: fill its slots
+        const size_t i = pq.top().second;
+        pq.pop();
+        if (P[i] >= INC_GROUP_PMAX || ij[i].m / (P[i] + 1) < 8) continue;
+        P[i]++;
+        used++;
+        pq.push({(double)ij[i].m / P[i], i});
+      }
+      for (size_t i = 0; i < ij.size(); ++i) {
         ij[i].P = P[i];
         ij[i].bar = (unsigned*)c.scratch.take(sizeof(unsigned));
-        ij[i].part = (double*)c.scratch.take(sizeof(double) * 2 * (size_t)P[i] * (ij[i].b + 2));
+        ij[i].part = (double*)c.scratch.take(sizeof(double) * inc_group_part(std::max(P[i], INC_GROUP_PMAX), ij[i].b));
       }
       for (size_t b0 = 0; b0 < ij.size();) {
         size_t b1 = b0;

@@ -128,7 +128,7 @@ struct IncJob {
   // group form (launch_inc_group): P CTAs split the m rows
   int P;
   unsigned* bar;        // group barrier counter, zero before the launch
-  double* part;         // 2 x P x (b + 2) partial sums
+  double* part;         // inc_group_part(P, b) doubles of partial sums
   unsigned long long wait_ns;  // bound of one group-barrier wait (%globaltimer ns)
 };
 
@@ -243,7 +243,8 @@ cudaError_t launch_inc_qr(const IncJob* jobs_dev, int njobs, cudaStream_t st);
 // The same test with the rows of each side split over a group of P CTAs
 // (map[cta] = (job, rank), cooperative launch); b_max: largest block, at
 // most inc_group_bmax().
-int inc_group_rows(int b);                 // rows per CTA for a block of b columns
+int inc_group_rows(int b);                 // most rows per CTA for a block of b columns
+size_t inc_group_part(int P, int b);       // doubles of a side's partial-sum area (IncJob.part)
 int inc_group_bmax();
 int inc_group_capacity(int b_max);          // co-resident CTAs
 cudaError_t launch_inc_group(const IncJob* jobs_dev, const int2* map_dev, int nctas, int b_max, int* err,
