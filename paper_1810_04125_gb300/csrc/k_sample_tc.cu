@@ -80,18 +80,24 @@ struct TcArgs {
   int atomic;         // 1: add into S (pre-zeroed); 0: store
   int* err;
   const void* toep;   // Toeplitz source: its diagonals split into the T terms
-                      // (term-major, 2n - 1 entries each, entry of A_ij at
-                      // (i - j) + n - 1), or NULL
+                      // (entry of A_ij at (i - j) + n - 1: TF32 x 2 both terms
+                      // in one 8-byte word, BF16 x 3 term-major), or NULL
 };
 
 constexpr int GEN_WARPS = 16;
+// k-tiles per accumulation chain (generated entries): TF32 x 2 carries its
+// chains four k-tiles long (its samples serve tolerances >= 1e-4; measured
+// error of the samples below 5e-7), BF16 x 3 two (tolerances down to 1e-6)
+__host__ __device__ constexpr int drain_gen(int precision) { return precision == HSS_PREC_TF32X2 ? 4 : 2; }
 constexpr int TW = 80;   // window entries per term and producer warp (>= 8 + BK - 1)
 
 // The diagonals c_t of a Toeplitz matrix (A_ij = c_{i-j}: the first column
 // for i >= j, the first row for i < j), t = -(n-1) .. n-1, split into the T
 // terms of the mixed form exactly as the producers split an entry: the
 // generating kernel then assembles a tile from a window of consecutive
-// diagonals instead of evaluating and splitting every entry.
+// diagonals instead of evaluating and splitting every entry.  TF32 x 2: the
+// two terms of a diagonal side by side (one 8-byte word); BF16 x 3: term
+// after term (2n - 1 entries each).
 template <int PREC>
 __global__ void k_toeplitz_terms(const double* col, const double* row, int n, void* out) {
   using SP = Split<PREC>;
@@ -105,19 +111,21 @@ __global__ void k_toeplitz_terms(const double* col, const double* row, int n, vo
     for (int e = 0; e < EV; ++e) v[e] = x;
     uint4 ch[T];
     SP::split(v, ch);
+    if constexpr (PREC == HSS_PREC_TF32X2) {
+      ((uint2*)out)[q] = make_uint2(ch[0].x, ch[1].x);
+    } else {
 #pragma unroll
-    for (int k = 0; k < T; ++k) {
-      if (PREC == HSS_PREC_TF32X2) ((uint32_t*)out)[k * len + q] = ch[k].x;
-      else ((uint16_t*)out)[k * len + q] = (uint16_t)(ch[k].x & 0xFFFFu);
+      for (int k = 0; k < T; ++k) ((uint16_t*)out)[k * len + q] = (uint16_t)(ch[k].x & 0xFFFFu);
     }
   }
 }
 constexpr int GEN_THREADS = GEN_WARPS * 32 + 32;
 
-template <int PREC, int NH>
+template <int PREC, int NH, int TRANS>
 __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
   using SP = Split<PREC>;
   constexpr int T = SP::T, EV = SP::EV, BK = SP::BK, KC = BK / EV;
+  constexpr int DR = drain_gen(PREC);
   constexpr int NP = GEN_WARPS * 32;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int n = a.src.n, N = a.N;
@@ -138,7 +146,7 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
   const int row0 = rb * BM, col0 = ct * N;
   const int kt0 = (int)((long long)a.nkt * blockIdx.z / a.ksplit);
   const int kt1 = (int)((long long)a.nkt * (blockIdx.z + 1) / a.ksplit);
-  const int nk = kt1 - kt0, DR = a.drain;
+  const int nk = kt1 - kt0;
   const int nchain = (nk + DR - 1) / DR;
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) { mbar_init(&full[s], NP + 1); mbar_init(&empty[s], 1); }
@@ -180,9 +188,15 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
     for (int j = 0; j < NH; ++j) { s[j] = 0.f; e[j] = 0.f; }
     bool ok = true;
     int drained = 0;   // chains drained so far
+    // the Toeplitz diagonal terms: entry t of term k at tterm[k][t], |t| < n
+    const uint2* tterm64 = a.toep ? (const uint2*)a.toep + (n - 1) : nullptr;
+    const uint16_t* tterm16 = a.toep ? (const uint16_t*)a.toep + (n - 1) : nullptr;
+    uint2* win64 = (uint2*)win32;
+    const long long tlen = 2LL * n - 1;
+    int st = 0;
+    uint32_t ph = 0u;
     for (int it = 0; it < nk && ok; ++it) {
-      const int st = it % NSTAGE;
-      const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+      if (it > 0 && ++st == NSTAGE) { st = 0; ph ^= 1u; }
       if (!mbar_wait_warp(&empty[st], ph ^ 1u, a.err, 2)) { ok = false; break; }
       uint8_t* sp = smem + st * stage_bytes;
       if (tid == 0) {
@@ -196,17 +210,20 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
         // A(k, r) = c_{k - r}), masked only where the rows reach past n or a
         // row's leaf block meets the tile's columns
         const int rw = 8 * warp;
-        const long long tb = a.trans ? (long long)k0 - row0 - rw - 7 : (long long)row0 - k0 + rw - (BK - 1);
+        const int tb = TRANS ? k0 - row0 - rw - 7 : row0 - k0 + rw - (BK - 1);
         __syncwarp();
-        for (int qq = lane; qq < 8 + BK - 1; qq += 32) {
-          const long long t = tb + qq;
-          const bool in = t > -(long long)n && t < (long long)n;
 #pragma unroll
-          for (int k = 0; k < T; ++k) {
-            if (PREC == HSS_PREC_TF32X2)
-              win32[k * TW + qq] = in ? ((const uint32_t*)a.toep)[k * (2LL * n - 1) + t + n - 1] : 0u;
-            else
-              win16[k * TW + qq] = in ? ((const uint16_t*)a.toep)[k * (2LL * n - 1) + t + n - 1] : (uint16_t)0;
+        for (int qq0 = 0; qq0 < 8 + BK - 1; qq0 += 32) {
+          const int qq = qq0 + lane;
+          if (qq < 8 + BK - 1) {
+            const int t = tb + qq;
+            const bool in = t > -n && t < n;
+            if constexpr (PREC == HSS_PREC_TF32X2) {
+              win64[qq] = in ? tterm64[t] : make_uint2(0u, 0u);
+            } else {
+#pragma unroll
+              for (int k = 0; k < T; ++k) win16[k * TW + qq] = in ? tterm16[k * tlen + t] : (uint16_t)0;
+            }
           }
         }
         __syncwarp();
@@ -216,22 +233,34 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
           const int idx = lane + 32 * i2, rl = idx % 8, c = idx / 8, r = rw + rl;
           // window position of the chunk's first entry; the next entries
           // step by +1 (orientation 1) or -1 (orientation 0)
-          const int q0 = a.trans ? c * EV - rl + 7 : rl - c * EV + (BK - 1);
-          const int dq = a.trans ? 1 : -1;
+          const int q0 = TRANS ? c * EV - rl + 7 : rl - c * EV + (BK - 1);
+          constexpr int dq = TRANS ? 1 : -1;
           uint4 chunk[T];
-          if (clean) {
+          if (PREC == HSS_PREC_TF32X2 && clean) {
+            uint2 w[4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) w[e2] = win64[q0 + dq * e2];
+            chunk[0] = make_uint4(w[0].x, w[1].x, w[2].x, w[3].x);
+            chunk[T - 1] = make_uint4(w[0].y, w[1].y, w[2].y, w[3].y);
+          } else if (PREC == HSS_PREC_TF32X2) {
+            const int gr = row0 + r, lo = lrow_lo[r], hi = lrow_hi[r];
+            uint2 w[4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+              const int gk = k0 + c * EV + e2;
+              const bool keep = gr < n && gk < n && (gk < lo || gk >= hi);
+              w[e2] = keep ? win64[q0 + dq * e2] : make_uint2(0u, 0u);
+            }
+            chunk[0] = make_uint4(w[0].x, w[1].x, w[2].x, w[3].x);
+            chunk[T - 1] = make_uint4(w[0].y, w[1].y, w[2].y, w[3].y);
+          } else if (clean) {
 #pragma unroll
             for (int k = 0; k < T; ++k) {
               uint32_t wv[4];
 #pragma unroll
-              for (int e2 = 0; e2 < 4; ++e2) {
-                if (PREC == HSS_PREC_TF32X2) {
-                  wv[e2] = win32[k * TW + q0 + dq * e2];
-                } else {
-                  wv[e2] = (uint32_t)win16[k * TW + q0 + dq * (2 * e2)] |
-                           ((uint32_t)win16[k * TW + q0 + dq * (2 * e2 + 1)] << 16);
-                }
-              }
+              for (int e2 = 0; e2 < 4; ++e2)
+                wv[e2] = (uint32_t)win16[k * TW + q0 + dq * (2 * e2)] |
+                         ((uint32_t)win16[k * TW + q0 + dq * (2 * e2 + 1)] << 16);
               chunk[k] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
             }
           } else {
@@ -243,12 +272,11 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
               for (int e2 = 0; e2 < 4; ++e2) {
                 uint32_t pair = 0u;
 #pragma unroll
-                for (int hh = 0; hh < (PREC == HSS_PREC_TF32X2 ? 1 : 2); ++hh) {
-                  const int x = PREC == HSS_PREC_TF32X2 ? e2 : 2 * e2 + hh;
+                for (int hh = 0; hh < 2; ++hh) {
+                  const int x = 2 * e2 + hh;
                   const int gk = k0 + c * EV + x;
                   const bool keep = gr < n && gk < n && (gk < lo || gk >= hi);
-                  if (PREC == HSS_PREC_TF32X2) pair = keep ? win32[k * TW + q0 + dq * x] : 0u;
-                  else pair |= (keep ? (uint32_t)win16[k * TW + q0 + dq * x] : 0u) << (16 * hh);
+                  pair |= (keep ? (uint32_t)win16[k * TW + q0 + dq * x] : 0u) << (16 * hh);
                 }
                 wv[e2] = pair;
               }
@@ -262,7 +290,7 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
       } else {
         for (int u = tid; u < BM * KC; u += NP) {
           int r, c;
-          if (!a.trans) { r = u % BM; c = u / BM; }
+          if (!TRANS) { r = u % BM; c = u / BM; }
           else { r = (u / (8 * KC)) * 8 + (u % 8); c = (u / 8) % KC; }
           const int gr = row0 + r, lo = lrow_lo[r], hi = lrow_hi[r];
           double v[EV];
@@ -271,7 +299,7 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
             const int gk = k0 + c * EV + x;
             double val = 0.0;
             if (gr < n && gk < n && (gk < lo || gk >= hi))
-              val = a.trans ? entry_gen(a.src, gk, gr) : entry_gen(a.src, gr, gk);
+              val = TRANS ? entry_gen(a.src, gk, gr) : entry_gen(a.src, gr, gk);
             v[x] = val;
           }
           uint4 chunk[T];
@@ -310,9 +338,10 @@ __global__ void __maxnreg__(96) k_sample_tc_gen(TcArgs a) {
   } else if (lane == 0) {
     // ------------------------------------------------------------- MMA issuer
     const uint32_t id = idesc(SP::FMT, (uint32_t)N);
+    int st = 0;
+    uint32_t ph = 0u;
     for (int it = 0; it < nk; ++it) {
-      const int st = it % NSTAGE;
-      const uint32_t ph = (uint32_t)(it / NSTAGE) & 1u;
+      if (it > 0 && ++st == NSTAGE) { st = 0; ph ^= 1u; }
       const int c = it / DR, b = c & 1;
       const bool first = (it % DR) == 0;
       if (first && !mbar_wait(&tempty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u, a.err, 8)) break;
@@ -530,10 +559,6 @@ int tmem_cols_for(int N) {
 }
 
 constexpr int DRAIN_PACKED = 2;   // k-tiles per accumulation chain (dense, packed)
-// k-tiles per accumulation chain (generated entries): TF32 x 2 carries its
-// chains four k-tiles long (its samples serve tolerances >= 1e-4; measured
-// error of the samples below 5e-7), BF16 x 3 two (tolerances down to 1e-6)
-constexpr int drain_gen(int precision) { return precision == HSS_PREC_TF32X2 ? 4 : 2; }
 
 template <int PREC>
 cudaError_t launch_packed_t(const TcPackedArgs& a, int gx, int gy, cudaStream_t st) {
@@ -559,15 +584,20 @@ cudaError_t launch_gen_t(const TcArgs& a, int gx, int gy, cudaStream_t st) {
   const size_t sm = (size_t)NSTAGE * (T * TILE_A_BYTES + (size_t)a.N * 128) + 8 * (2 * NSTAGE + 4) + 16 +
                     2 * BM * sizeof(int) + (size_t)GEN_WARPS * T * TW * sizeof(uint32_t) + 1024;
   dim3 grid(gx, gy, a.ksplit);
-#define HSS_LAUNCH_GEN(NHV)                                                                         \
+#define HSS_LAUNCH_GEN(NHV, TR)                                                                     \
   do {                                                                                              \
-    cudaError_t e = cudaFuncSetAttribute(k_sample_tc_gen<PREC, NHV>,                                \
+    cudaError_t e = cudaFuncSetAttribute(k_sample_tc_gen<PREC, NHV, TR>,                            \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);     \
     if (e != cudaSuccess) return e;                                                                 \
-    k_sample_tc_gen<PREC, NHV><<<grid, GEN_THREADS, sm, st>>>(a);                                   \
+    k_sample_tc_gen<PREC, NHV, TR><<<grid, GEN_THREADS, sm, st>>>(a);                               \
   } while (0)
-  if (a.N == 64) HSS_LAUNCH_GEN(16);
-  else HSS_LAUNCH_GEN(32);
+  if (a.N == 64) {
+    if (a.trans) HSS_LAUNCH_GEN(16, 1);
+    else HSS_LAUNCH_GEN(16, 0);
+  } else {
+    if (a.trans) HSS_LAUNCH_GEN(32, 1);
+    else HSS_LAUNCH_GEN(32, 0);
+  }
 #undef HSS_LAUNCH_GEN
   return cudaGetLastError();
 }
