@@ -1,11 +1,12 @@
 """The benchmark workloads at full size against the oracle's compression of
 the same matrices on the same R, stored by tests/golden/make_fullsize_golden.py
 (which runs the oracle alone): Gaussian kernel 8-D, n = 16384 dense,
-Doubling, TF32 x 2 sampling (the benchmark configuration), and the FP64
-form of it when its file is there.  Required: the same passes, every node's
-ranks equal except across singular values within the tie band (widened by
-the tested bound of the mixed sampling error for the TF32 x 2 form), and an
-error ||A - H||_F / ||A||_F within 1.1x the oracle's."""
+Doubling, TF32 x 2 sampling (the benchmark configuration) and its FP64 form,
+and the generated Toeplitz cos(0.3k)/(1+k), n = 131072, Incrementing, TF32 x 2.
+Required: the same passes, every node's ranks equal except across singular
+values within the tie band (widened by the tested bound of the mixed sampling
+error for the TF32 x 2 forms), and an error ||A - H||_F / ||A||_F within 1.1x
+the oracle's."""
 import os
 
 import numpy as np
@@ -77,4 +78,62 @@ def test_benchmark_configuration_against_oracle(name, prec):
     hss.hss_to_dense(H, D)
     err = float(torch.linalg.norm(D - Ad) / torch.linalg.norm(Ad))
     print(f"{name}: error {err:.4e}, oracle {float(kv['rel_error']):.4e}")
+    assert err <= 1.1 * float(kv["rel_error"]), (err, kv["rel_error"])
+
+
+def test_generated_toeplitz_against_oracle():
+    """The C5 workload at full size: Toeplitz cos(0.3k)/(1+k), n = 131072,
+    entries generated on the device, Incrementing from 256 by 128, TF32 x 2
+    sampling on the TF32-rounded R, against the oracle's compression stored in
+    tests/golden/fullsize_c5_tf32.txt: same passes, every node's ranks within
+    the tie band widened by the mixed sampling noise, error within 1.1x."""
+    g = read_golden("c5_tf32")
+    if g is None:
+        pytest.skip("no golden file for c5_tf32")
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1810_04125_gb300 import build, hss
+    build.build()
+    kv, nodes = g
+    n, leaf = int(kv["n"]), int(kv["leaf"])
+    k = torch.arange(n, dtype=torch.float64, device=gu.dev())
+    coef = torch.cos(0.3 * k) / (1.0 + k)
+    src = hss.toeplitz_source(coef, coef)
+    R = w.round_to_tf32(w.gaussian_matrix(0, n, 0, 1024))
+    opts = hss.make_opts(leaf, 1e-4, 1e-10, 256, 128, 1024, hss.HSS_INCREMENTING, gu.PREC["tf32x2"], 10, 0,
+                         gu.col_major(R))
+    H = hss.hss_compress(src, opts)
+    del R
+    st = H.stats()
+    assert st.converged == int(kv["converged"]) == 1
+    assert (st.d_final, st.n_adapt) == (int(kv["d_final"]), int(kv["n_adapt"]))
+    bad, diffs = [], []
+    for i, (kr, kc) in H.ranks().items():
+        ref = nodes[i]
+        for k_g, k_o, band in ((kr, ref["kr"], ref["near_mixed"][0]), (kc, ref["kc"], ref["near_mixed"][1])):
+            diffs.append(abs(k_g - k_o))
+            if abs(k_g - k_o) > band:
+                bad.append((i, k_g, k_o, band))
+    print(f"c5_tf32: {len(diffs)} node sides, rank differences: max {max(diffs)}, "
+          f"sum {sum(diffs)}, nonzero {sum(1 for x in diffs if x)}")
+    assert not bad, bad
+    # ||A - H||_F / ||A||_F by blocks of columns: H applied to the identity's
+    # columns against the columns of A built from the diagonals
+    blk = 4096
+    num = den = 0.0
+    I = torch.arange(n, device=gu.dev())
+    for j0 in range(0, n, blk):
+        wd = min(blk, n - j0)
+        X = torch.zeros((wd, n), dtype=torch.float64, device=gu.dev()).t()
+        X[j0 + torch.arange(wd, device=gu.dev()), torch.arange(wd, device=gu.dev())] = 1.0
+        Y = torch.empty((wd, n), dtype=torch.float64, device=gu.dev()).t()
+        hss.hss_matvec(H, X, Y)
+        J = torch.arange(j0, j0 + wd, device=gu.dev())
+        Ab = coef[(I[:, None] - J[None, :]).abs()]
+        num += float(((Ab - Y) ** 2).sum())
+        den += float((Ab ** 2).sum())
+        del X, Y, Ab
+    err = (num / den) ** 0.5
+    print(f"c5_tf32: error {err:.4e}, oracle {float(kv['rel_error']):.4e}")
     assert err <= 1.1 * float(kv["rel_error"]), (err, kv["rel_error"])
