@@ -124,3 +124,28 @@ def near_threshold_count(S: np.ndarray, er: float, ea: float, rule: str, mh: int
         if abs(s - thr) <= band * thr + noise:
             cnt += 1
     return cnt
+
+
+def near_threshold_count_qr(S: np.ndarray, er: float, ea: float, rule: str, mh: int = 0, nh: int = 0,
+                            band: float = 0.1, noise: float = 0.0) -> int:
+    """Number of pivots j of the full QRCP of S^* (d x m) whose |R_jj| lies
+    within +-band of the rank threshold at its position -- the quantity the
+    ID's rule itself compares (P4; eq. RRQRHMTstop divides the threshold by
+    f(j + 1) under ``rule == "hmt"``), where near_threshold_count looks at
+    the singular values.  Two QRCPs of the same sample in different
+    arithmetic can stop one pivot apart at each such |R_jj|.  ``noise``
+    widens the band as there."""
+    W = np.asarray(S, dtype=np.float64).T
+    d, m = W.shape
+    if min(d, m) == 0:
+        return 0
+    _, R, _, _ = qrcp(W, lambda j, rjj, r11: False)
+    rd = np.abs(np.diag(R))
+    r11 = float(rd[0])
+    cnt = 0
+    for j, r in enumerate(rd):
+        f = hmt_factor(j + 1, d, mh, nh) if rule == "hmt" else 1.0
+        thr = max(ea, er * r11) / f
+        if abs(r - thr) <= band * thr + noise:
+            cnt += 1
+    return cnt

@@ -4,10 +4,12 @@ Writes ``tests/golden/fullsize_<case>.txt`` from the plain CPU oracle alone
 (``oracle/`` and ``workloads/``; nothing of the CUDA library is imported or
 run): the passes (d_final, adaptations), every node's ranks, the number of
 singular values of each node's sample within 10 % of its rank threshold
-(the tie rule of the rank comparison) and, for the cases whose GPU form
-samples in TF32 x 2, that number with the band widened by the tested bound
-of the mixed sampling error (5e-7 of the rows of the sample the node's
-local sample is formed from; Weyl's inequality), the error
+(the tie rule of the rank comparison), the same count for the diagonal of
+the node's full QRCP (|R_jj| near the threshold: the ID rule's own
+decision quantity) and, for the cases whose GPU form samples in TF32 x 2,
+both counts with the band widened by the tested bound of the mixed sampling
+error (5e-7 of the rows of the sample the node's local sample is formed
+from; Weyl's inequality for the singular values), the error
 ||A - H||_F / ||A||_F (paper section 4.4.1) and the oracle's wall time on
 this host.
 
@@ -126,7 +128,8 @@ def main(names):
                  f"case {name}", f"n {n}", f"leaf {o.leaf}", f"converged {int(res.converged)}",
                  f"d_final {res.d_final}", f"n_adapt {res.n_adapt}", f"rel_error {err:.6e}",
                  f"oracle_seconds {t_compress:.1f}", f"cores {os.cpu_count()}",
-                 "# node level kr kc near_r near_c near_mixed_r near_mixed_c d_id"]
+                 "# node level kr kc near_r near_c near_mixed_r near_mixed_c d_id "
+                 "qr_near_r qr_near_c qr_near_mixed_r qr_near_mixed_c"]
         rule = "hmt" if o.strategy == "doubling" else "plain"
         norms = sample_row_norms(src, R, res) if name.endswith("tf32") else None
         for t in res.nodes[1:]:
@@ -134,17 +137,20 @@ def main(names):
                 continue
             scale = 1.0 / t.level if o.level_tol_scaling else 1.0
             er, ea = o.rtol * scale, o.atol * scale
-            near, near_m = [], []
+            near, near_m, qnear, qnear_m = [], [], [], []
             for side, S in (("r", t.Sr), ("c", t.Sc)):
                 S = S[:, :t.d_id]
                 near.append(qrcp.near_threshold_count(S, er, ea, rule, t.size, n - t.size))
+                qnear.append(qrcp.near_threshold_count_qr(S, er, ea, rule, t.size, n - t.size))
                 if norms is None:
                     near_m.append(near[-1])
+                    qnear_m.append(qnear[-1])
                 else:
                     noise = MIXED_NOISE * norms(t, side)
                     near_m.append(qrcp.near_threshold_count(S, er, ea, rule, t.size, n - t.size, noise=noise))
+                    qnear_m.append(qrcp.near_threshold_count_qr(S, er, ea, rule, t.size, n - t.size, noise=noise))
             lines.append(f"{t.idx} {t.level} {len(t.Jr)} {len(t.Jc)} {near[0]} {near[1]} {near_m[0]} {near_m[1]} "
-                         f"{t.d_id}")
+                         f"{t.d_id} {qnear[0]} {qnear[1]} {qnear_m[0]} {qnear_m[1]}")
         path = os.path.join(HERE, f"fullsize_{name}.txt")
         open(path, "w").write("\n".join(lines) + "\n")
         print(f"{name}: d_final {res.d_final}, adaptations {res.n_adapt}, max rank {res.max_rank()}, "

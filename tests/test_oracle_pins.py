@@ -722,3 +722,25 @@ def test_incrementing_relative_tests():
     for rho, want in ((10.0, True), (4.0, False)):
         st = dict(Q=np.zeros((m, 0)), rho=rho)
         assert hss.incrementing_block_test(S2, st, 0.0051, 0.0) == want, rho
+
+
+def test_near_threshold_count_qr_by_hand():
+    """The tie count on the QRCP diagonal (the rank rule's own quantity).
+    Orthogonal rows of prescribed norms: the pivots take them in decreasing
+    order and |R_jj| are the norms themselves, so the count follows by hand.
+    Two nearly parallel rows e1 and e1 + 1e-3 e2: |R_22| is the distance of
+    e1 from the first pivot's line, 1e-3 / sqrt(1 + 1e-6), right at a
+    threshold of 1e-3, while the smaller singular value is near
+    1e-3 / sqrt(2): only the diagonal count sees the tie."""
+    rng = np.random.default_rng(3)
+    Qm, _ = np.linalg.qr(rng.standard_normal((8, 8)))
+    norms = np.array([1.0, 0.5, 1.05e-3, 0.95e-3, 1e-5])
+    S = norms[:, None] * Qm[:5, :]          # 5 orthogonal rows, d = 8
+    assert qrcp.near_threshold_count_qr(S, 1e-3, 0.0, "plain") == 2
+    assert qrcp.near_threshold_count_qr(S, 1e-3, 0.0, "plain", band=0.01) == 0
+    assert qrcp.near_threshold_count_qr(S, 1e-3, 0.0, "plain", band=0.01, noise=1e-4) == 2
+    assert qrcp.near_threshold_count_qr(S, 0.0, 1e-5, "plain") == 1          # absolute threshold
+    T = np.array([[1.0, 0.0, 0.0, 0.0], [1.0, 1e-3, 0.0, 0.0]])
+    er = 1e-3 / np.sqrt(1.0 + 1e-6)    # threshold er |R_11| = 1e-3
+    assert qrcp.near_threshold_count_qr(T, er, 0.0, "plain") == 1
+    assert qrcp.near_threshold_count(T, er, 0.0, "plain") == 0
