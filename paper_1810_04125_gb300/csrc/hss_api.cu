@@ -313,6 +313,7 @@ struct Ctx {
   cudaStream_t st = nullptr;
   Scratch scratch;
   DevBuf jobs;
+  DevBuf gpack;   // operands of the tensor-core tile products split into their terms
   int* d_flag = nullptr;
   int nflag = 0;
   int* h_pinned = nullptr;
@@ -334,6 +335,7 @@ struct Ctx {
     for (auto& e : trace_ev)
       if (e) cudaEventDestroy(e);
     jobs.release(st);
+    gpack.release(st);
     if (d_flag) cudaFreeAsync(d_flag, st);
     scratch.release();
     if (h_pinned) cudaFreeHost(h_pinned);
@@ -534,15 +536,69 @@ hss_status run_gemms(Ctx& c, const std::vector<GemmJob>& jobs, const char* tag =
   }
   if (tiles.empty()) return HSS_OK;
   if (c.trace) CK(cudaEventRecord(c.trace_ev[0], c.st));
+  // tensor-core form: every operand split once into its TF32 terms (tiles
+  // in a context buffer reused in stream order) when the jobs are large
+  // (on average 2^18 operand elements or more: below that the extra launch
+  // and the packed copy cost more than the repeated splitting saves,
+  // measured on the batch of 64 matrices) and the tiles take at most 4 GB;
+  // else the kernel that splits while it stages
+  std::vector<GemmJob> pj;
+  std::vector<PackUnit> units;
+  bool packed = false;
+  if (tc) {
+    pj = jobs;
+    const size_t ab = gemm_tc_tile_bytes(0, tn), bb = gemm_tc_tile_bytes(1, tn);
+    size_t total = 0;
+    double elems = 0.0;
+    int njob = 0;
+    std::vector<size_t> oa(jobs.size(), 0), ob(jobs.size(), 0);
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      const GemmJob& j = jobs[i];
+      if (j.M <= 0 || j.N <= 0 || j.K <= 0) continue;
+      const size_t nkt = (j.K + 31) / 32, nrb = (j.M + tm - 1) / tm, ncb = (j.N + tn - 1) / tn;
+      oa[i] = total;
+      total += nrb * nkt * ab;
+      ob[i] = total;
+      total += ncb * nkt * bb;
+      elems += (double)j.K * ((double)j.M + (double)j.N);
+      njob++;
+    }
+    packed = total > 0 && total <= (size_t(4) << 30) && elems >= 262144.0 * njob;
+    if (packed) {
+      CK(c.gpack.ensure(total, c.st));
+      for (size_t i = 0; i < jobs.size(); ++i) {
+        GemmJob& j = pj[i];
+        if (j.M <= 0 || j.N <= 0 || j.K <= 0) continue;
+        const int nkt = (j.K + 31) / 32, nrb = (j.M + tm - 1) / tm, ncb = (j.N + tn - 1) / tn;
+        j.pa = (unsigned char*)c.gpack.p + oa[i];
+        j.pb = (unsigned char*)c.gpack.p + ob[i];
+        j.nkt = nkt;
+        for (int t = 0; t < nrb; ++t)
+          for (int kt = 0; kt < nkt; ++kt) units.push_back({(int)i, 0, t, kt});
+        for (int t = 0; t < ncb; ++t)
+          for (int kt = 0; kt < nkt; ++kt) units.push_back({(int)i, 1, t, kt});
+      }
+    }
+  }
   Staging sg;
-  const size_t oj = sg.put(jobs.data(), jobs.size() * sizeof(GemmJob));
+  const size_t oj = sg.put(packed ? pj.data() : jobs.data(), jobs.size() * sizeof(GemmJob));
   const size_t ot = sg.put(tiles.data(), tiles.size() * sizeof(GemmTile));
+  const size_t ou = packed ? sg.put(units.data(), units.size() * sizeof(PackUnit)) : 0;
   char* dev;
   CKS(sg.send(c, &dev));
-  if (tc) CK(launch_gemm_tc((const GemmJob*)(dev + oj), (const GemmTile*)(dev + ot), (int)tiles.size(), tn,
-                            c.d_flag + 3, c.st));
-  else CK(launch_gemm((const GemmJob*)(dev + oj), (const GemmTile*)(dev + ot), (int)tiles.size(), c.st));
-  c.launches++;
+  if (packed) {
+    CK(launch_gemm_tc_pack((const GemmJob*)(dev + oj), (const PackUnit*)(dev + ou), (int)units.size(), tn, c.st));
+    CK(launch_gemm_tc_packed((const GemmJob*)(dev + oj), (const GemmTile*)(dev + ot), (int)tiles.size(), tn,
+                             c.d_flag + 3, c.st));
+    c.launches += 2;
+  } else if (tc) {
+    CK(launch_gemm_tc((const GemmJob*)(dev + oj), (const GemmTile*)(dev + ot), (int)tiles.size(), tn,
+                      c.d_flag + 3, c.st));
+    c.launches++;
+  } else {
+    CK(launch_gemm((const GemmJob*)(dev + oj), (const GemmTile*)(dev + ot), (int)tiles.size(), c.st));
+    c.launches++;
+  }
   if (c.trace) {
     CK(cudaEventRecord(c.trace_ev[1], c.st));
     CK(cudaEventSynchronize(c.trace_ev[1]));

@@ -70,7 +70,15 @@ struct GemmJob {
   int c_split;
   int M, N, K;
   double alpha, beta, gamma;
+  // tensor-core form with packed operands (launch_gemm_tc_packed): A as
+  // tiles (ti, kt) of 128 rows x 32 k, B^T as tiles (tj, kt) of tile_n rows
+  // x 32 k, the three TF32 terms of a tile one after another
+  unsigned char* pa;
+  unsigned char* pb;
+  int nkt;
 };
+// One tile of an operand to pack: job, operand (0 = A, 1 = B), row tile, k tile.
+struct PackUnit { int job, which, tile, kt; };
 // One output tile of one job; k0..k1 is its share of K (split-K tiles add
 // alpha * partial into C atomically: the job then has beta == 0 and
 // gamma == 1, or gamma == 0 with C zeroed beforehand).
@@ -211,6 +219,15 @@ cudaError_t launch_gemm(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int 
 int gemm_tc_tile_n(int max_n);
 cudaError_t launch_gemm_tc(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles, int tile_n,
                            int* err, cudaStream_t st);
+// The same product from operands split once into their TF32 terms: the
+// pack kernel writes every listed operand tile (bytes per tile:
+// gemm_tc_tile_bytes), then one thread per CTA streams a tile pair per k-tile
+// by bulk copy and sixteen warps drain the chains.
+size_t gemm_tc_tile_bytes(int which, int tile_n);
+cudaError_t launch_gemm_tc_pack(const GemmJob* jobs_dev, const PackUnit* units_dev, int nunits, int tile_n,
+                                cudaStream_t st);
+cudaError_t launch_gemm_tc_packed(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles, int tile_n,
+                                  int* err, cudaStream_t st);
 // map == nullptr: one CTA per job; otherwise the launch is cooperative and
 // map holds the (job, rank within the job's group) of every position, (-1,
 // -1) for an idle one.  With place == nullptr CTA b takes map[b]; with

@@ -85,10 +85,9 @@ __device__ __forceinline__ const double* op_row(const Opnd& o, int i) {
 // l0..l0+3 (0 outside the job).  rows_fast: consecutive lanes take
 // consecutive tile rows (unit stride along the rows in global memory), else
 // consecutive 16-byte chunks along K.
-template <class F>
+template <class F, int NP = GT_WARPS * 32>
 __device__ __forceinline__ void stage_tile(uint8_t* dst, uint32_t term_bytes, int rows, bool rows_fast,
                                            int tid, F elem) {
-  constexpr int NP = GT_WARPS * 32;
   for (int u = tid; u < rows * GT_KC; u += NP) {
     int r, c;
     if (rows_fast) { r = u % rows; c = u / rows; }
@@ -263,6 +262,169 @@ __global__ void __maxnreg__(96) k_gemm_tc(const GemmJob* __restrict__ jobs,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Packed operands.  k_gemm_tc splits every operand element again for every
+// output tile that reads it (A once per column tile, B once per row tile);
+// here each element is split once into its three terms, in the canonical
+// layout of stage_tile, and the product kernel only moves whole tiles.
+template <int N>
+__global__ void __launch_bounds__(256) k_gemm_pack(const GemmJob* __restrict__ jobs,
+                                                   const PackUnit* __restrict__ units) {
+  constexpr uint32_t tileB = (uint32_t)N * 128u;
+  const PackUnit u = units[blockIdx.x];
+  const GemmJob& j = jobs[u.job];
+  const int k0 = u.kt * GT_BK, K = j.K;
+  if (u.which == 0) {
+    uint8_t* dst = j.pa + ((size_t)u.tile * j.nkt + u.kt) * (GT_T * (size_t)TILE_A_BYTES);
+    const int i0 = u.tile * BM, M = j.M;
+    const bool rows_fast = j.A.rs == 1 && !j.A.rows;
+    const long long cs = j.A.cs;
+    auto elem = [&](int r, int kc, double* v) {
+      const int i = i0 + r;
+      const double* row = i < M ? op_row(j.A, i) : nullptr;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int l = k0 + kc + x;
+        v[x] = (row && l < K) ? row[(long long)l * cs] : 0.0;
+      }
+    };
+    stage_tile<decltype(elem), 256>(dst, TILE_A_BYTES, BM, rows_fast, threadIdx.x, elem);
+  } else {
+    uint8_t* dst = j.pb + ((size_t)u.tile * j.nkt + u.kt) * (GT_T * (size_t)tileB);
+    const int j0 = u.tile * N, Nj = j.N;
+    const bool rows_fast = j.B.cs == 1;
+    const long long cs = j.B.cs;
+    auto elem = [&](int r, int kc, double* v) {
+      const int c = j0 + r;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int l = k0 + kc + x;
+        v[x] = (c < Nj && l < K) ? op_row(j.B, l)[(long long)c * cs] : 0.0;
+      }
+    };
+    stage_tile<decltype(elem), 256>(dst, tileB, N, rows_fast, threadIdx.x, elem);
+  }
+}
+
+constexpr int GP_THREADS = (2 + GT_WARPS) * 32;   // copy warp, MMA warp, 16 drain warps
+
+template <int N>
+__global__ void __maxnreg__(96) k_gemm_tc_pk(const GemmJob* __restrict__ jobs,
+                                              const GemmTile* __restrict__ tiles, int tmem_cols, int* err) {
+  constexpr int NH = N / 4, NS = gt_stages<N>();
+  constexpr uint32_t tileB = (uint32_t)N * 128u;
+  constexpr uint32_t a_bytes = GT_T * TILE_A_BYTES, b_bytes = GT_T * tileB;
+  constexpr uint32_t stage_bytes = a_bytes + b_bytes;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ GemmJob sj;
+  uint64_t* full = (uint64_t*)(smem + NS * stage_bytes);
+  uint64_t* empty = full + NS;
+  uint64_t* tfull = empty + NS;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const GemmTile tl = tiles[blockIdx.x];
+  if (tid == 0) {
+    sj = jobs[tl.job];
+    for (int s = 0; s < NS; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], GT_WARPS); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int M = sj.M, Nj = sj.N, K = sj.K;
+  const int i0 = tl.ti * BM, j0 = tl.tj * N;
+  const int nk = (K + GT_BK - 1) / GT_BK;   // one chain per k-tile
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint8_t* gA = sj.pa + (size_t)tl.ti * sj.nkt * a_bytes;
+      const uint8_t* gB = sj.pb + (size_t)tl.tj * sj.nkt * b_bytes;
+      int st = 0;
+      uint32_t ph = 0u;
+      for (int it = 0; it < nk; ++it) {
+        if (it > 0 && ++st == NS) { st = 0; ph ^= 1u; }
+        if (!mbar_wait(&empty[st], ph ^ 1u, err, 26)) break;
+        uint8_t* sp = smem + st * stage_bytes;
+        mbar_expect_tx(&full[st], stage_bytes);
+        bulk_g2s(sp, gA + (size_t)it * a_bytes, a_bytes, &full[st]);
+        bulk_g2s(sp + a_bytes, gB + (size_t)it * b_bytes, b_bytes, &full[st]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc(2u, (uint32_t)N);
+      int st = 0;
+      uint32_t ph = 0u;
+      for (int it = 0; it < nk; ++it) {
+        if (it > 0 && ++st == NS) { st = 0; ph ^= 1u; }
+        const int b = it & 1;
+        if (!mbar_wait(&tempty[b], ((uint32_t)(it >> 1) & 1u) ^ 1u, err, 27)) break;
+        if (!mbar_wait(&full[st], ph, err, 28)) break;
+        tc_fence_after();
+        mma_pairs(smem_u32(smem + st * stage_bytes), tileB, tmem, N, b, id);
+        mma_commit(&empty[st]);
+        mma_commit(&tfull[b]);
+      }
+    }
+  } else {
+    // drain warps 2 .. 17: TMEM lane quarter warp % 4, column quarter h
+    const int q = warp % 4, h = (warp - 2) / 4;
+    float s[NH], e[NH];
+#pragma unroll
+    for (int x = 0; x < NH; ++x) { s[x] = 0.f; e[x] = 0.f; }
+    bool ok = true;
+    for (int cd = 0; cd < nk; ++cd) {
+      const int b = cd & 1;
+      if (!mbar_wait_warp(&tfull[b], (uint32_t)(cd >> 1) & 1u, err, 29)) { ok = false; break; }
+      tc_fence_after();
+      drain_chain<NH>(tmem, N, b, q, h, s, e);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+    // epilogue: C(rows_c(i), j) = alpha acc + beta C0(i, j) + gamma C(...)
+    const int i = i0 + 32 * q + lane;
+    if (ok && i < M) {
+      int r = sj.c_rows ? sj.c_rows[i] : i;
+      double* base = sj.C;
+      if (r >= sj.c_split) { base = sj.C2; r -= sj.c_split; }
+      double* out = base + (long long)r * sj.c_rs;
+      const double* c0 = sj.beta != 0.0 ? op_row(sj.C0, i) : nullptr;
+      const double alpha = sj.alpha, beta = sj.beta, gamma = sj.gamma;
+      const long long ccs = sj.c_cs, c0cs = sj.C0.cs;
+      const int jb = j0 + h * NH;
+#pragma unroll
+      for (int x = 0; x < NH; ++x) {
+        const int jj = jb + x;
+        if (jj < Nj) {
+          double v = alpha * (f2d_exact(s[x]) + f2d_exact(e[x]));
+          if (c0) v += beta * c0[(long long)jj * c0cs];
+          double* dst = out + (long long)jj * ccs;
+          if (gamma != 0.0) v += gamma * *dst;
+          *dst = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)tmem_cols)
+                 : "memory");
+  }
+}
+
 template <int N>
 cudaError_t launch_t(const GemmJob* jobs, const GemmTile* tiles, int ntiles, int* err, cudaStream_t st) {
   constexpr int NS = gt_stages<N>();
@@ -287,6 +449,32 @@ cudaError_t launch_gemm_tc(const GemmJob* jobs_dev, const GemmTile* tiles_dev, i
   if (ntiles <= 0) return cudaSuccess;
   if (tile_n == 64) return launch_t<64>(jobs_dev, tiles_dev, ntiles, err, st);
   return cudaErrorInvalidValue;
+}
+
+size_t gemm_tc_tile_bytes(int which, int tile_n) {
+  return which == 0 ? (size_t)GT_T * TILE_A_BYTES : (size_t)GT_T * tile_n * 128;
+}
+
+cudaError_t launch_gemm_tc_pack(const GemmJob* jobs_dev, const PackUnit* units_dev, int nunits, int tile_n,
+                                cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  if (tile_n != 64) return cudaErrorInvalidValue;
+  k_gemm_pack<64><<<nunits, 256, 0, st>>>(jobs_dev, units_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc_packed(const GemmJob* jobs_dev, const GemmTile* tiles_dev, int ntiles, int tile_n,
+                                  int* err, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (tile_n != 64) return cudaErrorInvalidValue;
+  constexpr int N = 64, NS = gt_stages<64>();
+  const size_t sm = (size_t)NS * GT_T * (TILE_A_BYTES + (size_t)N * 128) + 8 * (2 * NS + 4) + 16 + 1024;
+  int tc = 32;
+  while (tc < 4 * N) tc *= 2;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc_pk<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_gemm_tc_pk<N><<<ntiles, GP_THREADS, sm, st>>>(jobs_dev, tiles_dev, tc, err);
+  return cudaGetLastError();
 }
 
 }  // namespace hss
