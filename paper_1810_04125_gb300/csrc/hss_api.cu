@@ -1214,8 +1214,20 @@ hss_status incrementing_tests(Ctx& c, const std::vector<std::pair<hss_matrix_s*,
         Node& t = H->nodes[id];
         for (int sd = 0; sd < (H->sym ? 1 : 2); ++sd) {
           Side& s = sd ? t.c : t.r;
-          if (s.done) s.tested = H->d;
-          else if (H->d > s.tested) sides.push_back({H, id, sd});
+          if (s.done) {
+            s.tested = H->d;
+          } else if (H->d > s.tested) {
+            // a block that brings the basis to m columns leaves the side
+            // sufficient whatever its test finds (the test passes, or Q_k
+            // joins and spans every row, P18): nothing to compute
+            const int be = block_end(H, s.tested);
+            if (s.q + (be - s.tested) >= s.m) {
+              s.tested = be;
+              s.done = true;
+            } else {
+              sides.push_back({H, id, sd});
+            }
+          }
         }
         if (H->sym) t.c = t.r;
       }
