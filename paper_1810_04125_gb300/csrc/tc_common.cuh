@@ -242,7 +242,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // accumulates only a short chain (DRAIN k-tiles) into one of two TMEM
 // buffers, with the leading split term (HI) and the correction terms (LO) in
 // separate accumulators; drain warps move a finished chain into per-thread
-// float-float (TwoSum) accumulators while the tensor core fills the other
+// float-float (compensated-sum) accumulators while the tensor core fills the other
 // buffer.  TMEM columns: buffer b, accumulator x at (2 b + x) N.
 //
 // Drain thread layout: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows) and
@@ -265,14 +265,16 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// (s, e) += x + y as float-float: TwoSum of s and x, then the low part
-// collects the rounding error and the (small) correction y.
-__device__ __forceinline__ void ff_add(float& s, float& e, float x, float y) {
-  const float t = __fadd_rn(s, x);
-  const float bp = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+// (s, e) += x by compensated (Kahan) summation: the pending correction e
+// joins the addend, and e keeps what the addition to s lost.  The sum of the
+// chains is then exact to about two roundings of its value, whatever their
+// number (Kahan's bound), in four additions instead of the seven of an
+// error-free TwoSum.
+__device__ __forceinline__ void ff_add(float& s, float& e, float x) {
+  const float xc = __fadd_rn(x, e);
+  const float t = __fadd_rn(s, xc);
+  e = __fsub_rn(xc, __fsub_rn(t, s));
   s = t;
-  e = __fadd_rn(e, __fadd_rn(err, y));
 }
 
 // Drain one finished chain from TMEM buffer b into (s, e).
@@ -287,7 +289,7 @@ __device__ __forceinline__ void drain_chain(uint32_t tmem, int N, int b, int q, 
     tmem_ld16_nw(hi + c, x);
     tmem_wait_ld();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) ff_add(s[c + i], e[c + i], x[i], 0.0f);
+    for (int i = 0; i < 16; ++i) ff_add(s[c + i], e[c + i], x[i]);
     tmem_ld16_nw(lo + c, x);
     tmem_wait_ld();
 #pragma unroll
