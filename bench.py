@@ -196,6 +196,7 @@ def run_gpu(args):
         cfg["workload"] = WORKLOAD["workload"].replace("16384", str(args.n))
     n = cfg["n"]
     P, A = build_inputs(dev, n, cfg["dim"], cfg["seed"], cfg["leaf"])
+    torch.cuda.synchronize()   # A is built on torch's stream; the library runs on its own
     PREC = {"fp64": hss.HSS_PREC_FP64, "tf32x2": hss.HSS_PREC_TF32X2, "bf16x3": hss.HSS_PREC_BF16X3}
     src = hss.dense_source(A)
 
@@ -225,6 +226,7 @@ def run_gpu(args):
             X = torch.zeros((w_, n), dtype=torch.float64, device=dev).t()
             X[j0:j0 + w_].copy_(torch.eye(w_, dtype=torch.float64, device=dev))
             Y = torch.empty((w_, n), dtype=torch.float64, device=dev).t()
+            stream.wait_stream(torch.cuda.current_stream())   # X is written on torch's stream
             hss.hss_matvec(H, X, Y, stream=stream)
             torch.cuda.synchronize()
             num += float(((A[:, j0:j0 + w_] - Y) ** 2).sum())
@@ -536,6 +538,7 @@ def run_config(args):
             edata = (src.kind, (X, src.p0))
         members.append((ds, src.n, edata))
         leaf, rtol, atol, strat, d0, dd, prec = W.leaf, W.rtol, W.atol, W.strategy, W.d0, W.dd, W.precision
+    torch.cuda.synchronize()   # the sources are built on torch's stream; the library runs on its own
     op = None
     if c == "c5op":   # FP64 sampling through the FFT operator; entries from the Toeplitz source
         op = hss.make_operator(_toeplitz_fft_operator(edata[1][0], edata[1][1]))
@@ -578,6 +581,7 @@ def run_config(args):
                 w_ = min(blk, n - j0)
                 Xi.zero_()
                 Xi[j0:j0 + w_, :w_].copy_(torch.eye(w_, dtype=torch.float64, device=dev))
+                stream.wait_stream(torch.cuda.current_stream())   # Xi is written on torch's stream
                 hss.hss_matvec(H, Xi[:, :w_], Y[:, :w_], stream=stream)
                 torch.cuda.synchronize()
                 Ab = ed[:, j0:j0 + w_] if c == "c4" else _entries_block(ed[0], ed[1], n, j0, w_, dev)
@@ -732,6 +736,7 @@ def run_table3(args):
                 "converged": int(st.converged), "rank": max(st.max_rank_r, st.max_rank_c),
                 "d_final": st.d_final, "compress_s": e0.elapsed_time(e1) / 1e3, "rel_error": None}
         if st.converged:
+            stream.wait_stream(torch.cuda.current_stream())
             hss.hss_to_dense(H, H_dense, stream=stream)
             torch.cuda.synchronize()
             cell["rel_error"] = float(torch.linalg.norm(H_dense - At)) / nA
@@ -795,6 +800,7 @@ def run_table4(args):
             wdt = min(blk, n - j0)
             E.zero_()
             E[j0:j0 + wdt, :wdt].copy_(torch.eye(wdt, dtype=torch.float64, device=dev))
+            stream.wait_stream(torch.cuda.current_stream())   # E is written on torch's stream
             hss.hss_matvec(H, E[:, :wdt], Y[:, :wdt], stream=stream)
             torch.cuda.synchronize()
             num += float(((Y[:, :wdt] - G[j0:j0 + wdt].t()) ** 2).sum())

@@ -378,8 +378,13 @@ hss_status hss_load(const char* path, hss_matrix* out);
 
 /* hss_free (and a failed compression) keep the handle's device memory in
  * 256 MB chunks, up to 32 GB per device, for the next compression on the same
- * device (after waiting for the device, as cudaFree would).  This call
- * returns the chunks cached for the current device with cudaFree. */
+ * device (after waiting for the device, as cudaFree would).  The work buffers
+ * of a call (packed operands, job lists, temporaries) come stream-ordered
+ * from a memory pool of the library's own per context, which keeps freed
+ * memory reserved, at most the largest set of work buffers one call held at
+ * once (the device's default pool is not touched).
+ * This call returns the chunks cached for the current device with cudaFree
+ * and, after waiting for the device, trims that pool to nothing. */
 hss_status hss_release_cached(void);
 const char* hss_status_str(hss_status s);
 const char* hss_last_error(void);

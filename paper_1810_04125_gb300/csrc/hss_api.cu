@@ -17,6 +17,8 @@
 #include <queue>
 #include <vector>
 
+#include <cuda.h>
+
 #include "hss_internal.h"
 
 #include <nvtx3/nvToolsExt.h>
@@ -70,6 +72,91 @@ struct ChunkCache {
 ChunkCache& chunk_cache() {
   static ChunkCache c;
   return c;
+}
+
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+
+// Id of the current context (driver entry points looked up through the
+// runtime, so the library does not link the driver library itself); false
+// when there is no current context yet or the lookup is unavailable.
+bool current_context_id(unsigned long long* id) {
+  static ctx_get_current_fn get_current = nullptr;
+  static ctx_get_id_fn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return false;
+    get_current = (ctx_get_current_fn)f1;
+    get_id = (ctx_get_id_fn)f2;
+  }
+  CUcontext ctx = nullptr;
+  return get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Stream-ordered buffers (packed operands, job lists, temporaries) come from
+// a memory pool of the library's own, one per context, that keeps the freed
+// memory reserved (at most the largest set of buffers one call held at
+// once).  The device's default pool returns freed memory to the system at
+// every synchronisation, and mapping it again cost milliseconds per
+// allocation (a batch of 64 matrices spent 29 % of its time there); the
+// default pool's own setting is left alone for the other users of it in the
+// process.  hss_release_cached trims the pool.
+struct PoolCache {
+  std::mutex mu;
+  std::vector<std::pair<unsigned long long, cudaMemPool_t>> pools;   // (context id, pool)
+};
+PoolCache& pool_cache() {
+  static PoolCache c;
+  return c;
+}
+
+cudaError_t lib_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  unsigned long long id = 0;
+  if (!current_context_id(&id)) {
+    cudaFree(nullptr);   // makes the device's primary context current
+    if (!current_context_id(&id)) return cudaDeviceGetDefaultMemPool(out, dev);
+  }
+  PoolCache& c = pool_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  for (auto& q : c.pools)
+    if (q.first == id) {
+      *out = q.second;
+      return cudaSuccess;
+    }
+  cudaMemPoolProps pp;
+  memset(&pp, 0, sizeof pp);
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.handleTypes = cudaMemHandleTypeNone;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  e = cudaMemPoolCreate(&pool, &pp);
+  if (e != cudaSuccess) return e;
+  unsigned long long keep = ~0ull;
+  e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  if (e != cudaSuccess) {
+    cudaMemPoolDestroy(pool);
+    return e;
+  }
+  c.pools.push_back({id, pool});
+  *out = pool;
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t dmalloc_async(T** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = lib_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync((void**)p, bytes, pool, st);
 }
 
 struct Arena {
@@ -290,7 +377,7 @@ struct DevBuf {
     p = nullptr;
     cap = 0;
     const size_t sz = std::max(bytes + bytes / 2, size_t(1) << 20);
-    cudaError_t e = cudaMallocAsync((void**)&p, sz, st);
+    cudaError_t e = dmalloc_async((void**)&p, sz, st);
     if (e != cudaSuccess) return e;
     cap = sz;
     return cudaSuccess;
@@ -342,7 +429,7 @@ struct Ctx {
   }
   hss_status flags(int nmat) {
     nflag = 8 + std::max(nmat, 0);
-    CK(cudaMallocAsync((void**)&d_flag, sizeof(int) * nflag, st));
+    CK(dmalloc_async((void**)&d_flag, sizeof(int) * nflag, st));
     CK(cudaMemsetAsync(d_flag, 0, sizeof(int) * nflag, st));
     return HSS_OK;
   }
@@ -739,7 +826,7 @@ hss_status sample_columns(Ctx& c, hss_matrix_s* H, int c0, int c1) {
     // the user's product A R (and A^T R), then the leaf diagonal blocks off
     CK(c.timer.mark(PH_SAMPLE, st));
     double* T = nullptr;
-    CK(cudaMallocAsync(&T, sizeof(double) * (size_t)n * w * norient, st));
+    CK(dmalloc_async(&T, sizeof(double) * (size_t)n * w * norient, st));
     for (int side = 0; side < norient; ++side) {
       const int rc = H->o.op->apply(H->o.op->ctx, side, n, w, Rc, n, T + (size_t)side * n * w, n, (void*)st);
       if (rc != 0) {
@@ -770,7 +857,7 @@ hss_status sample_columns(Ctx& c, hss_matrix_s* H, int c0, int c1) {
     if (!H->packA) {
       const size_t pb = packed_a_bytes(n, H->o.precision);
       CK(c.timer.mark(PH_SAMPLE, st));
-      CK(cudaMallocAsync(&H->packA, pb, st));
+      CK(dmalloc_async(&H->packA, pb, st));
       CK(launch_pack_a(s, H->o.leaf, H->o.precision, H->packA, st));
       c.launches++;
       // the split is part of the sampling work: a dense A read once, the
@@ -779,7 +866,7 @@ hss_status sample_columns(Ctx& c, hss_matrix_s* H, int c0, int c1) {
       CK(c.timer.mark(PH_RNG, st));
     }
     void* packR = nullptr;
-    CK(cudaMallocAsync(&packR, packed_r_bytes(n, w, H->o.precision), st));
+    CK(dmalloc_async(&packR, packed_r_bytes(n, w, H->o.precision), st));
     CK(launch_pack_r(Rc, n, n, w, H->o.precision, packR, st));
     c.launches++;
     if (sample_tc_packed_ksplit(n, w, H->o.precision) > 1) {
@@ -800,12 +887,12 @@ hss_status sample_columns(Ctx& c, hss_matrix_s* H, int c0, int c1) {
     if (H->src.kind == HSS_SRC_TOEPLITZ && !H->toep_terms) {
       // the diagonals split once per compression: the producers assemble
       // tiles from windows of them
-      CK(cudaMallocAsync(&H->toep_terms, toeplitz_terms_bytes(n, H->o.precision), st));
+      CK(dmalloc_async(&H->toep_terms, toeplitz_terms_bytes(n, H->o.precision), st));
       CK(launch_toeplitz_terms(s, H->o.precision, H->toep_terms, st));
       c.launches++;
     }
     void* packR = nullptr;
-    CK(cudaMallocAsync(&packR, packed_r_bytes(n, w, H->o.precision), st));
+    CK(dmalloc_async(&packR, packed_r_bytes(n, w, H->o.precision), st));
     CK(launch_pack_r(Rc, n, n, w, H->o.precision, packR, st));
     c.launches++;
     if (sample_tc_ksplit(n, w, H->o.precision) > 1) {
@@ -2051,6 +2138,11 @@ hss_status hss_release_cached(void) {
     }
   }
   if (dev >= 0 && dev < 64) c.held[dev] = 0;
+  // and the work-buffer pool's reserved memory, once the device is idle
+  cudaMemPool_t pool = nullptr;
+  CK(lib_pool(&pool));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemPoolTrimTo(pool, 0));
   return HSS_OK;
 }
 
@@ -2269,7 +2361,7 @@ hss_status hss_to_dense(hss_matrix H, double* out, long long ld, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int n = H->n, blk = std::min(n, 2048);
   double* X = nullptr;
-  CK(cudaMallocAsync((void**)&X, sizeof(double) * (size_t)n * blk, st));
+  CK(dmalloc_async((void**)&X, sizeof(double) * (size_t)n * blk, st));
   for (int c0 = 0; c0 < n; c0 += blk) {
     const int w = std::min(blk, n - c0);
     hss_status e = HSS_OK;
@@ -2310,7 +2402,7 @@ hss_status hss_matvec(hss_matrix H, int nrhs, const double* X, long long ldx, do
     offy[i] = tot; tot += (size_t)out_side(H->nodes[i]).k * nrhs;
   }
   double* buf = nullptr;
-  CK(cudaMallocAsync((void**)&buf, sizeof(double) * std::max<size_t>(tot, 1), st));
+  CK(dmalloc_async((void**)&buf, sizeof(double) * std::max<size_t>(tot, 1), st));
   auto xh = [&](int i) { return buf + offx[i]; };
   auto yh = [&](int i) { return buf + offy[i]; };
   const long long R_ = nrhs;
@@ -2480,7 +2572,7 @@ hss_status hss_get_entries(hss_matrix H, int nr, const int* I, int nc, const int
   const size_t b_nodes = Scratch::rnd(sizeof(EntryNode) * nn), b_inv = Scratch::rnd(sizeof(int) * std::max<size_t>(ninv, 1)),
                b_leaf = Scratch::rnd(sizeof(int) * n), b_vec = Scratch::rnd(sizeof(double) * (size_t)chunk * per);
   char* buf = nullptr;
-  CK(cudaMallocAsync((void**)&buf, b_nodes + b_inv + b_leaf + 2 * b_vec + 256, st));
+  CK(dmalloc_async((void**)&buf, b_nodes + b_inv + b_leaf + 2 * b_vec + 256, st));
   EntryNode* dn = (EntryNode*)buf;
   int* inv = (int*)(buf + b_nodes);
   int* dleaf = (int*)(buf + b_nodes + b_inv);
@@ -2594,7 +2686,7 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
       ++cnt;
     }
   int* d_lid = nullptr;
-  CK(cudaMallocAsync((void**)&d_lid, sizeof(int) * n, st));
+  CK(dmalloc_async((void**)&d_lid, sizeof(int) * n, st));
   CK(cudaMemcpyAsync(d_lid, lid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   SrcDev s = make_src(*A, d_lid);
   if (precision == HSS_PREC_FP64) {
@@ -2605,21 +2697,21 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
   // mixed forms: R rounded once to the tensor format, K split with atomics
   double* Rr = nullptr;
   int* err = nullptr;
-  CK(cudaMallocAsync((void**)&Rr, sizeof(double) * (size_t)n * std::max(ncols, 1), st));
-  CK(cudaMallocAsync((void**)&err, sizeof(int), st));
+  CK(dmalloc_async((void**)&Rr, sizeof(double) * (size_t)n * std::max(ncols, 1), st));
+  CK(dmalloc_async((void**)&err, sizeof(int), st));
   CK(cudaMemsetAsync(err, 0, sizeof(int), st));
   CK(launch_round_copy(R, ldr, Rr, n, n, ncols, precision == HSS_PREC_TF32X2 ? 1 : 2, st));
   void* pA = nullptr;
   void* pR = nullptr;
   void* tt = nullptr;
   const bool packed = A->kind == HSS_SRC_DENSE;
-  CK(cudaMallocAsync(&pR, packed_r_bytes(n, ncols, precision), st));
+  CK(dmalloc_async(&pR, packed_r_bytes(n, ncols, precision), st));
   CK(launch_pack_r(Rr, n, n, ncols, precision, pR, st));
   if (packed) {
-    CK(cudaMallocAsync(&pA, packed_a_bytes(n, precision), st));
+    CK(dmalloc_async(&pA, packed_a_bytes(n, precision), st));
     CK(launch_pack_a(s, leaf, precision, pA, st));
   } else if (A->kind == HSS_SRC_TOEPLITZ) {
-    CK(cudaMallocAsync(&tt, toeplitz_terms_bytes(n, precision), st));
+    CK(dmalloc_async(&tt, toeplitz_terms_bytes(n, precision), st));
     CK(launch_toeplitz_terms(s, precision, tt, st));
   }
   for (int side = 0; side < 2; ++side) {
@@ -2659,10 +2751,6 @@ hss_status hss_sample_offdiag(const hss_source* A, int leaf, int precision, int 
 // instead: it exists on every GPU that loads the library, until the process
 // exits, and bounds n by HSS_NOALLOC_MAX_N.
 // ===================================================================
-#include <mutex>
-
-#include <cuda.h>
-
 #define HSS_NOALLOC_MAX_N (1 << 20)   /* 4 MiB of leaf labels */
 
 static __device__ __align__(256) int g_noalloc_leaf_label[HSS_NOALLOC_MAX_N];
@@ -2689,30 +2777,6 @@ std::mutex g_noalloc_mu;
 // library's module at another address and gets a new id, so a cached
 // address never outlives its context
 std::vector<std::pair<unsigned long long, int*>> g_noalloc_ptr;
-
-typedef CUresult (*ctx_get_current_fn)(CUcontext*);
-typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
-
-// Id of the current context (driver entry points looked up through the
-// runtime, so the library does not link the driver library itself); false
-// when there is no current context yet or the lookup is unavailable.
-bool current_context_id(unsigned long long* id) {
-  static ctx_get_current_fn get_current = nullptr;
-  static ctx_get_id_fn get_id = nullptr;
-  if (!get_current || !get_id) {
-    void* f1 = nullptr;
-    void* f2 = nullptr;
-    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
-    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
-        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
-        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
-      return false;
-    get_current = (ctx_get_current_fn)f1;
-    get_id = (ctx_get_id_fn)f2;
-  }
-  CUcontext ctx = nullptr;
-  return get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, id) == CUDA_SUCCESS;
-}
 
 // Device address of the label array in the current context, looked up once
 // per context (host code must not pass the symbol itself to a kernel).  The
