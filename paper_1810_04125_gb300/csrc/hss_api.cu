@@ -2065,7 +2065,24 @@ hss_status hss_compress_batched(const hss_source* A, const hss_opts* opts, int c
   };
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
-  const double budget = 0.6 * (double)fr;
+  // memory the library already holds for reuse counts as free: the idle
+  // part of its work-buffer pool and the cached arena chunks of this device
+  double avail = (double)fr;
+  {
+    cudaMemPool_t pool = nullptr;
+    unsigned long long res = 0, used = 0;
+    if (lib_pool(&pool) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &res) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && res > used)
+      avail += (double)(res - used);
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+      ChunkCache& cc = chunk_cache();
+      std::lock_guard<std::mutex> lock(cc.mu);
+      avail += (double)cc.held[dev];
+    }
+  }
+  const double budget = 0.6 * avail;
   hss_status first = HSS_OK;
   int at = -1;
   for (size_t g0 = 0; g0 < order.size() && first == HSS_OK;) {
