@@ -269,6 +269,33 @@ def test_freed_memory_is_reused(hss, torch):
     assert H.ranks() == ranks
 
 
+def test_release_cached_returns_work_buffers(hss, torch):
+    """The work buffers of a call (packed operands, job lists) come from the
+    library's own memory pool, which keeps freed memory for the next call,
+    and the arena chunks of a freed handle stay cached: device memory stays
+    held after a mixed-form compression, and hss_release_cached gives all of
+    it back (the free memory returns to what it was before the call)."""
+    src = w.toeplitz_inverse_distance(2048)
+    o = Options(leaf=64, rtol=1e-6, atol=1e-12, d0=32, dd=32, d_max=512)
+    R = w.gaussian_matrix(7, src.n, 0, 512)
+
+    def free_after(release):
+        if release:
+            hss.hss_release_cached()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return torch.cuda.mem_get_info()[0]
+
+    H = gu.gpu_compress(src, R, o, precision="tf32x2")
+    del H
+    free0 = free_after(True)
+    H = gu.gpu_compress(src, R, o, precision="tf32x2")
+    assert H.stats().converged
+    del H
+    assert free_after(False) < free0 - (64 << 20)        # a 256 MB chunk at least, and the pool
+    assert free_after(True) >= free0 - (32 << 20)
+
+
 def test_checkpoint_round_trip(hss, torch, tmp_path):
     """hss_save / hss_load: the loaded handle has the same tree, ranks,
     statistics and generators, and its products equal the original's."""
